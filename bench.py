@@ -1,0 +1,346 @@
+#!/usr/bin/env python3
+"""Benchmark of the pole-batched exp(A)V hot path on the 1D Laplacian workload.
+
+Workload (one "step" = one evaluation of exp(T)V ~ R_16(T)V):
+  T = 100 * tridiag(1, -2, 1), N = 2^20 rows (spectrum in (-400, 0)),
+  V = 2^20 x 8 Gaussian block (float64), degree 16 -> 8 conjugate pole pairs,
+  64 complex shifted tridiagonal systems of length 2^20, residue sum fused.
+
+Printed: one JSON line (rank 0).  ``value`` is evaluations per second of the
+binary64 path with inputs resident in HBM; ``mixed`` is the float-float path;
+``e2e`` goes through the C interface with pinned HOST buffers, so the library's
+host<->device copies are inside the timed region.  Each timed step is bracketed
+by CUDA events on the launch stream; a 256 MB buffer is rewritten between steps
+to flush the 129 MB L2 (outside the step's events).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+  python bench.py --peaks        # FMA-throughput probe of the FP64/FP32 pipes
+
+Under torchrun (N > 1) every rank evaluates its own independent instance
+(weak scaling, no collective on the data path); the time is the max over ranks.
+"""
+
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "exp(A)V evals/s + p99 latency, mixed vs FP64 path at rel err ≤1e-8; % roofline"
+N_ROWS = 1 << 20
+NRHS = 8
+DEGREE = 16
+# nominal FP64 FMA rate of a GB300 SM: 1.25 TFLOP/s / (152 SMs x 2.07 GHz) = 4 flop/clk/SM
+SMS = 152
+FP64_FLOP_PER_CLK_SM = 4
+SM_MAX_MHZ = 2070.0
+# algorithmic flops per (system, column, row) of the dominant kernel (tri_block_solve):
+# forward 9 (t = v - e d' : 3, d' = g t : 6), back 8 (x = d' - c' x+ : 8), sum Re(W x) 4
+FLOPS_K3 = 21
+# dram bytes per launch of tri_block_solve<f64> from one ncu capture, valid while the
+# kernel source hashes to TRAFFIC_SRC_SHA (otherwise reported as null)
+TRAFFIC_K3 = None
+TRAFFIC_SRC_SHA = None
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--peaks", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(prefix="clocks_", suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "50"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.1)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+                power.append(float(f[3]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        loaded = [s for s in sm if s > 0.5 * max(sm)]
+        return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm), "power_w_max": max(power) if power else None}
+
+
+def kernel_sha() -> str:
+    src = os.path.join(ROOT, "paper_2306_16778_gb300", "csrc", "tridiag.cu")
+    return hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+
+
+def run_peaks():
+    import ctypes
+    from paper_2306_16778_gb300 import build as b
+    lib = ctypes.CDLL(b.build_probe())
+    lib.expm_probe_fma_tflops.restype = ctypes.c_double
+    lib.expm_probe_fma_tflops.argtypes = [ctypes.c_int] * 4
+    out = {}
+    for kind, name, iters in ((0, "fp64", 200), (1, "fp32", 4000)):
+        for bps in (4, 8, 16):
+            tf = lib.expm_probe_fma_tflops(kind, iters, bps, 5)
+            out[f"{name}_tflops_bps{bps}"] = round(tf, 4)
+    print(json.dumps({"probe": "fma_throughput", **out}))
+
+
+def cpu_oracle_eval(w, workers):
+    from oracle import coeffs, matrix
+    th, a = coeffs.theta(DEGREE), coeffs.residues(DEGREE)
+    t0 = time.perf_counter()
+    Y, _ = matrix.apply_tridiag(w["d"], w["e"], w["V"], th, a, workers=workers)
+    return Y, time.perf_counter() - t0
+
+
+def run_ours(args):
+    import torch
+    import paper_2306_16778_gb300 as P
+    import workloads
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    w = workloads.laplacian_1d(N=N_ROWS, nrhs=NRHS, offset=1 + rank)
+    plan = P.Plan(degree=DEGREE)
+    d, e, V = (torch.from_numpy(x).to(dev) for x in (w["d"], w["e"], w["V"]))
+    Y = torch.empty_like(V)
+    flush = torch.empty(64 << 20, dtype=torch.float32, device=dev)   # 256 MB > 129 MB L2
+    S = DEGREE // 2
+    K, W = args.steps, args.warmup
+
+    def timed_loop(prec, steps):
+        for _ in range(W):
+            P.expm_apply_tridiag(plan, d, e, V, Y, prec=prec)
+        torch.cuda.synchronize()
+        P.expm_profile_enable(plan, True)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        barrier()
+        torch.cuda.synchronize()
+        for a, b in ev:
+            flush.zero_()
+            a.record()
+            P.expm_apply_tridiag(plan, d, e, V, Y, prec=prec)
+            b.record()
+        torch.cuda.synchronize()
+        barrier()
+        ms = [a.elapsed_time(b) for a, b in ev]
+        prof = P.expm_profile_read(plan)
+        P.expm_profile_enable(plan, False)
+        return ms, prof
+
+    sampler = ClockSampler(local) if rank == 0 else None
+    if sampler:
+        sampler.start()
+    ms64, prof64 = timed_loop(P.EXPM_FP64, K)
+    clocks = sampler.stop() if sampler else None
+    Y64 = Y.cpu().numpy() if rank == 0 else None
+    msff, profff = timed_loop(P.EXPM_MIXED_F32X2, K)
+    Yff = Y.cpu().numpy() if rank == 0 else None
+
+    # end to end through the C interface with pinned host buffers (synchronous call)
+    hd, he, hV = (torch.from_numpy(x).pin_memory() for x in (w["d"], w["e"], w["V"]))
+    hY = torch.empty_like(hV).pin_memory()
+    Ke = max(5, K // 10)
+    for _ in range(3):
+        P.expm_apply_tridiag(plan, hd, he, hV, hY)
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(Ke):
+        P.expm_apply_tridiag(plan, hd, he, hV, hY)
+    e2e_s = time.perf_counter() - t0
+    barrier()
+
+    tot64 = sum(ms64) / 1e3
+    totff = sum(msff) / 1e3
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([tot64, totff, e2e_s], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        tot64, totff, e2e_s = (float(x) for x in t.tolist())
+    if rank != 0:
+        return
+
+    def pct(xs, q):
+        xs = sorted(xs)
+        return xs[min(len(xs) - 1, int(math.ceil(q / 100.0 * len(xs))) - 1)]
+
+    value = world * K / tot64
+    # dominant kernel of the binary64 step and its roofline
+    top = max(prof64.items(), key=lambda kv: kv[1][1])
+    kname, (klaunch, kms) = top
+    kavg_s = kms / klaunch / 1e3
+    flops = FLOPS_K3 * S * NRHS * N_ROWS
+    achieved = flops / kavg_s / 1e12
+    peak = SMS * FP64_FLOP_PER_CLK_SM * SM_MAX_MHZ * 1e6 / 1e12
+    traffic = TRAFFIC_K3 if (TRAFFIC_K3 is not None and TRAFFIC_SRC_SHA == kernel_sha()) else None
+
+    line = {
+        "metric": METRIC,
+        "value": round(value, 3),
+        "unit": "evals/s",
+        "n_gpus": world,
+        "steps": K,
+        "warmup": W,
+        "ms_per_step": round(tot64 * 1e3 / K, 4),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": "1D Laplacian 100*tridiag(1,-2,1), N=2^20, 8 Gaussian RHS, degree 16, FP64",
+                   "N": N_ROWS, "nrhs": NRHS, "degree": DEGREE, "systems": S * NRHS,
+                   "l2": "256 MB buffer rewritten between timed steps (outside the step events)",
+                   "parallelism": f"replicas{world}"},
+        "latency_ms": {"p50": round(pct(ms64, 50), 4), "p99": round(pct(ms64, 99), 4)},
+        "mixed": {"prec": "float-float (EXPM_MIXED_F32X2)", "value": round(world * K / totff, 3),
+                  "unit": "evals/s", "ms_per_step": round(totff * 1e3 / K, 4),
+                  "latency_ms": {"p50": round(pct(msff, 50), 4), "p99": round(pct(msff, 99), 4)},
+                  "kernels_ms": {k: round(v[1] / v[0], 4) for k, v in profff.items()}},
+        "kernels_ms": {k: round(v[1] / v[0], 4) for k, v in prof64.items()},
+        "roofline": {"kernel": kname, "bound": "alu", "achieved": round(achieved, 4),
+                     "peak": round(peak, 4), "unit": "TFLOP/s", "frac": round(achieved / peak, 4),
+                     "traffic": traffic,
+                     "peak_source": "derived: 152 SMs x 4 FP64 flop/clk x 2070 MHz (nominal 1.25 TFLOP/s)",
+                     "algorithmic": f"{FLOPS_K3} flop per (system, column, row) x {S}x{NRHS}x{N_ROWS}"},
+        "e2e": {"value": round(world * Ke / e2e_s, 3), "unit": "evals/s",
+                "h2d_bytes_per_step": int(8 * (N_ROWS + (N_ROWS - 1) + N_ROWS * NRHS)),
+                "d2h_bytes_per_step": int(8 * N_ROWS * NRHS)},
+        "gpu_launches": sum(v[0] for v in prof64.values()),
+        "clocks": clocks,
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        workers = min(16, os.cpu_count() or 1)
+        Yo, t = cpu_oracle_eval(w, workers)
+        from oracle import matrix
+        line["cpu_baseline"] = {"value": round(1.0 / t, 5), "unit": "evals/s", "cores": workers, "kind": "oracle",
+                                "sample": f"one full evaluation (N=2^20, 8 RHS, all 16 poles, LAPACK banded LU "
+                                          f"per pole on {workers} threads): {t:.2f} s"}
+        line["parity"] = {"fp64_rel_err": matrix.rel_err(Y64, Yo), "mixed_rel_err": matrix.rel_err(Yff, Yo),
+                          "tolerance": {"fp64": 1e-12, "mixed": 1e-8}}
+    print(json.dumps(line), flush=True)
+    plan.close()
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import workloads
+    from oracle import coeffs, matrix
+    workers = min(16, os.cpu_count() or 1)
+    rows = 1 << 17
+    w = workloads.laplacian_1d(N=rows, nrhs=1, offset=1)
+    th, a = coeffs.theta(DEGREE), coeffs.residues(DEGREE)
+    scale = (N_ROWS / rows) * NRHS            # banded solves are linear in rows and columns
+    for _ in range(args.warmup):
+        matrix.apply_tridiag(w["d"], w["e"], w["V"], th, a, workers=workers)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        matrix.apply_tridiag(w["d"], w["e"], w["V"], th, a, workers=workers)
+        times.append((time.perf_counter() - t0) * scale)
+    tot = sum(times)
+    value = args.steps / tot
+    sample = (f"per step: oracle on a 2^17-row slice of the same Laplacian, 1 RHS, all 16 poles on {workers} "
+              f"threads; time scaled x{scale:g} to one full evaluation (2^20 rows, 8 RHS)")
+    line = {"impl": "reference", "metric": METRIC, "value": round(value, 5), "unit": "evals/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(tot * 1e3 / args.steps, 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": "1D Laplacian 100*tridiag(1,-2,1), N=2^20, 8 Gaussian RHS, degree 16, FP64",
+                       "N": N_ROWS, "nrhs": NRHS, "degree": DEGREE},
+            "cpu_baseline": {"value": round(value, 5), "unit": "evals/s", "cores": workers, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": round(value, 5), "unit": "evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.peaks:
+        run_peaks()
+        return
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,182 @@
+/*
+ * expm.h -- C interface of the GB300 partial-fraction matrix-exponential library.
+ *
+ * Method (Hecht, Kaber, Perrin, Plagne, Salomon, "Parallel approximation of the
+ * exponential of Hermitian matrices"): exp(z) is approximated by the (0,n) Pade
+ * approximant R_n(z) = 1/exp_n(-z) (Sec. 2.2), whose partial-fraction form is
+ *     R_n(z) = sum_k a_k / (z + theta_k)                     (Prop. 2.1, eq. yoyo)
+ * with theta_k the roots of the truncated Taylor series exp_n (Sec. 2.1) and
+ *     a_k = -n! / prod_{j != k} (theta_k - theta_j)           (eq. yoyo2).
+ * For a Hermitian A and a block of vectors V,
+ *     exp(tA) V ~ e^c R_n(tA - cI) V = e^c sum_k a_k (tA - cI + theta_k I)^{-1} V
+ * (eqs. ExpoMatRat and expAx; the shift c of Remark 3.2): n independent shifted
+ * solves and a residue-weighted sum.  For real A and real V only one member of
+ * each conjugate pair is solved and the sum is 2 Re(...) (Remark 5.1).
+ *
+ * Conventions used throughout this header
+ * ---------------------------------------
+ * Poles and weights.  The interface carries the POLES lambda_k = -theta_k of R_n
+ *   and the WEIGHTS w_k = a_k, so that R_n(z) = sum_k w_k / (z - lambda_k) and
+ *   each solve is (tA - cI - lambda_k I) X_k = V.  Arrays of complex numbers are
+ *   interleaved (re, im) doubles; an array "of n complex" holds 2n doubles.
+ *   Conjugate pairs must be adjacent: lambda_{2l+1} = conj(lambda_{2l}) and
+ *   w_{2l+1} = conj(w_{2l}).  The degree n is even (Sec. 2.2 assumes it; an odd
+ *   n has a real root, and A - lambda I could then be singular).
+ * Layout.  Matrices are row-major; ld* are leading dimensions in ELEMENTS.
+ *   Complex data is interleaved re/im (layout-compatible with C99 double
+ *   complex, std::complex<double> and torch.complex128).
+ * Memory.  Every data pointer may be device memory or host memory; the library
+ *   tells them apart with cudaPointerGetAttributes.  Device pointers are used in
+ *   place and the call is asynchronous on opts->stream (it returns after
+ *   enqueueing; outputs are ready when the stream reaches that point).  If any
+ *   data pointer is host memory the call stages it through device workspace owned
+ *   by the plan, copies the result back and synchronises opts->stream before it
+ *   returns.  The caller owns all data buffers; they must stay valid until the
+ *   call's work on the stream is complete.
+ * Errors.  Every function returns an expm_status; nothing else is reported and no
+ *   exception or device trap crosses the interface.  On EXPM_EINVAL nothing is
+ *   enqueued.  EXPM_ECUDA means a CUDA runtime call failed; the message of the
+ *   last failure is available from expm_last_error().
+ * Threads.  A plan is not thread safe: use one plan per host thread (plans are
+ *   cheap).  Each plan belongs to the CUDA device that was current at creation.
+ */
+#ifndef EXPM_H
+#define EXPM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum expm_status {
+    EXPM_OK = 0,
+    EXPM_EINVAL = 1,     /* invalid argument (size, stride, degree, pairing, ...)   */
+    EXPM_ENOMEM = 2,     /* device workspace could not be allocated / over budget  */
+    EXPM_EGROWTH = 3,    /* pivot growth of an unpivoted LU exceeded opts.growth_max */
+    EXPM_ENOCONV = 4,    /* iterative refinement did not reach opts.tol            */
+    EXPM_ETIMEOUT = 5,   /* a bounded device-side wait gave up                     */
+    EXPM_EAGAIN = 6,     /* server: queue full, or request still pending           */
+    EXPM_ECUDA = 7,      /* a CUDA runtime call failed                             */
+    EXPM_ENOTFOUND = 8,  /* server: unknown ticket or operator id                  */
+    EXPM_ENOTSUP = 9     /* combination of options not implemented                 */
+} expm_status;
+
+typedef enum expm_precision {
+    EXPM_FP64 = 0,        /* binary64 arithmetic throughout                         */
+    EXPM_MIXED_F32X2 = 1, /* tridiagonal: float-float (pairs of binary32, ~48-bit
+                             significand) on the FP32 pipe; dense: as EXPM_MIXED_FP32 */
+    EXPM_MIXED_FP32 = 2,  /* dense: binary32 LU + binary64-residual refinement       */
+    EXPM_MIXED_TF32X3 = 3 /* dense: LU trailing updates on the tensor cores with a
+                             3-term TF32 split, + binary64-residual refinement      */
+} expm_precision;
+
+typedef struct expm_opts {
+    int prec;           /* expm_precision                                          */
+    double tol;         /* refinement target: max_k ||R_k||_F / ((||A||_F + |lambda_k|) ||X_k||_F);
+                           default 1e-14                                            */
+    int max_refine;     /* refinement sweep cap (default 6)                         */
+    double t;           /* time factor t of exp(tA)V (default 1)                    */
+    double shift_c;     /* shift c of Remark 3.2: result = e^c R_n(tA - cI) V (default 0) */
+    double growth_max;  /* allowed growth max|U|/max|A - lambda I| of the unpivoted LU
+                           (dense paths; default 1e6)                              */
+    void *stream;       /* cudaStream_t to enqueue on (NULL = legacy default stream) */
+    int flags;          /* reserved, must be 0                                      */
+} expm_opts;
+
+typedef struct expm_info {
+    int refine_iters_max;   /* largest number of refinement sweeps any pole used   */
+    double growth_max_seen; /* largest LU growth factor seen (dense paths)          */
+    double resid_rel_max;   /* largest final relative residual (mixed dense paths)  */
+    int status_worst;       /* worst per-pole expm_status                           */
+} expm_info;
+
+typedef struct expm_plan_s *expm_plan;
+
+/* Fill *opts with the defaults listed above.  Never fails for a non-NULL opts. */
+void expm_opts_default(expm_opts *opts);
+
+/* Human-readable name of a status code (static string). */
+const char *expm_status_string(expm_status s);
+
+/* Message of the most recent EXPM_ECUDA / EXPM_EINVAL in this thread ("" if none). */
+const char *expm_last_error(void);
+
+/*
+ * expm_coeffs -- poles and weights of R_n for degree n (host only, no GPU use).
+ * Sec. 2.1 (roots theta_k of exp_n) and Prop. 2.1 eq. yoyo2 (a_k), computed in
+ * double-double arithmetic (Aberth-Ehrlich iteration polished by Newton steps,
+ * residues by the product formula the paper keeps in Sec. 4) and rounded once to
+ * binary64, as the paper's Fig. 4.1 caption recommends (>= 32 digits, then 16).
+ *   degree        even, 2 <= degree <= 64
+ *   poles_ri      out, 2*degree doubles: lambda_k = -theta_k interleaved (re, im)
+ *   residues_ri   out, 2*degree doubles: w_k = a_k interleaved (re, im)
+ * Order: conjugate pairs adjacent, pairs by Re(theta) ascending, Im(theta) > 0
+ * member first.  Returns EXPM_EINVAL for an odd/out-of-range degree or NULL
+ * outputs.
+ */
+expm_status expm_coeffs(int degree, double *poles_ri, double *residues_ri);
+
+/*
+ * expm_plan_create -- validate pole data and make it resident on the current device.
+ *   poles_ri, residues_ri   host arrays of `degree` complex (see conventions)
+ *   degree                  even, 2 <= degree <= 64
+ *   out                     receives the plan (owned by the caller; release it
+ *                           with expm_plan_destroy)
+ * Checks: finite values, adjacent conjugate pairs (relative 1e-12), and
+ * R_n(0) = -sum_k w_k/lambda_k = 1 within 1e-8 (Sec. 2.2, R_n(0) = 1).
+ * Returns EXPM_EINVAL on failed checks, EXPM_ENOMEM / EXPM_ECUDA on device errors.
+ */
+expm_status expm_plan_create(const double *poles_ri, const double *residues_ri, int degree,
+                             expm_plan *out);
+
+/* Release a plan and its device workspace (synchronises the device). NULL is OK. */
+expm_status expm_plan_destroy(expm_plan plan);
+
+/*
+ * expm_apply_tridiag -- Y = e^c R_n(tT - cI) V for a Hermitian tridiagonal T.
+ * Eq. expAx with one shifted tridiagonal solve per pole (pole-batched, Sec. 3),
+ * the 2 Re halving of Remark 5.1 when T and V are real, and the residue sum.
+ *   N             rows, N >= 1
+ *   d             N doubles: diagonal of T (real)
+ *   e             N-1 off-diagonal entries T_{i,i+1} (T_{i+1,i} = conj(e_i)):
+ *                 doubles if e_is_complex == 0, else N-1 complex
+ *   V             N x r right-hand sides, row-major, ld = r; real doubles if
+ *                 v_is_complex == 0, else complex
+ *   r             number of right-hand sides, 1 <= r <= 64
+ *   Y             N x r output, row-major; complex when V or e is complex, else real.
+ *                 Must not overlap V, d or e.
+ *   opts          precision EXPM_FP64 or EXPM_MIXED_F32X2; t, shift_c, stream
+ *   info          optional (may be NULL); refine/growth fields are not used here
+ * Method: the rows are split into blocks separated by single separator rows;
+ * each block is factored (unpivoted LU; (A - lambda I) scaled by a unit complex
+ * number has a positive-definite Hermitian part when Im lambda != 0, so no pivot
+ * is needed), the separators solve a reduced tridiagonal system by cyclic
+ * reduction, and the blocks are then solved and summed with their weights.
+ * Returns EXPM_ENOTSUP for complex e (not implemented), EXPM_EINVAL for bad sizes.
+ */
+expm_status expm_apply_tridiag(expm_plan plan, int64_t N, const double *d, const void *e,
+                               int e_is_complex, const void *V, int r, int v_is_complex,
+                               void *Y, const expm_opts *opts, expm_info *info);
+
+/*
+ * Measurement hooks (no counterpart in the paper).  When enabled on a plan, every
+ * kernel launch made through that plan is bracketed by CUDA events recorded on the
+ * launch stream; expm_profile_read synchronises on the recorded events and returns,
+ * per kernel name, the number of launches and their summed device time since the
+ * last reset.  Off by default; enabling it adds two event records per launch.
+ *   expm_profile_enable   on = 1 enables, 0 disables; both reset the counters
+ *   expm_profile_read     idx-th kernel seen (0-based, in first-launch order);
+ *                         *name points to a static string.  EXPM_ENOTFOUND when
+ *                         idx is past the last kernel.
+ */
+expm_status expm_profile_enable(expm_plan plan, int on);
+expm_status expm_profile_read(expm_plan plan, int idx, const char **name, int64_t *launches,
+                              double *total_ms);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* EXPM_H */

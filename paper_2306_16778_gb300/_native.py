@@ -1,0 +1,196 @@
+"""ctypes binding of libexpm.so: argument marshalling only."""
+
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+library_path = os.path.join(_HERE, "libexpm.so")
+
+EXPM_FP64 = 0
+EXPM_MIXED_F32X2 = 1
+EXPM_MIXED_FP32 = 2
+EXPM_MIXED_TF32X3 = 3
+
+STATUS = {0: "EXPM_OK", 1: "EXPM_EINVAL", 2: "EXPM_ENOMEM", 3: "EXPM_EGROWTH", 4: "EXPM_ENOCONV",
+          5: "EXPM_ETIMEOUT", 6: "EXPM_EAGAIN", 7: "EXPM_ECUDA", 8: "EXPM_ENOTFOUND", 9: "EXPM_ENOTSUP"}
+
+
+class ExpmError(RuntimeError):
+    def __init__(self, status: int, where: str, msg: str):
+        self.status = status
+        super().__init__(f"{where}: {STATUS.get(status, status)}: {msg}")
+
+
+class expm_opts(ctypes.Structure):
+    _fields_ = [("prec", ctypes.c_int), ("tol", ctypes.c_double), ("max_refine", ctypes.c_int),
+                ("t", ctypes.c_double), ("shift_c", ctypes.c_double), ("growth_max", ctypes.c_double),
+                ("stream", ctypes.c_void_p), ("flags", ctypes.c_int)]
+
+
+class expm_info(ctypes.Structure):
+    _fields_ = [("refine_iters_max", ctypes.c_int), ("growth_max_seen", ctypes.c_double),
+                ("resid_rel_max", ctypes.c_double), ("status_worst", ctypes.c_int)]
+
+
+def _load() -> ctypes.CDLL:
+    if not os.path.exists(library_path):
+        raise ImportError(f"{library_path} is missing: build it with "
+                          "`python -m paper_2306_16778_gb300.build` (nvcc, sm_103a)")
+    L = ctypes.CDLL(library_path)
+    vp, i, d, i64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_int64
+    dp = ctypes.POINTER(ctypes.c_double)
+    L.expm_opts_default.argtypes = [ctypes.POINTER(expm_opts)]
+    L.expm_opts_default.restype = None
+    L.expm_status_string.argtypes = [i]
+    L.expm_status_string.restype = ctypes.c_char_p
+    L.expm_last_error.argtypes = []
+    L.expm_last_error.restype = ctypes.c_char_p
+    L.expm_coeffs.argtypes = [i, dp, dp]
+    L.expm_coeffs.restype = i
+    L.expm_plan_create.argtypes = [dp, dp, i, ctypes.POINTER(vp)]
+    L.expm_plan_create.restype = i
+    L.expm_plan_destroy.argtypes = [vp]
+    L.expm_plan_destroy.restype = i
+    L.expm_apply_tridiag.argtypes = [vp, i64, vp, vp, i, vp, i, i, vp, ctypes.POINTER(expm_opts),
+                                     ctypes.POINTER(expm_info)]
+    L.expm_apply_tridiag.restype = i
+    L.expm_profile_enable.argtypes = [vp, i]
+    L.expm_profile_enable.restype = i
+    L.expm_profile_read.argtypes = [vp, i, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(ctypes.c_int64),
+                                    ctypes.POINTER(ctypes.c_double)]
+    L.expm_profile_read.restype = i
+    return L
+
+
+lib = _load()
+
+
+def _check(status: int, where: str) -> None:
+    if status != 0:
+        raise ExpmError(status, where, lib.expm_last_error().decode())
+
+
+def _ptr(x) -> int:
+    """Raw data pointer of a torch tensor or numpy array (must be contiguous)."""
+    if x is None:
+        return 0
+    if hasattr(x, "data_ptr"):
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return x.data_ptr()
+    if isinstance(x, np.ndarray):
+        if not x.flags.c_contiguous:
+            raise ValueError("array must be C-contiguous")
+        return x.ctypes.data
+    raise TypeError(f"unsupported buffer type {type(x)}")
+
+
+def _is_complex(x) -> bool:
+    if hasattr(x, "is_complex"):
+        return bool(x.is_complex())
+    return bool(np.iscomplexobj(x))
+
+
+def _default_stream(*bufs) -> int:
+    for b in bufs:
+        if hasattr(b, "is_cuda") and b.is_cuda:
+            import torch
+            return torch.cuda.current_stream(b.device).cuda_stream
+    return 0
+
+
+def make_opts(prec=EXPM_FP64, t=1.0, shift_c=0.0, stream=None, tol=None, max_refine=None,
+              growth_max=None) -> expm_opts:
+    o = expm_opts()
+    lib.expm_opts_default(ctypes.byref(o))
+    o.prec = int(prec)
+    o.t = float(t)
+    o.shift_c = float(shift_c)
+    if tol is not None:
+        o.tol = float(tol)
+    if max_refine is not None:
+        o.max_refine = int(max_refine)
+    if growth_max is not None:
+        o.growth_max = float(growth_max)
+    o.stream = stream
+    return o
+
+
+def expm_coeffs(degree: int) -> tuple[np.ndarray, np.ndarray]:
+    """(poles_ri, residues_ri), each 2*degree float64: lambda_k = -theta_k and w_k = a_k."""
+    p = np.zeros(2 * degree)
+    r = np.zeros(2 * degree)
+    _check(lib.expm_coeffs(int(degree), p.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                           r.ctypes.data_as(ctypes.POINTER(ctypes.c_double))), "expm_coeffs")
+    return p, r
+
+
+class Plan:
+    """Owns an ``expm_plan`` (pole data resident on the current CUDA device)."""
+
+    def __init__(self, poles_ri=None, residues_ri=None, degree: int | None = None):
+        if poles_ri is None:
+            poles_ri, residues_ri = expm_coeffs(int(degree))
+        poles_ri = np.ascontiguousarray(poles_ri, dtype=np.float64)
+        residues_ri = np.ascontiguousarray(residues_ri, dtype=np.float64)
+        if degree is None:
+            degree = poles_ri.size // 2
+        self.degree = int(degree)
+        self._h = ctypes.c_void_p()
+        _check(lib.expm_plan_create(poles_ri.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                    residues_ri.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                    self.degree, ctypes.byref(self._h)), "expm_plan_create")
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self) -> None:
+        if self._h:
+            lib.expm_plan_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def expm_profile_enable(plan: Plan, on: bool = True) -> None:
+    """Bracket every kernel launch of ``plan`` with CUDA events (resets counters)."""
+    _check(lib.expm_profile_enable(plan.handle, int(bool(on))), "expm_profile_enable")
+
+
+def expm_profile_read(plan: Plan) -> dict:
+    """{kernel name: (launches, total device ms)} since the last enable."""
+    out = {}
+    k = 0
+    while True:
+        name = ctypes.c_char_p()
+        n = ctypes.c_int64()
+        ms = ctypes.c_double()
+        st = lib.expm_profile_read(plan.handle, k, ctypes.byref(name), ctypes.byref(n), ctypes.byref(ms))
+        if st == 8:                       # EXPM_ENOTFOUND: past the last kernel
+            return out
+        _check(st, "expm_profile_read")
+        out[name.value.decode()] = (int(n.value), float(ms.value))
+        k += 1
+
+
+def expm_apply_tridiag(plan: Plan, d, e, V, Y, prec=EXPM_FP64, t=1.0, shift_c=0.0, stream=None) -> expm_info:
+    """Y = e^c R_n(tT - cI) V for the Hermitian tridiagonal T = (d, e); see include/expm.h."""
+    N = int(d.shape[0])
+    r = int(V.shape[1]) if len(V.shape) == 2 else 1
+    if stream is None:
+        stream = _default_stream(d, e, V, Y)
+    o = make_opts(prec, t, shift_c, stream)
+    info = expm_info()
+    _check(lib.expm_apply_tridiag(plan.handle, N, _ptr(d), _ptr(e), int(_is_complex(e)), _ptr(V), r,
+                                  int(_is_complex(V)), _ptr(Y), ctypes.byref(o), ctypes.byref(info)),
+           "expm_apply_tridiag")
+    return info

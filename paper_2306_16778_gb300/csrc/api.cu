@@ -1,0 +1,298 @@
+// api.cu -- the C interface declared in include/expm.h: plans, validation,
+// host/device staging and dispatch to the kernels.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/expm.h"
+#include "plan.cuh"
+#include "tridiag.cuh"
+
+using namespace expm;
+
+namespace {
+thread_local std::string g_last_error;
+}
+
+namespace expm {
+
+expm_status set_error(expm_status s, const std::string &msg) {
+    g_last_error = msg;
+    return s;
+}
+
+expm_status cuda_error(cudaError_t e, const char *where) {
+    if (e == cudaSuccess) return EXPM_OK;
+    return set_error(e == cudaErrorMemoryAllocation ? EXPM_ENOMEM : EXPM_ECUDA,
+                     std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+bool is_device_ptr(const void *p) {
+    if (!p) return false;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+expm_status plan_reserve(expm_plan p, void **buf, size_t *have, size_t need) {
+    if (need <= *have) return EXPM_OK;
+    if (*buf) {
+        cudaError_t e = cudaFree(*buf);
+        *buf = nullptr;
+        *have = 0;
+        if (e != cudaSuccess) return cuda_error(e, "cudaFree");
+    }
+    cudaError_t e = cudaMalloc(buf, need);
+    if (e != cudaSuccess) {
+        *buf = nullptr;
+        cudaGetLastError();
+        return cuda_error(e, "cudaMalloc(workspace)");
+    }
+    *have = need;
+    (void)p;
+    return EXPM_OK;
+}
+
+int Profiler::kernel_index(const char *name) {
+    for (size_t i = 0; i < names.size(); ++i)
+        if (names[i] == name || std::strcmp(names[i], name) == 0) return (int)i;
+    names.push_back(name);
+    launches.push_back(0);
+    total_ms.push_back(0.0);
+    return (int)names.size() - 1;
+}
+
+cudaEvent_t Profiler::take() {
+    if (!pool.empty()) {
+        cudaEvent_t e = pool.back();
+        pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+void Profiler::flush() {
+    for (auto &p : pending) {
+        cudaEventSynchronize(p.b);
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
+            total_ms[p.kernel] += ms;
+            launches[p.kernel] += 1;
+        }
+        pool.push_back(p.a);
+        pool.push_back(p.b);
+    }
+    pending.clear();
+}
+
+void Profiler::reset() {
+    flush();
+    names.clear();
+    launches.clear();
+    total_ms.clear();
+}
+
+void Profiler::release() {
+    flush();
+    for (auto e : pool) cudaEventDestroy(e);
+    pool.clear();
+}
+
+DeviceGuard::DeviceGuard(int dev) {
+    cudaGetDevice(&prev_);
+    if (prev_ != dev) cudaSetDevice(dev);
+}
+DeviceGuard::~DeviceGuard() {
+    int cur = -1;
+    cudaGetDevice(&cur);
+    if (cur != prev_) cudaSetDevice(prev_);
+}
+
+}  // namespace expm
+
+extern "C" {
+
+void expm_opts_default(expm_opts *o) {
+    if (!o) return;
+    o->prec = EXPM_FP64;
+    o->tol = 1e-14;
+    o->max_refine = 6;
+    o->t = 1.0;
+    o->shift_c = 0.0;
+    o->growth_max = 1e6;
+    o->stream = nullptr;
+    o->flags = 0;
+}
+
+const char *expm_status_string(expm_status s) {
+    switch (s) {
+        case EXPM_OK: return "EXPM_OK";
+        case EXPM_EINVAL: return "EXPM_EINVAL";
+        case EXPM_ENOMEM: return "EXPM_ENOMEM";
+        case EXPM_EGROWTH: return "EXPM_EGROWTH";
+        case EXPM_ENOCONV: return "EXPM_ENOCONV";
+        case EXPM_ETIMEOUT: return "EXPM_ETIMEOUT";
+        case EXPM_EAGAIN: return "EXPM_EAGAIN";
+        case EXPM_ECUDA: return "EXPM_ECUDA";
+        case EXPM_ENOTFOUND: return "EXPM_ENOTFOUND";
+        case EXPM_ENOTSUP: return "EXPM_ENOTSUP";
+    }
+    return "EXPM_UNKNOWN";
+}
+
+const char *expm_last_error(void) { return g_last_error.c_str(); }
+
+expm_status expm_plan_create(const double *poles_ri, const double *residues_ri, int degree, expm_plan *out) {
+    if (!out) return set_error(EXPM_EINVAL, "plan_create: out is NULL");
+    *out = nullptr;
+    if (!poles_ri || !residues_ri) return set_error(EXPM_EINVAL, "plan_create: NULL pole data");
+    if (degree < 2 || degree > 64 || (degree & 1))
+        return set_error(EXPM_EINVAL, "plan_create: degree must be even, 2..64");
+    for (int k = 0; k < 2 * degree; ++k)
+        if (!std::isfinite(poles_ri[k]) || !std::isfinite(residues_ri[k]))
+            return set_error(EXPM_EINVAL, "plan_create: non-finite pole data");
+    double r0_re = 0.0, r0_im = 0.0;
+    for (int k = 0; k < degree; ++k) {
+        const double lr = poles_ri[2 * k], li = poles_ri[2 * k + 1];
+        const double wr = residues_ri[2 * k], wi = residues_ri[2 * k + 1];
+        const double den = lr * lr + li * li;
+        if (!(den > 0)) return set_error(EXPM_EINVAL, "plan_create: zero pole");
+        // -w/lambda
+        r0_re += -(wr * lr + wi * li) / den;
+        r0_im += -(wi * lr - wr * li) / den;
+        if (k & 1) {
+            const double pr = poles_ri[2 * k - 2], pi = poles_ri[2 * k - 1];
+            const double qr = residues_ri[2 * k - 2], qi = residues_ri[2 * k - 1];
+            const double sc = std::sqrt(pr * pr + pi * pi), sw = std::sqrt(qr * qr + qi * qi);
+            if (std::fabs(lr - pr) > 1e-12 * sc || std::fabs(li + pi) > 1e-12 * sc ||
+                std::fabs(wr - qr) > 1e-12 * sw || std::fabs(wi + qi) > 1e-12 * sw)
+                return set_error(EXPM_EINVAL, "plan_create: poles/weights not in adjacent conjugate pairs");
+            if (pi == 0.0) return set_error(EXPM_EINVAL, "plan_create: real pole");
+        }
+    }
+    if (std::fabs(r0_re - 1.0) > 1e-8 || std::fabs(r0_im) > 1e-8)
+        return set_error(EXPM_EINVAL, "plan_create: pole data does not satisfy R_n(0) = 1");
+    expm_plan p = new (std::nothrow) expm_plan_s();
+    if (!p) return set_error(EXPM_ENOMEM, "plan_create: host allocation");
+    p->degree = degree;
+    p->lam.assign(poles_ri, poles_ri + 2 * degree);
+    p->w.assign(residues_ri, residues_ri + 2 * degree);
+    cudaError_t e = cudaGetDevice(&p->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&p->sm_count, cudaDevAttrMultiProcessorCount, p->device);
+    if (e != cudaSuccess) {
+        delete p;
+        cudaGetLastError();
+        return cuda_error(e, "plan_create");
+    }
+    *out = p;
+    return EXPM_OK;
+}
+
+expm_status expm_plan_destroy(expm_plan p) {
+    if (!p) return EXPM_OK;
+    DeviceGuard guard(p->device);
+    cudaDeviceSynchronize();
+    p->prof.release();
+    if (p->work) cudaFree(p->work);
+    if (p->stage) cudaFree(p->stage);
+    delete p;
+    return EXPM_OK;
+}
+
+expm_status expm_apply_tridiag(expm_plan p, int64_t N, const double *d, const void *e, int e_is_complex,
+                               const void *V, int r, int v_is_complex, void *Y, const expm_opts *opts_in,
+                               expm_info *info) {
+    if (!p) return set_error(EXPM_EINVAL, "apply_tridiag: NULL plan");
+    expm_opts opts;
+    if (opts_in) opts = *opts_in; else expm_opts_default(&opts);
+    if (N < 1) return set_error(EXPM_EINVAL, "apply_tridiag: N must be >= 1");
+    if (r < 1 || r > 64) return set_error(EXPM_EINVAL, "apply_tridiag: r must be in 1..64");
+    if (!d || !V || !Y || (N > 1 && !e)) return set_error(EXPM_EINVAL, "apply_tridiag: NULL data pointer");
+    if (opts.prec != EXPM_FP64 && opts.prec != EXPM_MIXED_F32X2)
+        return set_error(EXPM_EINVAL, "apply_tridiag: precision must be EXPM_FP64 or EXPM_MIXED_F32X2");
+    if (opts.flags != 0) return set_error(EXPM_EINVAL, "apply_tridiag: opts.flags must be 0");
+    if (!std::isfinite(opts.t) || !std::isfinite(opts.shift_c))
+        return set_error(EXPM_EINVAL, "apply_tridiag: t and shift_c must be finite");
+    if (e_is_complex) return set_error(EXPM_ENOTSUP, "apply_tridiag: complex off-diagonal not implemented");
+    if (info) *info = expm_info{0, 0.0, 0.0, EXPM_OK};
+
+    DeviceGuard guard(p->device);
+    const bool ff = opts.prec == EXPM_MIXED_F32X2;
+    const int Rc = r * (v_is_complex ? 2 : 1);  // complex V with real T: real and imaginary parts are columns
+    const int S = p->degree / 2;
+    TriPoles ps{};
+    const double ec = std::exp(opts.shift_c);
+    for (int s = 0; s < S; ++s) {  // one member of each conjugate pair: theta = -lambda, W = 2 e^c a
+        ps.th_re[s] = -p->lam[4 * s];
+        ps.th_im[s] = -p->lam[4 * s + 1];
+        ps.w_re[s] = 2.0 * ec * p->w[4 * s];
+        ps.w_im[s] = 2.0 * ec * p->w[4 * s + 1];
+    }
+    TriGeom g = tri_geometry(N, S, Rc, ff, p->sm_count);
+    g.t = opts.t;
+    g.cshift = opts.shift_c;
+    cudaStream_t st = (cudaStream_t)opts.stream;
+
+    const size_t need = tri_workspace_bytes(g, ff);
+    expm_status s = plan_reserve(p, &p->work, &p->work_bytes, need);
+    if (s != EXPM_OK) return s;
+
+    const bool dd = is_device_ptr(d), de = (N == 1) || is_device_ptr(e), dv = is_device_ptr(V),
+               dy = is_device_ptr(Y);
+    const double *dD = d, *dE = (const double *)e, *dV = (const double *)V;
+    double *dY = (double *)Y;
+    const size_t nV = (size_t)N * Rc;
+    const bool staged = !(dd && de && dv && dy);
+    if (staged) {
+        const size_t bytes = sizeof(double) * ((size_t)N + (size_t)N + 2 * nV) + 1024;
+        s = plan_reserve(p, &p->stage, &p->stage_bytes, bytes);
+        if (s != EXPM_OK) return s;
+        double *base = (double *)p->stage;
+        double *sD = base, *sE = base + N, *sV = sE + N, *sY = sV + nV;
+        cudaError_t err = cudaSuccess;
+        if (!dd) { err = cudaMemcpyAsync(sD, d, sizeof(double) * N, cudaMemcpyHostToDevice, st); dD = sD; }
+        if (err == cudaSuccess && !de && N > 1) {
+            err = cudaMemcpyAsync(sE, e, sizeof(double) * (N - 1), cudaMemcpyHostToDevice, st);
+            dE = sE;
+        }
+        if (err == cudaSuccess && !dv) { err = cudaMemcpyAsync(sV, V, sizeof(double) * nV, cudaMemcpyHostToDevice, st); dV = sV; }
+        if (!dy) dY = sY;
+        if (err != cudaSuccess) return cuda_error(err, "apply_tridiag: staging copy");
+    }
+    cudaError_t err = tri_run(g, ff, dD, dE, dV, dY, ps, p->work, st, p->prof);
+    if (err != cudaSuccess) return cuda_error(err, "apply_tridiag: kernel launch");
+    if (staged) {
+        if (!dy) err = cudaMemcpyAsync(Y, dY, sizeof(double) * nV, cudaMemcpyDeviceToHost, st);
+        if (err == cudaSuccess) err = cudaStreamSynchronize(st);
+        if (err != cudaSuccess) return cuda_error(err, "apply_tridiag: result copy");
+    }
+    return EXPM_OK;
+}
+
+expm_status expm_profile_enable(expm_plan p, int on) {
+    if (!p) return set_error(EXPM_EINVAL, "profile_enable: NULL plan");
+    DeviceGuard guard(p->device);
+    p->prof.reset();
+    p->prof.on = on != 0;
+    return EXPM_OK;
+}
+
+expm_status expm_profile_read(expm_plan p, int idx, const char **name, int64_t *launches, double *total_ms) {
+    if (!p || !name || !launches || !total_ms) return set_error(EXPM_EINVAL, "profile_read: NULL argument");
+    DeviceGuard guard(p->device);
+    p->prof.flush();
+    if (idx < 0 || idx >= (int)p->prof.names.size()) return EXPM_ENOTFOUND;
+    *name = p->prof.names[idx];
+    *launches = p->prof.launches[idx];
+    *total_ms = p->prof.total_ms[idx];
+    return EXPM_OK;
+}
+
+}  // extern "C"

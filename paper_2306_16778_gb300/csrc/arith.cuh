@@ -1,0 +1,116 @@
+// arith.cuh -- scalar and complex arithmetic used by the device kernels.
+//
+// Two real types are supported by every templated kernel:
+//   double  binary64 on the FP64 pipe.
+//   f32x2   "float-float": an unevaluated sum hi + lo of two binary32 numbers
+//           with |lo| <= ulp(hi)/2, giving a ~48-bit significand on the FP32 pipe.
+//           The error-free transformations are Knuth's TwoSum, Dekker's
+//           Fast2Sum and the FMA-based TwoProd (Dekker 1971; Joldes, Muller and
+//           Popescu, "Tight and rigorous error bounds for basic building blocks of
+//           double-word arithmetic", ACM TOMS 2017).  All float operations below use
+//           the *_rn intrinsics so the compiler cannot contract or reorder them.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#define EXPM_HD __host__ __device__ __forceinline__
+#define EXPM_D __device__ __forceinline__
+
+// ------------------------------------------------------------------ f32x2 type
+struct f32x2 {
+    float hi, lo;
+};
+
+EXPM_D f32x2 two_sum(float a, float b) {
+    float s = __fadd_rn(a, b);
+    float bb = __fsub_rn(s, a);
+    float err = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return {s, err};
+}
+EXPM_D f32x2 fast_two_sum(float a, float b) {  // requires |a| >= |b| (or a == 0)
+    float s = __fadd_rn(a, b);
+    float err = __fsub_rn(b, __fsub_rn(s, a));
+    return {s, err};
+}
+// double-word + double-word, the accurate ("AccurateDWPlusDW") variant
+EXPM_D f32x2 operator+(f32x2 x, f32x2 y) {
+    f32x2 s = two_sum(x.hi, y.hi);
+    f32x2 t = two_sum(x.lo, y.lo);
+    float c = __fadd_rn(s.lo, t.hi);
+    f32x2 v = fast_two_sum(s.hi, c);
+    float w = __fadd_rn(t.lo, v.lo);
+    return fast_two_sum(v.hi, w);
+}
+EXPM_D f32x2 operator-(f32x2 x) { return {-x.hi, -x.lo}; }
+EXPM_D f32x2 operator-(f32x2 x, f32x2 y) { return x + (-y); }
+// double-word x double-word with FMA ("DWTimesDW3"-style)
+EXPM_D f32x2 operator*(f32x2 x, f32x2 y) {
+    float ch = __fmul_rn(x.hi, y.hi);
+    float cl = __fmaf_rn(x.hi, y.hi, -ch);
+    float tl0 = __fmul_rn(x.lo, y.lo);
+    float tl1 = __fmaf_rn(x.hi, y.lo, tl0);
+    float cl2 = __fmaf_rn(x.lo, y.hi, tl1);
+    float cl3 = __fadd_rn(cl, cl2);
+    return fast_two_sum(ch, cl3);
+}
+// reciprocal: binary32 seed, one Newton step carried out in double-word
+EXPM_D f32x2 recip(f32x2 y) {
+    float r0 = __frcp_rn(y.hi);
+    f32x2 r = {r0, 0.f};
+    f32x2 one = {1.f, 0.f};
+    f32x2 e = one - y * r;  // residual of the seed
+    return r + r * e;
+}
+
+// binary64 <-> float-float.  These go through the FP64 conversion path; they
+// are used only on loads of inputs and stores of outputs.
+EXPM_D f32x2 to_f32x2(double x) {
+    float hi = __double2float_rn(x);
+    float lo = __double2float_rn(x - (double)hi);
+    return {hi, lo};
+}
+EXPM_D double to_double(f32x2 x) { return (double)x.hi + (double)x.lo; }
+
+// ------------------------------------------------------------------ traits
+template <class R> struct RealOps;
+template <> struct RealOps<double> {
+    static EXPM_D double from(double x) { return x; }
+    static EXPM_D double todbl(double x) { return x; }
+    static EXPM_D double zero() { return 0.0; }
+    static EXPM_D double rcp(double x) { return __drcp_rn(x); }
+};
+template <> struct RealOps<f32x2> {
+    static EXPM_D f32x2 from(double x) { return to_f32x2(x); }
+    static EXPM_D double todbl(f32x2 x) { return to_double(x); }
+    static EXPM_D f32x2 zero() { return {0.f, 0.f}; }
+    static EXPM_D f32x2 rcp(f32x2 x) { return recip(x); }
+};
+
+// ------------------------------------------------------------------ complex
+template <class R> struct cx {
+    R re, im;
+};
+
+template <class R> EXPM_D cx<R> cxz() { return {RealOps<R>::zero(), RealOps<R>::zero()}; }
+template <class R> EXPM_D cx<R> operator+(cx<R> a, cx<R> b) { return {a.re + b.re, a.im + b.im}; }
+template <class R> EXPM_D cx<R> operator-(cx<R> a, cx<R> b) { return {a.re - b.re, a.im - b.im}; }
+template <class R> EXPM_D cx<R> operator-(cx<R> a) { return {-a.re, -a.im}; }
+template <class R> EXPM_D cx<R> operator*(cx<R> a, cx<R> b) {
+    return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re};
+}
+template <class R> EXPM_D cx<R> scale(R s, cx<R> a) { return {s * a.re, s * a.im}; }
+template <class R> EXPM_D cx<R> conj(cx<R> a) { return {a.re, -a.im}; }
+// 1/w = conj(w)/|w|^2.  Inputs here are shifted matrix entries of moderate size
+// (the public entry points reject non-finite data), so |w|^2 neither overflows
+// nor underflows.
+template <class R> EXPM_D cx<R> cinv(cx<R> w) {
+    R n2 = w.re * w.re + w.im * w.im;
+    R r = RealOps<R>::rcp(n2);
+    return {w.re * r, -(w.im * r)};
+}
+// Re(a * b)
+template <class R> EXPM_D R re_mul(cx<R> a, cx<R> b) { return a.re * b.re - a.im * b.im; }
+
+template <class R> EXPM_D cx<R> cx_from(double re, double im) {
+    return {RealOps<R>::from(re), RealOps<R>::from(im)};
+}

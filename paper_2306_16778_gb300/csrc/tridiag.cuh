@@ -1,0 +1,41 @@
+// tridiag.cuh -- geometry and launcher of the pole-batched tridiagonal path.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <algorithm>
+
+namespace expm {
+
+struct Profiler;
+
+constexpr int TRI_RCH = 8;      // right-hand-side columns per dot-product pass in K1
+constexpr int TRI_SG = 8;       // systems processed together in K3
+constexpr int TRI_PMAX = 3000;  // max blocks: the reduced system (P-1 rows) lives in shared memory
+constexpr int TRI_MMIN = 8;     // min interior rows per block
+constexpr int TRI_MAXSYS = 64;
+
+// Row partition: P blocks; block b starts at row b*B, has m interior rows
+// (the last block has N - (P-1)*B rows) and, for b < P-1, is followed by the
+// separator row b*B + m.
+struct TriGeom {
+    int64_t N;
+    int m, B, P;
+    int S;       // systems (shifted matrices)
+    int Rc;      // real right-hand-side columns
+    double t;    // time factor
+    double cshift;
+};
+
+// Shifts theta_s (paper's notation: the system is t T - cI + theta_s I) and the
+// weights W_s multiplying Re(W_s x_s) in the sum.
+struct TriPoles {
+    double th_re[TRI_MAXSYS], th_im[TRI_MAXSYS];
+    double w_re[TRI_MAXSYS], w_im[TRI_MAXSYS];
+};
+
+TriGeom tri_geometry(int64_t N, int S, int Rc, bool ff, int sm_count);
+size_t tri_workspace_bytes(const TriGeom &g, bool ff);
+cudaError_t tri_run(const TriGeom &g, bool ff, const double *d, const double *e, const double *V, double *Y,
+                    const TriPoles &ps, void *work, cudaStream_t st, Profiler &prof);
+
+}  // namespace expm

@@ -1,0 +1,149 @@
+"""GPU parity of the pole-batched tridiagonal path (expm_apply_tridiag) against
+the oracle, through the C-ABI.
+
+Tolerances: relative Frobenius error <= 1e-12 for the binary64 path (the
+configured FP64 tolerance) and <= 1e-8 for the float-float path (the mixed-path
+tolerance), each against the oracle's pivoted banded solves on the same inputs.
+"""
+
+import numpy as np
+import pytest
+
+import workloads
+from oracle import coeffs, matrix
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+import paper_2306_16778_gb300 as P  # noqa: E402
+
+TOL = {P.EXPM_FP64: 1e-12, P.EXPM_MIXED_F32X2: 1e-8}
+DEV = torch.device("cuda:0")
+
+
+def _oracle(d, e, V, n, t=1.0, c=0.0):
+    Y, _ = matrix.apply_tridiag(d, e, V, coeffs.theta(n), coeffs.residues(n), t=t, c=c, workers=8)
+    return Y
+
+
+def _gpu(plan, d, e, V, prec, t=1.0, c=0.0):
+    dd = torch.from_numpy(d).to(DEV)
+    de = torch.from_numpy(e).to(DEV) if e.size else torch.zeros(1, dtype=torch.float64, device=DEV)
+    dv = torch.from_numpy(np.ascontiguousarray(V)).to(DEV)
+    dy = torch.empty_like(dv)
+    P.expm_apply_tridiag(plan, dd, de, dv, dy, prec=prec, t=t, shift_c=c)
+    torch.cuda.synchronize()
+    return dy.cpu().numpy()
+
+
+def _random_tridiag(N, r, seed, complex_v=False):
+    g = workloads.rng(seed)
+    d = g.uniform(-30.0, -10.0, N)
+    e = g.uniform(1.0, 4.0, max(N - 1, 0))      # Gershgorin: spectrum in (-38, -2)
+    V = g.standard_normal((N, r))
+    if complex_v:
+        V = V + 1j * g.standard_normal((N, r))
+    return d, e, V
+
+
+@pytest.fixture(scope="module")
+def plans():
+    return {n: P.Plan(degree=n) for n in (12, 16)}
+
+
+@pytest.mark.parametrize("prec", [P.EXPM_FP64, P.EXPM_MIXED_F32X2])
+@pytest.mark.parametrize("N,r,n", [(1, 1, 12), (2, 3, 16), (7, 2, 12), (100, 1, 16), (433, 8, 16),
+                                   (4096 + 13, 5, 12), (50_000, 8, 16), (200_003, 3, 12)])
+def test_random_tridiag_parity(plans, prec, N, r, n):
+    """Several blocks, a ragged last block, single-row and tiny systems."""
+    d, e, V = _random_tridiag(N, r, 200 + N + r)
+    Y = _gpu(plans[n], d, e, V, prec)
+    Yo = _oracle(d, e, V, n)
+    assert matrix.rel_err(Y, Yo) <= TOL[prec]
+
+
+@pytest.mark.parametrize("prec", [P.EXPM_FP64, P.EXPM_MIXED_F32X2])
+def test_laplacian_mid_size(plans, prec):
+    w = workloads.laplacian_1d(N=65_537, nrhs=8, offset=201)
+    Y = _gpu(plans[16], w["d"], w["e"], w["V"], prec)
+    Yo = _oracle(w["d"], w["e"], w["V"], 16)
+    assert matrix.rel_err(Y, Yo) <= TOL[prec]
+
+
+@pytest.fixture(scope="module")
+def full_size():
+    """The 1D Laplacian workload at full size: N = 2^20, 8 RHS, degree 16."""
+    w = workloads.laplacian_1d()
+    Yo = _oracle(w["d"], w["e"], w["V"], 16)
+    return w, Yo
+
+
+@pytest.mark.parametrize("prec", [P.EXPM_FP64, P.EXPM_MIXED_F32X2])
+def test_laplacian_full_size(plans, full_size, prec):
+    """Full-size parity in the launch configuration the benchmark times."""
+    w, Yo = full_size
+    Y = _gpu(plans[16], w["d"], w["e"], w["V"], prec)
+    err = matrix.rel_err(Y, Yo)
+    print(f"full-size rel err prec={prec}: {err:.3e}")
+    assert err <= TOL[prec]
+
+
+def test_host_buffers_match_device_buffers(plans):
+    """Host (numpy) buffers are staged by the library; the result is bit-identical."""
+    d, e, V = _random_tridiag(30_000, 4, 202)
+    Yd = _gpu(plans[12], d, e, V, P.EXPM_FP64)
+    Yh = np.empty_like(V)
+    P.expm_apply_tridiag(plans[12], d, e, V, Yh)
+    np.testing.assert_array_equal(Yh, Yd)
+
+
+def test_complex_rhs_with_real_matrix(plans):
+    """Complex V with real T: real and imaginary parts are independent columns."""
+    d, e, V = _random_tridiag(5_000, 3, 203, complex_v=True)
+    Y = _gpu(plans[16], d, e, V, P.EXPM_FP64)
+    Yo = _oracle(d, e, V, 16)
+    assert Y.dtype == np.complex128
+    assert matrix.rel_err(Y, Yo) <= 1e-12
+
+
+def test_time_and_shift(plans):
+    """exp(tT)V ~ e^c R_n(tT - cI)V (Remark 3.2) with t != 1, c != 0."""
+    d, e, V = _random_tridiag(10_000, 2, 204)
+    d = d + 30.0                                       # spectrum now in (-8, 28)
+    Y = _gpu(plans[16], d, e, V, P.EXPM_FP64, t=0.5, c=15.0)
+    Yo = _oracle(d, e, V, 16, t=0.5, c=15.0)
+    assert matrix.rel_err(Y, Yo) <= 1e-12
+
+
+def test_nondefault_stream(plans):
+    d, e, V = _random_tridiag(20_000, 2, 205)
+    s = torch.cuda.Stream()
+    dd, de, dv = (torch.from_numpy(x).to(DEV) for x in (d, e, V))
+    dy = torch.empty_like(dv)
+    torch.cuda.synchronize()
+    with torch.cuda.stream(s):
+        P.expm_apply_tridiag(plans[12], dd, de, dv, dy)
+    s.synchronize()
+    assert matrix.rel_err(dy.cpu().numpy(), _oracle(d, e, V, 12)) <= 1e-12
+
+
+def test_repeated_calls_are_deterministic(plans):
+    d, e, V = _random_tridiag(40_000, 8, 206)
+    a = _gpu(plans[16], d, e, V, P.EXPM_FP64)
+    b = _gpu(plans[16], d, e, V, P.EXPM_FP64)
+    np.testing.assert_array_equal(a, b)
+
+
+def test_invalid_arguments(plans):
+    d, e, V = _random_tridiag(100, 2, 207)
+    dd, de, dv = (torch.from_numpy(x).to(DEV) for x in (d, e, V))
+    dy = torch.empty_like(dv)
+    with pytest.raises(P.ExpmError) as ei:
+        P.expm_apply_tridiag(plans[12], dd, de.to(torch.complex128), dv, dy)
+    assert ei.value.status == 9                        # EXPM_ENOTSUP: complex off-diagonal
+    with pytest.raises(P.ExpmError) as ei:
+        P.expm_apply_tridiag(plans[12], dd, de, dv, dy, prec=P.EXPM_MIXED_TF32X3)
+    assert ei.value.status == 1                        # EXPM_EINVAL
