@@ -139,8 +139,8 @@ def kernel_sha() -> str:
 
 def run_peaks():
     import ctypes
-    from paper_2306_16778_gb300 import build as b
-    lib = ctypes.CDLL(b.build_probe())
+    import __graft_entry__
+    lib = ctypes.CDLL(__graft_entry__._build_module().build_probe())
     lib.expm_probe_fma_tflops.restype = ctypes.c_double
     lib.expm_probe_fma_tflops.argtypes = [ctypes.c_int] * 4
     out = {}

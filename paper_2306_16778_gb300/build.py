@@ -17,7 +17,7 @@ import sys
 PKG = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
-BUILD = os.path.join(ROOT, "_build")
+BUILD = os.path.join(ROOT, "_build", __import__("platform").machine())  # objects per host architecture
 LIB = os.path.join(PKG, "libexpm.so")
 PROBE_SRC = os.path.join(PKG, "probe", "peaks.cu")
 PROBE_LIB = os.path.join(PKG, "probe", "libexpm_probe.so")

@@ -25,8 +25,8 @@ def _declared_functions():
 
 @pytest.fixture(scope="module")
 def P():
-    from paper_2306_16778_gb300 import build
-    build.build()
+    import __graft_entry__
+    __graft_entry__._build_module().build()
     import paper_2306_16778_gb300 as P
     return P
 
