@@ -161,6 +161,37 @@ expm_status expm_apply_tridiag(expm_plan plan, int64_t N, const double *d, const
                                void *Y, const expm_opts *opts, expm_info *info);
 
 /*
+ * expm_apply_dense -- Y = e^c R_n(tA - cI) V for a dense Hermitian A.
+ * Eq. expAx with one shifted dense solve per pole: unpivoted blocked LU of
+ * tA - cI + theta I per conjugate pole pair (Sec. 3), triangular solves, and the
+ * residue-weighted sum.  Real symmetric A with real V solves one pole of each pair
+ * and takes 2 Re(...) (Remark 5.1); complex Hermitian A solves both poles of a pair
+ * with one factorization, since tA - cI + conj(theta) I = (tA - cI + theta I)^H.
+ *   n             order of A, n >= 1
+ *   A             n x n, row-major, leading dimension lda >= n (elements); real
+ *                 doubles if a_is_complex == 0, else complex.  Only Hermitian A is
+ *                 supported; the full matrix is read (no symmetry is exploited).
+ *   V             n x k right-hand sides, leading dimension ldv >= k; real if
+ *                 v_is_complex == 0, else complex
+ *   k             1 <= k <= 4096
+ *   Y             n x k output, leading dimension ldy >= k; complex when A or V is
+ *                 complex, else real.  Must not overlap A or V.
+ *   opts          prec: EXPM_FP64 (binary64 throughout) or EXPM_MIXED_FP32 /
+ *                 EXPM_MIXED_F32X2 (binary32 factorization, binary64 iterative
+ *                 refinement with binary64 residuals until
+ *                 ||R_k||_F <= tol (||tA||_F + |theta_k - c|) ||X_k||_F, at most
+ *                 max_refine sweeps); growth_max bounds max|U| / max|tA - cI + theta I|.
+ *   info          optional: refinement sweeps, worst relative residual, worst growth.
+ * The call synchronises opts->stream before returning (it reads back the growth
+ * factors and, in mixed precision, the residual norms).  Returns EXPM_EGROWTH if a
+ * growth factor exceeds growth_max, EXPM_ENOCONV if refinement did not reach tol
+ * (Y is written in both cases), EXPM_EINVAL for bad sizes.
+ */
+expm_status expm_apply_dense(expm_plan plan, int n, const void *A, int lda, int a_is_complex, const void *V,
+                             int ldv, int k, int v_is_complex, void *Y, int ldy, const expm_opts *opts,
+                             expm_info *info);
+
+/*
  * Measurement hooks (no counterpart in the paper).  When enabled on a plan, every
  * kernel launch made through that plan is bracketed by CUDA events recorded on the
  * launch stream; expm_profile_read synchronises on the recorded events and returns,

@@ -18,6 +18,7 @@ from ._native import (  # noqa: F401
     EXPM_MIXED_TF32X3,
     ExpmError,
     Plan,
+    expm_apply_dense,
     expm_apply_tridiag,
     expm_profile_enable,
     expm_profile_read,

@@ -58,6 +58,9 @@ def _load() -> ctypes.CDLL:
     L.expm_apply_tridiag.argtypes = [vp, i64, vp, vp, i, vp, i, i, vp, ctypes.POINTER(expm_opts),
                                      ctypes.POINTER(expm_info)]
     L.expm_apply_tridiag.restype = i
+    L.expm_apply_dense.argtypes = [vp, i, vp, i, i, vp, i, i, i, vp, i, ctypes.POINTER(expm_opts),
+                                   ctypes.POINTER(expm_info)]
+    L.expm_apply_dense.restype = i
     L.expm_profile_enable.argtypes = [vp, i]
     L.expm_profile_enable.restype = i
     L.expm_profile_read.argtypes = [vp, i, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(ctypes.c_int64),
@@ -180,6 +183,25 @@ def expm_profile_read(plan: Plan) -> dict:
         _check(st, "expm_profile_read")
         out[name.value.decode()] = (int(n.value), float(ms.value))
         k += 1
+
+
+def expm_apply_dense(plan: Plan, A, V, Y, prec=EXPM_FP64, t=1.0, shift_c=0.0, stream=None, tol=None,
+                     max_refine=None, growth_max=None, check=True) -> expm_info:
+    """Y = e^c R_n(tA - cI) V for a dense Hermitian A (n x n) and V (n x k); see include/expm.h.
+
+    With ``check=False`` EXPM_EGROWTH / EXPM_ENOCONV are returned in ``info.status_worst``
+    instead of raised."""
+    n = int(A.shape[0])
+    k = int(V.shape[1]) if len(V.shape) == 2 else 1
+    if stream is None:
+        stream = _default_stream(A, V, Y)
+    o = make_opts(prec, t, shift_c, stream, tol, max_refine, growth_max)
+    info = expm_info()
+    st = lib.expm_apply_dense(plan.handle, n, _ptr(A), n, int(_is_complex(A)), _ptr(V), k, k, int(_is_complex(V)),
+                              _ptr(Y), k, ctypes.byref(o), ctypes.byref(info))
+    if check or st not in (3, 4):
+        _check(st, "expm_apply_dense")
+    return info
 
 
 def expm_apply_tridiag(plan: Plan, d, e, V, Y, prec=EXPM_FP64, t=1.0, shift_c=0.0, stream=None) -> expm_info:

@@ -9,6 +9,7 @@
 #include "../../include/expm.h"
 #include "plan.cuh"
 #include "tridiag.cuh"
+#include "dense.cuh"
 
 using namespace expm;
 
@@ -273,6 +274,96 @@ expm_status expm_apply_tridiag(expm_plan p, int64_t N, const double *d, const vo
         if (err == cudaSuccess) err = cudaStreamSynchronize(st);
         if (err != cudaSuccess) return cuda_error(err, "apply_tridiag: result copy");
     }
+    return EXPM_OK;
+}
+
+expm_status expm_apply_dense(expm_plan p, int n, const void *A, int lda, int a_is_complex, const void *V, int ldv,
+                             int k, int v_is_complex, void *Y, int ldy, const expm_opts *opts_in, expm_info *info) {
+    if (!p) return set_error(EXPM_EINVAL, "apply_dense: NULL plan");
+    expm_opts opts;
+    if (opts_in) opts = *opts_in; else expm_opts_default(&opts);
+    if (n < 1 || k < 1 || k > 4096) return set_error(EXPM_EINVAL, "apply_dense: need n >= 1 and 1 <= k <= 4096");
+    if (lda < n || ldv < k || ldy < k) return set_error(EXPM_EINVAL, "apply_dense: leading dimension too small");
+    if (!A || !V || !Y) return set_error(EXPM_EINVAL, "apply_dense: NULL data pointer");
+    if (opts.prec != EXPM_FP64 && opts.prec != EXPM_MIXED_FP32 && opts.prec != EXPM_MIXED_F32X2)
+        return set_error(EXPM_EINVAL, "apply_dense: precision must be EXPM_FP64, EXPM_MIXED_FP32 or EXPM_MIXED_F32X2");
+    if (opts.flags != 0) return set_error(EXPM_EINVAL, "apply_dense: opts.flags must be 0");
+    if (!std::isfinite(opts.t) || !std::isfinite(opts.shift_c) || !(opts.tol > 0) || opts.max_refine < 0)
+        return set_error(EXPM_EINVAL, "apply_dense: bad t, shift_c, tol or max_refine");
+    if (info) *info = expm_info{0, 0.0, 0.0, EXPM_OK};
+    DeviceGuard guard(p->device);
+    cudaStream_t st = (cudaStream_t)opts.stream;
+    const int S = p->degree / 2;
+    const bool complex_a = a_is_complex != 0;
+    DenseGeom g{};
+    g.n = n;
+    g.complex_a = complex_a;
+    g.npairs = S;
+    g.nsys = complex_a ? 2 * S : S;
+    // real A with complex V: real and imaginary parts are separate real columns
+    const bool split_v = !complex_a && v_is_complex;
+    g.kc = split_v ? 2 * k : k;
+    g.mixed = opts.prec != EXPM_FP64;
+    g.t = opts.t;
+    g.tol = opts.tol;
+    g.max_refine = opts.max_refine;
+    DenseSystems sys{};
+    sys.cshift = opts.shift_c;
+    const double ec = std::exp(opts.shift_c);
+    for (int s = 0; s < S; ++s) {
+        const double tr = -p->lam[4 * s], ti = -p->lam[4 * s + 1];  // theta = -lambda (Im > 0 member first)
+        const double ar = p->w[4 * s], ai = p->w[4 * s + 1];
+        if (complex_a) {
+            sys.th_re[2 * s] = tr; sys.th_im[2 * s] = ti; sys.w_re[2 * s] = ec * ar; sys.w_im[2 * s] = ec * ai;
+            sys.th_re[2 * s + 1] = tr; sys.th_im[2 * s + 1] = -ti;
+            sys.w_re[2 * s + 1] = ec * ar; sys.w_im[2 * s + 1] = -ec * ai;
+        } else {
+            sys.th_re[s] = tr; sys.th_im[s] = ti; sys.w_re[s] = 2 * ec * ar; sys.w_im[s] = 2 * ec * ai;
+        }
+    }
+    const bool da = is_device_ptr(A), dv = is_device_ptr(V), dy = is_device_ptr(Y);
+    const size_t ea = complex_a ? 2 : 1, ev = v_is_complex ? 2 : 1, ey = (complex_a || v_is_complex) ? 2 : 1;
+    const size_t nA = (size_t)n * lda * ea, nV = (size_t)n * ldv * ev, nY = (size_t)n * ldy * ey;
+    const double *dA = (const double *)A, *dV = (const double *)V;
+    double *dY = (double *)Y;
+    const bool staged = !(da && dv && dy);
+    if (staged) {
+        expm_status s = plan_reserve(p, &p->stage, &p->stage_bytes, sizeof(double) * (nA + nV + nY) + 1024);
+        if (s != EXPM_OK) return s;
+        double *base = (double *)p->stage;
+        cudaError_t err = cudaSuccess;
+        if (!da) { err = cudaMemcpyAsync(base, A, sizeof(double) * nA, cudaMemcpyHostToDevice, st); dA = base; }
+        if (err == cudaSuccess && !dv) {
+            err = cudaMemcpyAsync(base + nA, V, sizeof(double) * nV, cudaMemcpyHostToDevice, st);
+            dV = base + nA;
+        }
+        if (!dy) dY = base + nA + nV;
+        if (err != cudaSuccess) return cuda_error(err, "apply_dense: staging copy");
+    }
+    expm_status s = plan_reserve(p, &p->work, &p->work_bytes, dense_workspace_bytes(g));
+    if (s != EXPM_OK) return s;
+    DenseResult res{};
+    const int64_t ldv_eff = split_v ? 2 * (int64_t)ldv : ldv;   // in units of the loaded element
+    const int64_t ldy_eff = split_v ? 2 * (int64_t)ldy : ldy;
+    cudaError_t err = dense_run(g, dA, lda, dV, ldv_eff, (complex_a && v_is_complex) ? 1 : 0, dY, ldy_eff, sys, p->work,
+                                st, p->prof, &res);
+    if (err != cudaSuccess) return cuda_error(err, "apply_dense: kernels");
+    if (staged && !dy) {
+        err = cudaMemcpyAsync(Y, dY, sizeof(double) * nY, cudaMemcpyDeviceToHost, st);
+        if (err == cudaSuccess) err = cudaStreamSynchronize(st);
+        if (err != cudaSuccess) return cuda_error(err, "apply_dense: result copy");
+    }
+    expm_status out = EXPM_OK;
+    if (res.growth_max > opts.growth_max) out = EXPM_EGROWTH;
+    else if (g.mixed && !(res.resid_rel_max <= opts.tol)) out = EXPM_ENOCONV;
+    if (info) {
+        info->refine_iters_max = res.iters;
+        info->growth_max_seen = res.growth_max;
+        info->resid_rel_max = res.resid_rel_max;
+        info->status_worst = out;
+    }
+    if (out == EXPM_EGROWTH) return set_error(out, "apply_dense: LU growth exceeds opts.growth_max");
+    if (out == EXPM_ENOCONV) return set_error(out, "apply_dense: refinement did not reach opts.tol");
     return EXPM_OK;
 }
 

@@ -79,6 +79,12 @@ template <> struct RealOps<double> {
     static EXPM_D double zero() { return 0.0; }
     static EXPM_D double rcp(double x) { return __drcp_rn(x); }
 };
+template <> struct RealOps<float> {
+    static EXPM_D float from(double x) { return (float)x; }
+    static EXPM_D double todbl(float x) { return (double)x; }
+    static EXPM_D float zero() { return 0.f; }
+    static EXPM_D float rcp(float x) { return __frcp_rn(x); }
+};
 template <> struct RealOps<f32x2> {
     static EXPM_D f32x2 from(double x) { return to_f32x2(x); }
     static EXPM_D double todbl(f32x2 x) { return to_double(x); }
