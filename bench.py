@@ -67,6 +67,10 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--peaks", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--rows", type=int, default=N_ROWS,
+                    help="rows of the Laplacian (smaller cases are for profiling only)")
+    ap.add_argument("--fp64-only", action="store_true",
+                    help="time only the binary64 path (profiling runs)")
     return ap.parse_args()
 
 
@@ -176,7 +180,8 @@ def run_ours(args):
             import torch.distributed as dist
             dist.barrier()
 
-    w = workloads.laplacian_1d(N=N_ROWS, nrhs=NRHS, offset=1 + rank)
+    rows = args.rows
+    w = workloads.laplacian_1d(N=rows, nrhs=NRHS, offset=1 + rank)
     plan = P.Plan(degree=DEGREE)
     d, e, V = (torch.from_numpy(x).to(dev) for x in (w["d"], w["e"], w["V"]))
     Y = torch.empty_like(V)
@@ -210,6 +215,12 @@ def run_ours(args):
     ms64, prof64 = timed_loop(P.EXPM_FP64, K)
     clocks = sampler.stop() if sampler else None
     Y64 = Y.cpu().numpy() if rank == 0 else None
+    if args.fp64_only:
+        if rank == 0:
+            print(json.dumps({"fp64_only": True, "rows": rows, "ms_per_step": sum(ms64) / K,
+                              "kernels_ms": {k: v[1] / v[0] for k, v in prof64.items()}}), flush=True)
+        plan.close()
+        return
     msff, profff = timed_loop(P.EXPM_MIXED_F32X2, K)
     Yff = Y.cpu().numpy() if rank == 0 else None
 
@@ -245,7 +256,7 @@ def run_ours(args):
     top = max(prof64.items(), key=lambda kv: kv[1][1])
     kname, (klaunch, kms) = top
     kavg_s = kms / klaunch / 1e3
-    flops = FLOPS_K3 * S * NRHS * N_ROWS
+    flops = FLOPS_K3 * S * NRHS * rows
     achieved = flops / kavg_s / 1e12
     peak = SMS * FP64_FLOP_PER_CLK_SM * SM_MAX_MHZ * 1e6 / 1e12
     traffic = TRAFFIC_K3 if (TRAFFIC_K3 is not None and TRAFFIC_SRC_SHA == kernel_sha()) else None

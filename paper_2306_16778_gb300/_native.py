@@ -39,7 +39,7 @@ class expm_info(ctypes.Structure):
 def _load() -> ctypes.CDLL:
     if not os.path.exists(library_path):
         raise ImportError(f"{library_path} is missing: build it with "
-                          "`python -m paper_2306_16778_gb300.build` (nvcc, sm_103a)")
+                          "`python paper_2306_16778_gb300/build.py` (nvcc, sm_103a)")
     L = ctypes.CDLL(library_path)
     vp, i, d, i64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_int64
     dp = ctypes.POINTER(ctypes.c_double)

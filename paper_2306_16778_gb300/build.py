@@ -1,6 +1,6 @@
 """Build the native library ``libexpm.so`` in-tree with nvcc for sm_103a.
 
-Usage: ``python -m paper_2306_16778_gb300.build`` (or ``build()`` from Python).
+Usage: ``python paper_2306_16778_gb300/build.py`` (or ``build()`` from Python).
 Each translation unit is compiled in parallel into ``_build/`` and then linked
 as a shared library next to this file.  Only one ``-gencode`` is emitted
 (compute_103a -> sm_103a); no CPU fallback is built.
