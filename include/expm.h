@@ -161,6 +161,36 @@ expm_status expm_apply_tridiag(expm_plan plan, int64_t N, const double *d, const
                                void *Y, const expm_opts *opts, expm_info *info);
 
 /*
+ * expm_apply_tridiag_noalloc -- expm_apply_tridiag for callers that must not allocate.
+ * The paper has no counterpart: this is a deployment variant of the same computation.
+ * Who needs it: callers that cannot let the library call cudaMalloc/cudaFree, for
+ * example a serving process whose device memory is reserved at start-up by another
+ * framework's caching allocator, or a latency-critical loop in which an allocation
+ * (which may synchronise the device and take unbounded time) is not acceptable.
+ * It runs the same kernels as expm_apply_tridiag, with their scratch in a fixed array
+ * of EXPM_NOALLOC_SCRATCH_BYTES bytes that the library holds in device memory on
+ * every GPU that loads it, until the process exits.  The call allocates nothing and
+ * enqueues asynchronously on opts->stream.
+ *   Arguments and result: as expm_apply_tridiag, except that d, e, V and Y must be
+ *   device memory (host buffers would need staging memory: EXPM_EINVAL).
+ *   Size limit: a problem whose scratch exceeds EXPM_NOALLOC_SCRATCH_BYTES is
+ *   rejected with EXPM_EINVAL and a message giving the bytes needed (about
+ *   N * (256 + 128 r) bytes for degree 16 and r >= 2 real right-hand sides, so N up
+ *   to about 26,000 for r = 8).
+ *   Set-up: the first call on each device looks up the array's device address
+ *   (cudaGetSymbolAddress) with that device current; make that first call before any
+ *   stream capture.
+ *   Sharing: all calls on a device share the one array and it keeps whatever the last
+ *   call left in it (every kernel writes the scratch it later reads; nothing needs to
+ *   start at zero).  Calls whose work overlaps on the GPU -- different streams, or
+ *   different host threads -- race on the array: serialise them.
+ */
+#define EXPM_NOALLOC_SCRATCH_BYTES (32u << 20)
+expm_status expm_apply_tridiag_noalloc(expm_plan plan, int64_t N, const double *d, const void *e,
+                                       int e_is_complex, const void *V, int r, int v_is_complex, void *Y,
+                                       const expm_opts *opts, expm_info *info);
+
+/*
  * expm_apply_dense -- Y = e^c R_n(tA - cI) V for a dense Hermitian A.
  * Eq. expAx with one shifted dense solve per pole: unpivoted blocked LU of
  * tA - cI + theta I per conjugate pole pair (Sec. 3), triangular solves, and the

@@ -20,6 +20,7 @@ from ._native import (  # noqa: F401
     Plan,
     expm_apply_dense,
     expm_apply_tridiag,
+    expm_apply_tridiag_noalloc,
     expm_profile_enable,
     expm_profile_read,
     expm_coeffs,

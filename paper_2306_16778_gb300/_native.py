@@ -61,6 +61,9 @@ def _load() -> ctypes.CDLL:
     L.expm_apply_dense.argtypes = [vp, i, vp, i, i, vp, i, i, i, vp, i, ctypes.POINTER(expm_opts),
                                    ctypes.POINTER(expm_info)]
     L.expm_apply_dense.restype = i
+    L.expm_apply_tridiag_noalloc.argtypes = [vp, i64, vp, vp, i, vp, i, i, vp, ctypes.POINTER(expm_opts),
+                                             ctypes.POINTER(expm_info)]
+    L.expm_apply_tridiag_noalloc.restype = i
     L.expm_profile_enable.argtypes = [vp, i]
     L.expm_profile_enable.restype = i
     L.expm_profile_read.argtypes = [vp, i, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(ctypes.c_int64),
@@ -162,6 +165,22 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+
+def expm_apply_tridiag_noalloc(plan: Plan, d, e, V, Y, prec=EXPM_FP64, t=1.0, shift_c=0.0,
+                               stream=None) -> expm_info:
+    """As ``expm_apply_tridiag`` but with no device allocation: scratch comes from a
+    fixed array inside the library (see include/expm.h).  Device buffers only."""
+    N = int(d.shape[0])
+    r = int(V.shape[1]) if len(V.shape) == 2 else 1
+    if stream is None:
+        stream = _default_stream(d, e, V, Y)
+    o = make_opts(prec, t, shift_c, stream)
+    info = expm_info()
+    _check(lib.expm_apply_tridiag_noalloc(plan.handle, N, _ptr(d), _ptr(e), int(_is_complex(e)), _ptr(V), r,
+                                          int(_is_complex(V)), _ptr(Y), ctypes.byref(o), ctypes.byref(info)),
+           "expm_apply_tridiag_noalloc")
+    return info
 
 
 def expm_profile_enable(plan: Plan, on: bool = True) -> None:
