@@ -1,6 +1,6 @@
 // tridiag.cu -- pole-batched shifted tridiagonal solves with the fused residue sum.
 //
-// Computes Y = sum_s Re(W_s X_s) (real data) where X_s solves
+// Computes Y = sum_s Re(W_s X_s) where X_s solves
 //     (t T - c I + theta_s I) X_s = V,     T real symmetric tridiagonal,
 // for every "system" s (one member of each conjugate pole pair, Remark 5.1) and
 // every right-hand-side column j.  This is eq. expAx of the paper with the
@@ -15,13 +15,18 @@
 // Because M_b is complex symmetric, the two end values of y_b = M_b^{-1} v_b that
 // this system needs are dot products: y_b[first] = u_b^T v_b, y_b[last] = w_b^T v_b.
 //
-//   K1 tri_block_factor   one thread per (system, block): unpivoted LU of M_b
-//                         (stored), spikes u_b and w_b, the end values y_b.
-//   K2 tri_reduced_cr     one CTA per (system, column): the reduced system by
-//                         cyclic reduction in shared memory.
-//   K3 tri_block_solve    one thread per (block, column): forward and back
-//                         substitution of every system with the separator values as
-//                         boundary data, and the weighted sum over systems.
+//   K0 tri_prep          d' = t d - c and e' = t e (and, for float-float, V split
+//                        into float pairs) -- once per call, so no kernel below
+//                        repeats the scaling or a binary64 conversion per system.
+//   K1a tri_block_factor one thread per (system, block): unpivoted LU of M_b
+//                        (stored) and the unit spikes u_b, w_b.
+//   K1b tri_block_dots   one thread per (system, block, column): y_b end values.
+//   K2 tri_reduced_cr    one CTA per (system, column): the reduced system by cyclic
+//                        reduction in shared memory.
+//   K3 tri_block_solve   one thread per (block, column, system): forward and back
+//                        substitution with the separator values as boundary data;
+//                        Re(W_s x_s) summed over the systems by a shuffle tree.
+//   K4 tri_finish        float-float only: the float pairs of Y to binary64.
 //
 // No pivoting: for Im(theta) != 0, (-i sign(Im theta)) M has Hermitian part
 // |Im theta| I, positive definite, so every leading block and every Schur
@@ -39,40 +44,95 @@
 
 namespace expm {
 
+// ------------------------------------------------------------------ conversions
+
+// binary64 -> float pair with integer operations only (no FP64-pipe work): hi takes
+// the leading 24 significand bits, lo the remaining 29 bits rounded to 24; the pair
+// is then renormalised.  Values outside [2^-74, 2^128) take the binary64 route.
+EXPM_D f32x2 split_bits(double x) {
+    const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+    const int ex = (int)((u >> 52) & 0x7ff);
+    if (ex < 1023 + 52 - 126 || ex > 1023 + 127) return to_f32x2(x);
+    const unsigned sign = (unsigned)(u >> 63) << 31;
+    const float hi = __uint_as_float(sign | ((unsigned)(ex - 1023 + 127) << 23) | (unsigned)((u >> 29) & 0x7fffffu));
+    const float scalef = __uint_as_float((unsigned)(ex - 1023 - 52 + 127) << 23);
+    float lo = __fmul_rn(__uint2float_rn((unsigned)(u & 0x1fffffffu)), scalef);
+    if (sign) lo = -lo;
+    return fast_two_sum(hi, lo);
+}
+
+// float -> binary64 by bit widening (normal floats; zero and the rest fall back)
+EXPM_D double widen_bits(float f) {
+    const unsigned u = __float_as_uint(f);
+    const unsigned ex = (u >> 23) & 0xff;
+    if (ex == 0 || ex == 0xff) return (double)f;
+    const unsigned long long b = ((unsigned long long)(u >> 31) << 63) |
+                                 ((unsigned long long)(ex - 127 + 1023) << 52) |
+                                 ((unsigned long long)(u & 0x7fffffu) << 29);
+    return __longlong_as_double((long long)b);
+}
+
+template <class R> struct Store;
+template <> struct Store<double> {
+    static EXPM_D double split(double x) { return x; }
+};
+template <> struct Store<f32x2> {
+    static EXPM_D f32x2 split(double x) { return split_bits(x); }
+};
+
+// ------------------------------------------------------------------ K0
 template <class R>
-__global__ void __launch_bounds__(128) tri_block_factor(TriGeom g, const double *__restrict__ d,
-                                                        const double *__restrict__ e,
-                                                        const double *__restrict__ V, TriPoles ps,
+__global__ void tri_prep(TriGeom g, const double *__restrict__ d, const double *__restrict__ e,
+                         const double *__restrict__ V, R *__restrict__ dP, R *__restrict__ eP, R *__restrict__ VP) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < g.N; i += stride) {
+        dP[i] = Store<R>::split(g.t * d[i] - g.cshift);
+        eP[i] = Store<R>::split(i + 1 < g.N ? g.t * e[i] : 0.0);
+    }
+    if (VP != nullptr) {
+        const int64_t nv = g.N * g.Rc;
+        for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nv; i += stride)
+            VP[i] = Store<R>::split(V[i]);
+    }
+}
+
+// ------------------------------------------------------------------ K1a
+// One thread per (system, block): LU of M_b and the two unit spikes.  The loads of
+// the next row are issued one iteration ahead so the serial factorization chain
+// does not wait on memory.
+template <class R>
+__global__ void __launch_bounds__(128) tri_block_factor(TriGeom g, const R *__restrict__ dP,
+                                                        const R *__restrict__ eP, TriPoles ps,
                                                         cx<R> *__restrict__ fact, cx<R> *__restrict__ us,
-                                                        cx<R> *__restrict__ wsp, cx<R> *__restrict__ spk,
-                                                        cx<R> *__restrict__ yend) {
-    using O = RealOps<R>;
+                                                        cx<R> *__restrict__ wsp, cx<R> *__restrict__ spk) {
     const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (tid >= (int64_t)g.S * g.P) return;
     const int b = (int)(tid % g.P);
     const int s = (int)(tid / g.P);
     const int64_t first = (int64_t)b * g.B;
     const int len = (b < g.P - 1) ? g.m : (int)(g.N - first);
-    const cx<R> theta = cx_from<R>(ps.th_re[s] - g.cshift, ps.th_im[s]);
-    const R tt = O::from(g.t);
+    const cx<R> theta = cx_from<R>(ps.th_re[s], ps.th_im[s]);
     cx<R> *F = fact + ((int64_t)s * g.N) * 2;
     cx<R> *U = us + (int64_t)s * g.N;
     cx<R> *W = wsp + (int64_t)s * g.N;
 
     // forward: LU of M_b (c'_i, g_i = 1/w_i) and the forward-eliminated eps_first
     cx<R> cprev = cxz<R>(), hprev = cxz<R>();
+    R dn = dP[first], en = eP[first];
+    R eprev = RealOps<R>::zero();  // e'[q-1]
     for (int i = 0; i < len; ++i) {
         const int64_t q = first + i;
-        cx<R> w = {tt * O::from(d[q]) + theta.re, theta.im};
-        R elow = O::zero();
-        if (i > 0) {
-            elow = tt * O::from(e[q - 1]);
-            w = w - scale(elow, cprev);
+        const R dq = dn, eq = en;  // d'[q], e'[q]
+        if (i + 1 < len) {
+            dn = dP[q + 1];
+            en = eP[q + 1];
         }
+        cx<R> w = {dq + theta.re, theta.im};
+        if (i > 0) w = w - scale(eprev, cprev);
         const cx<R> gi = cinv(w);
-        cx<R> cp = cxz<R>();
-        if (i < len - 1) cp = scale(tt * O::from(e[q]), gi);
-        const cx<R> h = (i == 0) ? gi : -(gi * scale(elow, hprev));
+        const cx<R> cp = (i < len - 1) ? scale(eq, gi) : cxz<R>();
+        const cx<R> h = (i == 0) ? gi : -(gi * scale(eprev, hprev));
+        eprev = eq;
         F[2 * q] = cp;
         F[2 * q + 1] = gi;
         U[q] = h;
@@ -80,72 +140,79 @@ __global__ void __launch_bounds__(128) tri_block_factor(TriGeom g, const double 
         hprev = h;
     }
     // backward: u = M_b^{-1} eps_first, w = M_b^{-1} eps_last
-    cx<R> un = cxz<R>(), wn = cxz<R>();
-    cx<R> u0, uL, w0, wL;
-    for (int i = len - 1; i >= 0; --i) {
+    const int64_t last = first + len - 1;
+    cx<R> un = U[last], wn = F[2 * last + 1];
+    const cx<R> uL = un, wL = wn;
+    W[last] = wn;
+    cx<R> hnext = cxz<R>(), cnext = cxz<R>();
+    if (len > 1) {
+        hnext = U[last - 1];
+        cnext = F[2 * (last - 1)];
+    }
+    for (int i = len - 2; i >= 0; --i) {
         const int64_t q = first + i;
-        cx<R> u, w;
-        if (i == len - 1) {
-            u = U[q];
-            w = F[2 * q + 1];
-            uL = u;
-            wL = w;
-        } else {
-            const cx<R> cp = F[2 * q];
-            u = U[q] - cp * un;
-            w = -(cp * wn);
+        const cx<R> h = hnext, cp = cnext;
+        if (i > 0) {
+            hnext = U[q - 1];
+            cnext = F[2 * (q - 1)];
         }
-        U[q] = u;
-        W[q] = w;
-        un = u;
-        wn = w;
+        un = h - cp * un;
+        wn = -(cp * wn);
+        U[q] = un;
+        W[q] = wn;
     }
-    u0 = un;
-    w0 = wn;
     cx<R> *SP = spk + ((int64_t)s * g.P + b) * 4;
-    SP[0] = u0;
-    SP[1] = uL;
-    SP[2] = w0;
-    SP[3] = wL;
-    // end values of y_b = M_b^{-1} v_b for every column: u^T v and w^T v
-    cx<R> *YE = yend + ((int64_t)s * g.P + b) * g.Rc * 2;
-    for (int j0 = 0; j0 < g.Rc; j0 += TRI_RCH) {
-        cx<R> yu[TRI_RCH], yw[TRI_RCH];
-#pragma unroll
-        for (int jj = 0; jj < TRI_RCH; ++jj) yu[jj] = yw[jj] = cxz<R>();
-        for (int i = 0; i < len; ++i) {
-            const int64_t q = first + i;
-            const cx<R> u = U[q], w = W[q];
-            const double *vr = V + q * g.Rc + j0;
-#pragma unroll
-            for (int jj = 0; jj < TRI_RCH; ++jj) {
-                if (j0 + jj < g.Rc) {
-                    const R v = O::from(vr[jj]);
-                    yu[jj] = yu[jj] + scale(v, u);
-                    yw[jj] = yw[jj] + scale(v, w);
-                }
-            }
-        }
-#pragma unroll
-        for (int jj = 0; jj < TRI_RCH; ++jj)
-            if (j0 + jj < g.Rc) {
-                YE[2 * (j0 + jj)] = yu[jj];
-                YE[2 * (j0 + jj) + 1] = yw[jj];
-            }
-    }
+    SP[0] = un;  // u_b[first]
+    SP[1] = uL;  // u_b[last]
+    SP[2] = wn;  // w_b[first]
+    SP[3] = wL;  // w_b[last]
 }
 
+// ------------------------------------------------------------------ K1b
+// One thread per (system, block, column): y_b[first] = u_b^T v_b, y_b[last] = w_b^T v_b.
+template <class R>
+__global__ void __launch_bounds__(128) tri_block_dots(TriGeom g, const R *__restrict__ VP,
+                                                      const cx<R> *__restrict__ us, const cx<R> *__restrict__ wsp,
+                                                      cx<R> *__restrict__ yend) {
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (tid >= (int64_t)g.S * g.P * g.Rc) return;
+    const int j = (int)(tid % g.Rc);
+    const int64_t sb = tid / g.Rc;
+    const int b = (int)(sb % g.P);
+    const int s = (int)(sb / g.P);
+    const int64_t first = (int64_t)b * g.B;
+    const int len = (b < g.P - 1) ? g.m : (int)(g.N - first);
+    const cx<R> *U = us + (int64_t)s * g.N;
+    const cx<R> *W = wsp + (int64_t)s * g.N;
+    cx<R> yu = cxz<R>(), yw = cxz<R>();
+    cx<R> un = U[first], wn = W[first];
+    R vn = VP[first * g.Rc + j];
+    for (int i = 0; i < len; ++i) {
+        const int64_t q = first + i;
+        const cx<R> u = un, w = wn;
+        const R v = vn;
+        if (i + 1 < len) {
+            un = U[q + 1];
+            wn = W[q + 1];
+            vn = VP[(q + 1) * g.Rc + j];
+        }
+        yu = yu + scale(v, u);
+        yw = yw + scale(v, w);
+    }
+    cx<R> *YE = yend + ((int64_t)s * g.P + b) * g.Rc * 2;
+    YE[2 * j] = yu;
+    YE[2 * j + 1] = yw;
+}
+
+// ------------------------------------------------------------------ K2
 // Reduced system for the separators of one (system, column):
 //   A_b sigma_{b-1} + B_b sigma_b + C_b sigma_{b+1} = D_b,   b = 0 .. P-2
 // solved by cyclic reduction (odd-even elimination) in shared memory.
 template <class R>
-__global__ void __launch_bounds__(1024) tri_reduced_cr(TriGeom g, const double *__restrict__ d,
-                                                       const double *__restrict__ e,
-                                                       const double *__restrict__ V, TriPoles ps,
-                                                       const cx<R> *__restrict__ spk,
-                                                       const cx<R> *__restrict__ yend,
-                                                       cx<R> *__restrict__ sigma) {
-    using O = RealOps<R>;
+__global__ void __launch_bounds__(1024) tri_reduced_cr(TriGeom g, const R *__restrict__ dP,
+                                                       const R *__restrict__ eP, const R *__restrict__ VP,
+                                                       TriPoles ps, const cx<R> *__restrict__ spk,
+                                                       const cx<R> *__restrict__ yend, cx<R> *__restrict__ sigma) {
     extern __shared__ unsigned char smem_raw[];
     const int n = g.P - 1;
     cx<R> *A = reinterpret_cast<cx<R> *>(smem_raw);
@@ -154,31 +221,24 @@ __global__ void __launch_bounds__(1024) tri_reduced_cr(TriGeom g, const double *
     cx<R> *D = C + n;
     const int s = blockIdx.x / g.Rc;
     const int j = blockIdx.x % g.Rc;
-    const cx<R> theta = cx_from<R>(ps.th_re[s] - g.cshift, ps.th_im[s]);
-    const R tt = O::from(g.t);
+    const cx<R> theta = cx_from<R>(ps.th_re[s], ps.th_im[s]);
     const cx<R> *SP = spk + (int64_t)s * g.P * 4;
     const cx<R> *YE = yend + (int64_t)s * g.P * g.Rc * 2;
 
     for (int b = threadIdx.x; b < n; b += blockDim.x) {
         const int64_t r = (int64_t)b * g.B + g.m;  // separator row
-        const R el = tt * O::from(e[r - 1]);       // couples sigma_b and the last row of block b
-        const R er = tt * O::from(e[r]);           // couples sigma_b and the first row of block b+1
+        const R el = eP[r - 1];                    // couples sigma_b and the last row of block b
+        const R er = eP[r];                        // couples sigma_b and the first row of block b+1
         const cx<R> uL = SP[4 * b + 1], wL = SP[4 * b + 3];
         const cx<R> u0n = SP[4 * (b + 1) + 0], w0n = SP[4 * (b + 1) + 2];
         cx<R> Ab = cxz<R>(), Cb = cxz<R>();
-        if (b >= 1) {
-            const R erp = tt * O::from(e[r - g.B]);  // t e at the previous separator's right side
-            Ab = -scale(el * erp, uL);
-        }
-        if (b + 1 <= n - 1) {
-            const R eln = tt * O::from(e[r + g.B - 1]);  // t e at the next separator's left side
-            Cb = -scale(er * eln, w0n);
-        }
-        cx<R> Bb = {tt * O::from(d[r]) + theta.re, theta.im};
+        if (b >= 1) Ab = -scale(el * eP[r - g.B], uL);               // e' at the previous separator's right
+        if (b + 1 <= n - 1) Cb = -scale(er * eP[r + g.B - 1], w0n);  // e' at the next separator's left
+        cx<R> Bb = {dP[r] + theta.re, theta.im};
         Bb = Bb - scale(el * el, wL) - scale(er * er, u0n);
         const cx<R> yL = YE[(int64_t)b * g.Rc * 2 + 2 * j + 1];        // y_b[last]
         const cx<R> y0n = YE[(int64_t)(b + 1) * g.Rc * 2 + 2 * j + 0];  // y_{b+1}[first]
-        cx<R> Db = {O::from(V[r * g.Rc + j]), O::zero()};
+        cx<R> Db = {VP[r * g.Rc + j], RealOps<R>::zero()};
         Db = Db - scale(el, yL) - scale(er, y0n);
         A[b] = Ab;
         Bc[b] = Bb;
@@ -186,8 +246,7 @@ __global__ void __launch_bounds__(1024) tri_reduced_cr(TriGeom g, const double *
         D[b] = Db;
     }
     __syncthreads();
-    int stride = 1;
-    for (; 2 * stride - 1 < n; stride *= 2) {
+    for (int stride = 1; 2 * stride - 1 < n; stride *= 2) {
         for (int i = 2 * stride - 1 + 2 * stride * threadIdx.x; i < n; i += 2 * stride * blockDim.x) {
             const int lo = i - stride, hi = i + stride;
             const cx<R> k1 = A[i] * cinv(Bc[lo]);
@@ -223,90 +282,106 @@ __global__ void __launch_bounds__(1024) tri_reduced_cr(TriGeom g, const double *
     for (int b = threadIdx.x; b < n; b += blockDim.x) SG[(int64_t)b * g.Rc + j] = D[b];
 }
 
-// K3: one thread per (block, column).  Systems are processed in groups of
-// TRI_SG; the forward sweep of a group stores d'_i in `scr`, the back sweep
-// forms x_i for every system of the group and adds Re(W_s x_i) into Y.
+// ------------------------------------------------------------------ K3
+// One thread per (block, column, system).  The systems of one (block, column) sit in
+// LG consecutive lanes (LG = power of two >= S, <= 32); each lane runs the forward
+// and back substitution of its system, and Re(W_s x_s) is summed over the LG lanes
+// by a shuffle tree in a fixed order (the result does not depend on scheduling).
+// The next row's loads are issued one iteration ahead.  Output: binary64 Y, or for
+// float-float the unrounded pair (hi, lo) stored in Y's 8 bytes, finished by K4.
+template <class T> EXPM_D T shfl_down(unsigned mask, T v, int off) { return __shfl_down_sync(mask, v, off); }
+template <> EXPM_D f32x2 shfl_down<f32x2>(unsigned mask, f32x2 v, int off) {
+    return {__shfl_down_sync(mask, v.hi, off), __shfl_down_sync(mask, v.lo, off)};
+}
+template <class R> EXPM_D void store_out(double *Y, int64_t idx, R v);
+template <> EXPM_D void store_out<double>(double *Y, int64_t idx, double v) { Y[idx] = v; }
+template <> EXPM_D void store_out<f32x2>(double *Y, int64_t idx, f32x2 v) {
+    reinterpret_cast<f32x2 *>(Y)[idx] = v;
+}
+
 template <class R>
-__global__ void __launch_bounds__(128) tri_block_solve(TriGeom g, const double *__restrict__ e,
-                                                       const double *__restrict__ V, TriPoles ps,
+__global__ void __launch_bounds__(128) tri_block_solve(TriGeom g, const R *__restrict__ eP,
+                                                       const R *__restrict__ VP, TriPoles ps,
                                                        const cx<R> *__restrict__ fact,
                                                        const cx<R> *__restrict__ sigma,
                                                        cx<R> *__restrict__ scr, double *__restrict__ Y) {
-    using O = RealOps<R>;
+    const int LG = g.LG;
     const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (tid >= (int64_t)g.P * g.Rc) return;
-    const int j = (int)(tid % g.Rc);
-    const int b = (int)(tid / g.Rc);
+    const int sl = (int)(tid % LG);
+    const int64_t bj = tid / LG;
+    // groups past the end leave as a whole (LG divides the CTA size); the shuffles
+    // use the group's own lane mask
+    if (bj >= (int64_t)g.P * g.Rc) return;
+    const unsigned lane = threadIdx.x & 31;
+    const unsigned gmask = (LG == 32) ? 0xffffffffu : (((1u << LG) - 1u) << (lane & ~(unsigned)(LG - 1)));
+    const int j = (int)(bj % g.Rc);
+    const int b = (int)(bj / g.Rc);
+    const bool active = sl < g.S;
+    const int s = active ? sl : 0;  // idle lanes shadow system 0 and contribute zero
     const int64_t first = (int64_t)b * g.B;
     const int len = (b < g.P - 1) ? g.m : (int)(g.N - first);
-    const R tt = O::from(g.t);
     const bool has_left = b > 0, has_right = b < g.P - 1;
-    const R eleft = has_left ? tt * O::from(e[first - 1]) : O::zero();
-    const R eright = has_right ? tt * O::from(e[first + len - 1]) : O::zero();
+    const cx<R> wgt = active ? cx_from<R>(ps.w_re[s], ps.w_im[s]) : cxz<R>();
+    const cx<R> *SG = sigma + (int64_t)s * g.P * g.Rc;
+    const cx<R> sl_v = has_left ? SG[(int64_t)(b - 1) * g.Rc + j] : cxz<R>();
+    const cx<R> sr_v = has_right ? SG[(int64_t)b * g.Rc + j] : cxz<R>();
+    const R eleft = has_left ? eP[first - 1] : RealOps<R>::zero();
+    const R eright = has_right ? eP[first + len - 1] : RealOps<R>::zero();
+    const cx<R> *F = fact + (int64_t)s * g.N * 2;
+    cx<R> *SC = scr + (((int64_t)first * g.Rc + j) * LG + sl);  // this lane's column
+    const int64_t sstride = (int64_t)g.Rc * LG;
 
-    for (int s0 = 0; s0 < g.S; s0 += TRI_SG) {
-        const int ns = min(TRI_SG, g.S - s0);
-        cx<R> sl[TRI_SG], sr[TRI_SG], dp[TRI_SG];
-#pragma unroll
-        for (int k = 0; k < TRI_SG; ++k) {
-            sl[k] = sr[k] = dp[k] = cxz<R>();
-            if (k < ns) {
-                const cx<R> *SG = sigma + (int64_t)(s0 + k) * g.P * g.Rc;
-                if (has_left) sl[k] = SG[(int64_t)(b - 1) * g.Rc + j];
-                if (has_right) sr[k] = SG[(int64_t)b * g.Rc + j];
-            }
+    // forward substitution
+    cx<R> dp = cxz<R>();
+    R vn = VP[first * g.Rc + j];
+    cx<R> gn = F[2 * first + 1];
+    R en = RealOps<R>::zero();
+    for (int i = 0; i < len; ++i) {
+        const int64_t q = first + i;
+        const R vq = vn, elq = en;  // v[q], e'[q-1]
+        const cx<R> gi = gn;
+        if (i + 1 < len) {
+            vn = VP[(q + 1) * g.Rc + j];
+            gn = F[2 * (q + 1) + 1];
+            en = eP[q];
         }
-        // forward substitution, all systems of the group together
-        for (int i = 0; i < len; ++i) {
-            const int64_t q = first + i;
-            const R v = O::from(V[q * g.Rc + j]);
-            const R elow = (i > 0) ? tt * O::from(e[q - 1]) : O::zero();
-            cx<R> *SC = scr + (((int64_t)q * TRI_SG) * g.Rc + j);
-#pragma unroll
-            for (int k = 0; k < TRI_SG; ++k) {
-                if (k < ns) {
-                    cx<R> rhs = {v, O::zero()};
-                    if (i == 0 && has_left) rhs = rhs - scale(eleft, sl[k]);
-                    if (i == len - 1 && has_right) rhs = rhs - scale(eright, sr[k]);
-                    if (i > 0) rhs = rhs - scale(elow, dp[k]);
-                    const cx<R> gi = fact[((int64_t)(s0 + k) * g.N + q) * 2 + 1];
-                    dp[k] = gi * rhs;
-                    SC[(int64_t)k * g.Rc] = dp[k];
-                }
-            }
+        cx<R> rhs = {vq, RealOps<R>::zero()};
+        if (i == 0 && has_left) rhs = rhs - scale(eleft, sl_v);
+        if (i == len - 1 && has_right) rhs = rhs - scale(eright, sr_v);
+        if (i > 0) rhs = rhs - scale(elq, dp);
+        dp = gi * rhs;
+        SC[(int64_t)i * sstride] = dp;
+    }
+    // back substitution and the weighted sum over systems
+    cx<R> xn = cxz<R>();
+    cx<R> scn = SC[(int64_t)(len - 1) * sstride];
+    cx<R> cn = (len > 1) ? F[2 * (first + len - 2)] : cxz<R>();  // c' of row last-1
+    for (int i = len - 1; i >= 0; --i) {
+        const int64_t q = first + i;
+        const cx<R> sc = scn;
+        if (i > 0) scn = SC[(int64_t)(i - 1) * sstride];
+        cx<R> x = sc;
+        if (i < len - 1) {
+            x = sc - cn * xn;             // cn is c'[q]
+            if (i > 0) cn = F[2 * (q - 1)];  // c'[q-1] for the next row
         }
-        // back substitution and weighted sum
-        cx<R> xn[TRI_SG];
-#pragma unroll
-        for (int k = 0; k < TRI_SG; ++k) xn[k] = cxz<R>();
-        for (int i = len - 1; i >= 0; --i) {
-            const int64_t q = first + i;
-            const cx<R> *SC = scr + (((int64_t)q * TRI_SG) * g.Rc + j);
-            R acc = O::zero();
-#pragma unroll
-            for (int k = 0; k < TRI_SG; ++k) {
-                if (k < ns) {
-                    cx<R> x = SC[(int64_t)k * g.Rc];
-                    if (i < len - 1) x = x - fact[((int64_t)(s0 + k) * g.N + q) * 2] * xn[k];
-                    xn[k] = x;
-                    acc = acc + re_mul(cx_from<R>(ps.w_re[s0 + k], ps.w_im[s0 + k]), x);
-                }
-            }
-            double out = O::todbl(acc);
-            if (s0 > 0) out += Y[q * g.Rc + j];
-            Y[q * g.Rc + j] = out;
-        }
-        // the separator row that follows this block
-        if (has_right) {
-            const int64_t r = first + len;
-            R acc = O::zero();
-#pragma unroll
-            for (int k = 0; k < TRI_SG; ++k)
-                if (k < ns) acc = acc + re_mul(cx_from<R>(ps.w_re[s0 + k], ps.w_im[s0 + k]), sr[k]);
-            double out = O::todbl(acc);
-            if (s0 > 0) out += Y[r * g.Rc + j];
-            Y[r * g.Rc + j] = out;
-        }
+        xn = x;
+        R acc = re_mul(wgt, x);
+        for (int off = LG / 2; off > 0; off >>= 1) acc = acc + shfl_down(gmask, acc, off);
+        if (sl == 0) store_out<R>(Y, q * g.Rc + j, acc);
+    }
+    // the separator row that follows this block
+    R acc = re_mul(wgt, sr_v);
+    for (int off = LG / 2; off > 0; off >>= 1) acc = acc + shfl_down(gmask, acc, off);
+    if (sl == 0 && has_right) store_out<R>(Y, (first + len) * g.Rc + j, acc);
+}
+
+// ------------------------------------------------------------------ K4
+__global__ void tri_finish(int64_t n, double *__restrict__ Y) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const f32x2 v = reinterpret_cast<const f32x2 *>(Y)[i];
+        Y[i] = widen_bits(v.hi) + widen_bits(v.lo);
     }
 }
 
@@ -317,7 +392,7 @@ TriGeom tri_geometry(int64_t N, int S, int Rc, bool ff, int sm_count) {
     g.N = N;
     g.S = S;
     g.Rc = Rc;
-    // enough (system, block) threads to keep every SM sub-partition busy in K1
+    // enough (system, block) threads to keep every SM sub-partition busy in K1a
     const int64_t warps_per_sm = ff ? 8 : 4;
     const int64_t target = (int64_t)sm_count * warps_per_sm * 32;
     int64_t P = (target + S - 1) / S;
@@ -334,63 +409,99 @@ TriGeom tri_geometry(int64_t N, int S, int Rc, bool ff, int sm_count) {
     g.m = (int)m;
     g.B = (int)(m + 1);
     g.P = (int)P;
+    int lg = 1;
+    while (lg < S) lg *= 2;
+    g.LG = lg;
     return g;
-}
-
-size_t tri_workspace_bytes(const TriGeom &g, bool ff) {
-    const size_t c = 16;  // sizeof(cx<double>) == sizeof(cx<f32x2>)
-    (void)ff;
-    size_t fact = (size_t)g.S * g.N * 2 * c;
-    size_t us = (size_t)g.S * g.N * c, ws = us;
-    size_t spk = (size_t)g.S * g.P * 4 * c;
-    size_t yend = (size_t)g.S * g.P * g.Rc * 2 * c;
-    size_t sig = (size_t)g.S * g.P * g.Rc * c;
-    size_t scr = (size_t)g.N * TRI_SG * g.Rc * c;
-    size_t k1 = us + ws;
-    return fact + spk + yend + sig + std::max(k1, scr) + 6 * 256;
 }
 
 static inline size_t align_up(size_t x) { return (x + 255) & ~size_t(255); }
 
+struct TriLayout {
+    size_t fact, spk, yend, sig, scratch, prepd, prepe, prepv, total;
+};
+
+static TriLayout tri_layout(const TriGeom &g, bool ff) {
+    const size_t c = 16;  // sizeof(cx<double>) == sizeof(cx<f32x2>)
+    TriLayout L{};
+    size_t off = 0;
+    L.fact = off;
+    off += align_up((size_t)g.S * g.N * 2 * c);
+    L.spk = off;
+    off += align_up((size_t)g.S * g.P * 4 * c);
+    L.yend = off;
+    off += align_up((size_t)g.S * g.P * g.Rc * 2 * c);
+    L.sig = off;
+    off += align_up((size_t)g.S * g.P * g.Rc * c);
+    L.scratch = off;  // K1's spikes and K3's forward values share this region
+    off += align_up(std::max((size_t)g.S * g.N * 2 * c, (size_t)g.N * g.LG * g.Rc * c));
+    L.prepd = off;
+    off += align_up((size_t)g.N * 8);
+    L.prepe = off;
+    off += align_up((size_t)g.N * 8);
+    L.prepv = off;
+    if (ff) off += align_up((size_t)g.N * g.Rc * 8);
+    L.total = off;
+    return L;
+}
+
+size_t tri_workspace_bytes(const TriGeom &g, bool ff) { return tri_layout(g, ff).total; }
+
 template <class R>
 static cudaError_t tri_run_t(const TriGeom &g, const double *d, const double *e, const double *V,
                              double *Y, const TriPoles &ps, void *work, cudaStream_t st, Profiler &prof) {
-    const size_t c = sizeof(cx<R>);
+    const bool ff = !std::is_same<R, double>::value;
+    const TriLayout L = tri_layout(g, ff);
     unsigned char *p = (unsigned char *)work;
-    cx<R> *fact = (cx<R> *)p;
-    p += align_up((size_t)g.S * g.N * 2 * c);
-    cx<R> *spk = (cx<R> *)p;
-    p += align_up((size_t)g.S * g.P * 4 * c);
-    cx<R> *yend = (cx<R> *)p;
-    p += align_up((size_t)g.S * g.P * g.Rc * 2 * c);
-    cx<R> *sig = (cx<R> *)p;
-    p += align_up((size_t)g.S * g.P * g.Rc * c);
-    // K1's spike scratch and K3's forward scratch share one region
-    cx<R> *us = (cx<R> *)p;
+    cx<R> *fact = (cx<R> *)(p + L.fact);
+    cx<R> *spk = (cx<R> *)(p + L.spk);
+    cx<R> *yend = (cx<R> *)(p + L.yend);
+    cx<R> *sig = (cx<R> *)(p + L.sig);
+    cx<R> *us = (cx<R> *)(p + L.scratch);
     cx<R> *wsp = us + (size_t)g.S * g.N;
-    cx<R> *scr = (cx<R> *)p;
+    cx<R> *scr = (cx<R> *)(p + L.scratch);
+    R *dP = (R *)(p + L.prepd);
+    R *eP = (R *)(p + L.prepe);
+    R *VP = ff ? (R *)(p + L.prepv) : nullptr;
+    const R *Vuse = ff ? VP : reinterpret_cast<const R *>(V);
+    const unsigned pgrid = (unsigned)std::min<int64_t>((g.N * (ff ? g.Rc : 1) + 255) / 256, 152 * 8);
 
-    const bool ff = sizeof(R) != sizeof(double) || !std::is_same<R, double>::value;
+    cudaError_t err = prof.timed(ff ? "tri_prep<f32x2>" : "tri_prep<f64>", st, [&] {
+        tri_prep<R><<<pgrid, 256, 0, st>>>(g, d, e, V, dP, eP, VP);
+        return cudaGetLastError();
+    });
+    if (err != cudaSuccess) return err;
     const int64_t n1 = (int64_t)g.S * g.P;
-    cudaError_t err = prof.timed(ff ? "tri_block_factor<f32x2>" : "tri_block_factor<f64>", st, [&] {
-        tri_block_factor<R><<<(unsigned)((n1 + 127) / 128), 128, 0, st>>>(g, d, e, V, ps, fact, us, wsp, spk,
-                                                                            yend);
+    err = prof.timed(ff ? "tri_block_factor<f32x2>" : "tri_block_factor<f64>", st, [&] {
+        tri_block_factor<R><<<(unsigned)((n1 + 127) / 128), 128, 0, st>>>(g, dP, eP, ps, fact, us, wsp, spk);
+        return cudaGetLastError();
+    });
+    if (err != cudaSuccess) return err;
+    const int64_t n1b = n1 * g.Rc;
+    err = prof.timed(ff ? "tri_block_dots<f32x2>" : "tri_block_dots<f64>", st, [&] {
+        tri_block_dots<R><<<(unsigned)((n1b + 127) / 128), 128, 0, st>>>(g, Vuse, us, wsp, yend);
         return cudaGetLastError();
     });
     if (err != cudaSuccess) return err;
     if (g.P > 1) {
-        const size_t smem = (size_t)4 * (g.P - 1) * c;
+        const size_t smem = (size_t)4 * (g.P - 1) * sizeof(cx<R>);
         err = cudaFuncSetAttribute(tri_reduced_cr<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (err != cudaSuccess) return err;
         err = prof.timed(ff ? "tri_reduced_cr<f32x2>" : "tri_reduced_cr<f64>", st, [&] {
-            tri_reduced_cr<R><<<g.S * g.Rc, 512, smem, st>>>(g, d, e, V, ps, spk, yend, sig);
+            tri_reduced_cr<R><<<g.S * g.Rc, 512, smem, st>>>(g, dP, eP, Vuse, ps, spk, yend, sig);
             return cudaGetLastError();
         });
         if (err != cudaSuccess) return err;
     }
-    const int64_t n3 = (int64_t)g.P * g.Rc;
-    return prof.timed(ff ? "tri_block_solve<f32x2>" : "tri_block_solve<f64>", st, [&] {
-        tri_block_solve<R><<<(unsigned)((n3 + 127) / 128), 128, 0, st>>>(g, e, V, ps, fact, sig, scr, Y);
+    const int64_t n3 = (int64_t)g.P * g.Rc * g.LG;  // LG divides 128: groups never straddle CTAs
+    err = prof.timed(ff ? "tri_block_solve<f32x2>" : "tri_block_solve<f64>", st, [&] {
+        tri_block_solve<R><<<(unsigned)((n3 + 127) / 128), 128, 0, st>>>(g, eP, Vuse, ps, fact, sig, scr, Y);
+        return cudaGetLastError();
+    });
+    if (err != cudaSuccess || !ff) return err;
+    return prof.timed("tri_finish<f32x2>", st, [&] {
+        const int64_t ny = g.N * g.Rc;
+        tri_finish<<<(unsigned)std::min<int64_t>((ny + 255) / 256, 152 * 8), 256, 0, st>>>(ny, Y);
         return cudaGetLastError();
     });
 }

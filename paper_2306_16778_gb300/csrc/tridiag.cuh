@@ -8,11 +8,9 @@ namespace expm {
 
 struct Profiler;
 
-constexpr int TRI_RCH = 8;      // right-hand-side columns per dot-product pass in K1
-constexpr int TRI_SG = 8;       // systems processed together in K3
 constexpr int TRI_PMAX = 3000;  // max blocks: the reduced system (P-1 rows) lives in shared memory
 constexpr int TRI_MMIN = 8;     // min interior rows per block
-constexpr int TRI_MAXSYS = 64;
+constexpr int TRI_MAXSYS = 32;  // real data: one system per conjugate pair, degree <= 64
 
 // Row partition: P blocks; block b starts at row b*B, has m interior rows
 // (the last block has N - (P-1)*B rows) and, for b < P-1, is followed by the
@@ -21,6 +19,7 @@ struct TriGeom {
     int64_t N;
     int m, B, P;
     int S;       // systems (shifted matrices)
+    int LG;      // lanes per (block, column) group in the solve kernel: power of two >= S
     int Rc;      // real right-hand-side columns
     double t;    // time factor
     double cshift;
