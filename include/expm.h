@@ -222,6 +222,81 @@ expm_status expm_apply_dense(expm_plan plan, int n, const void *A, int lda, int 
                              expm_info *info);
 
 /*
+ * expm_apply_batched -- Y_i = e^c R_n(tA_i - cI) V_i for `count` independent dense
+ * Hermitian problems of uneven sizes (eq. expAx per instance, Sec. 3).
+ *   count            number of instances (0 is a no-op)
+ *   n[i], k[i]       order of A_i and number of right-hand sides (1 <= k[i] <= 4096);
+ *                    host arrays
+ *   A[i]             n[i] x n[i], row-major, leading dimension n[i]; real symmetric
+ *                    (a_is_complex == 0) or complex Hermitian, device memory
+ *   V[i], Y[i]       n[i] x k[i], row-major, leading dimension k[i], device memory;
+ *                    V complex iff v_is_complex (complex V needs complex A); Y complex
+ *                    iff A or V is complex
+ *   opts             as expm_apply_dense (precision, refinement, growth limit, stream)
+ *   per_instance     optional host array of `count` expm_info, filled per instance
+ * Method: instances are grouped by size into buckets and zero-padded to the bucket's
+ * order (exact: the padded part of tA - cI + theta I is the diagonal (theta - c) I);
+ * each bucket is one batch of (instance, pole pair) units for the dense kernels
+ * (unpivoted LU, triangular solves, refinement, residue sum).  The call
+ * synchronises opts->stream.  Returns EXPM_EGROWTH / EXPM_ENOCONV if any instance
+ * failed the growth or refinement test (all Y_i are written; per_instance says
+ * which), EXPM_ENOTSUP for complex V with real A.
+ */
+expm_status expm_apply_batched(expm_plan plan, int count, const int *n, const void *const *A, int a_is_complex,
+                               const void *const *V, const int *k, int v_is_complex, void *const *Y,
+                               const expm_opts *opts, expm_info *per_instance);
+
+/*
+ * Request server (no counterpart in the paper: a serving pattern around eq. expAx).
+ * Operators are registered once and copied into server-owned device memory; requests
+ * bring device buffers V (n x k, row-major, ld k; real or complex) and Y and are
+ * executed asynchronously by `max_inflight` worker threads, each on its own CUDA
+ * stream, as soon as a worker and enough of the HBM budget are free (continuous
+ * batching: work of requests admitted at different times overlaps on the device).
+ * Factorizations (tridiagonal block LUs and spikes; dense per-pair LUs) are cached per
+ * (operator, plan, precision class, t, c), counted in the budget and evicted least
+ * recently used; a request whose factorization is cached runs only its solve part.
+ * Each result depends only on its own inputs (deterministic kernels, no reduction
+ * across requests), so it is the same alone and in the mix.
+ *
+ *   expm_server_create     hbm_budget_bytes: bound on solve scratch + cached factors
+ *                          (operator copies are not counted); 1 <= max_inflight <= 64.
+ *                          Uses the CUDA device current at creation.
+ *   expm_server_register_op  desc: EXPM_OP_TRIDIAG (d, e as in expm_apply_tridiag;
+ *                          real e only) or EXPM_OP_DENSE (A, lda, a_is_complex); the
+ *                          data may be host or device memory and is copied.
+ *   expm_server_submit     V and Y device memory, valid until poll reports the request
+ *                          finished; 1 <= k <= 64; opts as for the matching apply call
+ *                          (opts->stream is ignored).  EXPM_EAGAIN when the queue is
+ *                          full, EXPM_ENOMEM when one request exceeds the whole budget,
+ *                          EXPM_ENOTFOUND for an unknown operator.
+ *   expm_server_poll       EXPM_EAGAIN while pending; otherwise the request's final
+ *                          status, its info and timestamps ts = {submit, admit, start,
+ *                          done} in seconds since server creation; the ticket is then
+ *                          released (a second poll returns EXPM_ENOTFOUND).
+ *   expm_server_destroy    drops queued requests, waits for running ones, frees all.
+ */
+typedef struct expm_server_s *expm_server;
+enum { EXPM_OP_TRIDIAG = 1, EXPM_OP_DENSE = 2 };
+typedef struct expm_op_desc {
+    int kind;          /* EXPM_OP_TRIDIAG or EXPM_OP_DENSE             */
+    int64_t n;         /* rows (tridiagonal N or dense order n)        */
+    const double *d;   /* tridiagonal: diagonal (n doubles)            */
+    const void *e;     /* tridiagonal: off-diagonal (n-1 entries)      */
+    int e_is_complex;  /* tridiagonal: must be 0                       */
+    const void *A;     /* dense: n x n, row-major                      */
+    int lda;           /* dense: leading dimension (elements)          */
+    int a_is_complex;  /* dense: complex Hermitian if nonzero          */
+} expm_op_desc;
+
+expm_status expm_server_create(size_t hbm_budget_bytes, int max_inflight, expm_server *out);
+expm_status expm_server_register_op(expm_server server, const expm_op_desc *desc, uint64_t *op_id);
+expm_status expm_server_submit(expm_server server, uint64_t op_id, const expm_plan plan, const void *V, int k,
+                               int v_is_complex, void *Y, const expm_opts *opts, uint64_t *ticket);
+expm_status expm_server_poll(expm_server server, uint64_t ticket, expm_info *info, double ts[4]);
+expm_status expm_server_destroy(expm_server server);
+
+/*
  * Measurement hooks (no counterpart in the paper).  When enabled on a plan, every
  * kernel launch made through that plan is bracketed by CUDA events recorded on the
  * launch stream; expm_profile_read synchronises on the recorded events and returns,

@@ -18,6 +18,8 @@ from ._native import (  # noqa: F401
     EXPM_MIXED_TF32X3,
     ExpmError,
     Plan,
+    Server,
+    expm_apply_batched,
     expm_apply_dense,
     expm_apply_tridiag,
     expm_apply_tridiag_noalloc,

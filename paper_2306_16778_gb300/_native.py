@@ -31,6 +31,16 @@ class expm_opts(ctypes.Structure):
                 ("stream", ctypes.c_void_p), ("flags", ctypes.c_int)]
 
 
+class expm_op_desc(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("n", ctypes.c_int64), ("d", ctypes.c_void_p), ("e", ctypes.c_void_p),
+                ("e_is_complex", ctypes.c_int), ("A", ctypes.c_void_p), ("lda", ctypes.c_int),
+                ("a_is_complex", ctypes.c_int)]
+
+
+EXPM_OP_TRIDIAG = 1
+EXPM_OP_DENSE = 2
+
+
 class expm_info(ctypes.Structure):
     _fields_ = [("refine_iters_max", ctypes.c_int), ("growth_max_seen", ctypes.c_double),
                 ("resid_rel_max", ctypes.c_double), ("status_worst", ctypes.c_int)]
@@ -64,6 +74,21 @@ def _load() -> ctypes.CDLL:
     L.expm_apply_tridiag_noalloc.argtypes = [vp, i64, vp, vp, i, vp, i, i, vp, ctypes.POINTER(expm_opts),
                                              ctypes.POINTER(expm_info)]
     L.expm_apply_tridiag_noalloc.restype = i
+    L.expm_apply_batched.argtypes = [vp, i, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(vp), i,
+                                     ctypes.POINTER(vp), ctypes.POINTER(ctypes.c_int), i, ctypes.POINTER(vp),
+                                     ctypes.POINTER(expm_opts), ctypes.POINTER(expm_info)]
+    L.expm_apply_batched.restype = i
+    u64 = ctypes.c_uint64
+    L.expm_server_create.argtypes = [ctypes.c_size_t, i, ctypes.POINTER(vp)]
+    L.expm_server_create.restype = i
+    L.expm_server_register_op.argtypes = [vp, ctypes.POINTER(expm_op_desc), ctypes.POINTER(u64)]
+    L.expm_server_register_op.restype = i
+    L.expm_server_submit.argtypes = [vp, u64, vp, vp, i, i, vp, ctypes.POINTER(expm_opts), ctypes.POINTER(u64)]
+    L.expm_server_submit.restype = i
+    L.expm_server_poll.argtypes = [vp, u64, ctypes.POINTER(expm_info), ctypes.POINTER(ctypes.c_double)]
+    L.expm_server_poll.restype = i
+    L.expm_server_destroy.argtypes = [vp]
+    L.expm_server_destroy.restype = i
     L.expm_profile_enable.argtypes = [vp, i]
     L.expm_profile_enable.restype = i
     L.expm_profile_read.argtypes = [vp, i, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(ctypes.c_int64),
@@ -223,6 +248,27 @@ def expm_apply_dense(plan: Plan, A, V, Y, prec=EXPM_FP64, t=1.0, shift_c=0.0, st
     return info
 
 
+def expm_apply_batched(plan: Plan, As, Vs, Ys, prec=EXPM_FP64, t=1.0, shift_c=0.0, stream=None, tol=None,
+                       max_refine=None, growth_max=None, check=True):
+    """Y_i = e^c R_n(tA_i - cI) V_i for lists of device tensors (see include/expm.h).
+    Returns the list of per-instance expm_info."""
+    cnt = len(As)
+    n_arr = (ctypes.c_int * cnt)(*[int(a.shape[0]) for a in As])
+    k_arr = (ctypes.c_int * cnt)(*[int(v.shape[1]) if len(v.shape) == 2 else 1 for v in Vs])
+    a_arr = (ctypes.c_void_p * cnt)(*[_ptr(a) for a in As])
+    v_arr = (ctypes.c_void_p * cnt)(*[_ptr(v) for v in Vs])
+    y_arr = (ctypes.c_void_p * cnt)(*[_ptr(y) for y in Ys])
+    if stream is None:
+        stream = _default_stream(*As[:1])
+    o = make_opts(prec, t, shift_c, stream, tol, max_refine, growth_max)
+    infos = (expm_info * max(cnt, 1))()
+    st = lib.expm_apply_batched(plan.handle, cnt, n_arr, a_arr, int(_is_complex(As[0])) if cnt else 0, v_arr, k_arr,
+                                int(_is_complex(Vs[0])) if cnt else 0, y_arr, ctypes.byref(o), infos)
+    if check or st not in (3, 4):
+        _check(st, "expm_apply_batched")
+    return list(infos)[:cnt]
+
+
 def expm_apply_tridiag(plan: Plan, d, e, V, Y, prec=EXPM_FP64, t=1.0, shift_c=0.0, stream=None) -> expm_info:
     """Y = e^c R_n(tT - cI) V for the Hermitian tridiagonal T = (d, e); see include/expm.h."""
     N = int(d.shape[0])
@@ -235,3 +281,59 @@ def expm_apply_tridiag(plan: Plan, d, e, V, Y, prec=EXPM_FP64, t=1.0, shift_c=0.
                                   int(_is_complex(V)), _ptr(Y), ctypes.byref(o), ctypes.byref(info)),
            "expm_apply_tridiag")
     return info
+
+
+class Server:
+    """Owns an ``expm_server``: continuous-batching exp(tA)V requests (include/expm.h)."""
+
+    def __init__(self, hbm_budget_bytes: int, max_inflight: int = 4):
+        self._h = ctypes.c_void_p()
+        _check(lib.expm_server_create(int(hbm_budget_bytes), int(max_inflight), ctypes.byref(self._h)),
+               "expm_server_create")
+        self._keep = {}
+
+    def register_tridiag(self, d, e) -> int:
+        desc = expm_op_desc(EXPM_OP_TRIDIAG, int(d.shape[0]), _ptr(d), _ptr(e), int(_is_complex(e)), None, 0, 0)
+        oid = ctypes.c_uint64()
+        _check(lib.expm_server_register_op(self._h, ctypes.byref(desc), ctypes.byref(oid)), "expm_server_register_op")
+        return int(oid.value)
+
+    def register_dense(self, A) -> int:
+        n = int(A.shape[0])
+        desc = expm_op_desc(EXPM_OP_DENSE, n, None, None, 0, _ptr(A), n, int(_is_complex(A)))
+        oid = ctypes.c_uint64()
+        _check(lib.expm_server_register_op(self._h, ctypes.byref(desc), ctypes.byref(oid)), "expm_server_register_op")
+        return int(oid.value)
+
+    def submit(self, op_id: int, plan: "Plan", V, Y, prec=EXPM_FP64, t=1.0, shift_c=0.0, tol=None,
+               max_refine=None) -> int:
+        """Queue a request; V and Y must stay alive until poll() reports it finished."""
+        k = int(V.shape[1]) if len(V.shape) == 2 else 1
+        o = make_opts(prec, t, shift_c, None, tol, max_refine)
+        tk = ctypes.c_uint64()
+        _check(lib.expm_server_submit(self._h, int(op_id), plan.handle, _ptr(V), k, int(_is_complex(V)), _ptr(Y),
+                                      ctypes.byref(o), ctypes.byref(tk)), "expm_server_submit")
+        self._keep[int(tk.value)] = (V, Y, plan)
+        return int(tk.value)
+
+    def poll(self, ticket: int):
+        """None while pending, else (status, expm_info, timestamps[4])."""
+        info = expm_info()
+        ts = (ctypes.c_double * 4)()
+        st = lib.expm_server_poll(self._h, int(ticket), ctypes.byref(info), ts)
+        if st == 6:                 # EXPM_EAGAIN: pending
+            return None
+        self._keep.pop(int(ticket), None)
+        return st, info, list(ts)
+
+    def close(self) -> None:
+        if self._h:
+            lib.expm_server_destroy(self._h)
+            self._h = ctypes.c_void_p()
+            self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -297,6 +297,7 @@ expm_status expm_apply_dense(expm_plan p, int n, const void *A, int lda, int a_i
     const bool complex_a = a_is_complex != 0;
     DenseGeom g{};
     g.n = n;
+    g.ninst = 1;
     g.complex_a = complex_a;
     g.npairs = S;
     g.nsys = complex_a ? 2 * S : S;
@@ -343,10 +344,19 @@ expm_status expm_apply_dense(expm_plan p, int n, const void *A, int lda, int a_i
     expm_status s = plan_reserve(p, &p->work, &p->work_bytes, dense_workspace_bytes(g));
     if (s != EXPM_OK) return s;
     DenseResult res{};
-    const int64_t ldv_eff = split_v ? 2 * (int64_t)ldv : ldv;   // in units of the loaded element
-    const int64_t ldy_eff = split_v ? 2 * (int64_t)ldy : ldy;
-    cudaError_t err = dense_run(g, dA, lda, dV, ldv_eff, (complex_a && v_is_complex) ? 1 : 0, dY, ldy_eff, sys, p->work,
-                                st, p->prof, &res);
+    DenseIO io{};
+    io.A = dA;
+    io.lda = lda;
+    io.astride = 0;
+    io.V = dV;
+    io.ldv = split_v ? 2 * (int64_t)ldv : ldv;  // in units of the loaded element
+    io.vstride = 0;
+    io.v_cplx = (complex_a && v_is_complex) ? 1 : 0;
+    io.Y = dY;
+    io.ldy = split_v ? 2 * (int64_t)ldy : ldy;
+    io.ystride = 0;
+    io.y_real = complex_a ? 0 : 1;
+    cudaError_t err = dense_run(g, io, sys, p->work, st, p->prof, &res);
     if (err != cudaSuccess) return cuda_error(err, "apply_dense: kernels");
     if (staged && !dy) {
         err = cudaMemcpyAsync(Y, dY, sizeof(double) * nY, cudaMemcpyDeviceToHost, st);

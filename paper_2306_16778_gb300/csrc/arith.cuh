@@ -116,6 +116,16 @@ template <class R> EXPM_D cx<R> cinv(cx<R> w) {
 }
 // Re(a * b)
 template <class R> EXPM_D R re_mul(cx<R> a, cx<R> b) { return a.re * b.re - a.im * b.im; }
+// s - c*x (complex), and v - e*d for real v, e (the Thomas updates), written so
+// that binary64 uses two FMAs per component.
+template <class R> EXPM_D cx<R> csub_mul(cx<R> s, cx<R> c, cx<R> x) { return s - c * x; }
+template <> EXPM_D cx<double> csub_mul<double>(cx<double> s, cx<double> c, cx<double> x) {
+    return {fma(c.im, x.im, fma(-c.re, x.re, s.re)), fma(-c.im, x.re, fma(-c.re, x.im, s.im))};
+}
+template <class R> EXPM_D cx<R> real_minus_scaled(R v, R e, cx<R> d) { return {v - e * d.re, -(e * d.im)}; }
+template <> EXPM_D cx<double> real_minus_scaled<double>(double v, double e, cx<double> d) {
+    return {fma(-e, d.re, v), -e * d.im};
+}
 
 template <class R> EXPM_D cx<R> cx_from(double re, double im) {
     return {RealOps<R>::from(re), RealOps<R>::from(im)};

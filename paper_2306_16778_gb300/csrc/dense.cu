@@ -18,6 +18,7 @@
 // GEMM (all pole pairs in one launch).
 #include <cmath>
 #include <cstdio>
+#include <algorithm>
 #include <cstring>
 #include <vector>
 
@@ -30,40 +31,43 @@ namespace expm {
 
 // ------------------------------------------------------------------ small kernels
 
-// X[b] (n x kc, cx<T>) = V as complex; V real (v_cplx = 0, ldv in doubles) or complex
-// (ldv in complex entries).  Shared by every batch b.
+// X[z] (n x kc, cx<T>) = V of instance z / per_inst as complex; V real (v_cplx = 0)
+// or complex (v_cplx = 1).
 template <class T>
-__global__ void load_rhs(int n, int kc, const double *__restrict__ V, int64_t ldv, int v_cplx, cx<T> *X,
-                         int64_t xstride) {
+__global__ void load_rhs(int n, int kc, DenseIO io, int per_inst, cx<T> *X, int64_t xstride) {
+    const int z = blockIdx.z;
+    const double *V = io.V + (int64_t)(z / per_inst) * io.vstride * (io.v_cplx ? 2 : 1);
     const int64_t total = (int64_t)n * kc;
     for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
          idx += (int64_t)gridDim.x * blockDim.x) {
-        const int i = (int)(idx / kc), j = (int)(idx % kc);
+        const int64_t i = idx / kc, j = idx % kc;
         cx<T> v;
-        if (v_cplx) v = {(T)V[2 * (i * ldv + j)], (T)V[2 * (i * ldv + j) + 1]};
-        else v = {(T)V[i * ldv + j], (T)0};
-        X[(int64_t)blockIdx.z * xstride + idx] = v;
+        if (io.v_cplx) v = {(T)V[2 * (i * io.ldv + j)], (T)V[2 * (i * io.ldv + j) + 1]};
+        else v = {(T)V[i * io.ldv + j], (T)0};
+        X[(int64_t)z * xstride + idx] = v;
     }
 }
 
-// R[b] = V - (theta_b - c) X[b]   (the diagonal part of the residual; the tA X part
-// is subtracted by a GEMM afterwards)
-__global__ void residual_diag(int n, int kc, const double *__restrict__ V, int64_t ldv, int v_cplx,
-                              const cx<double> *X, cx<double> *R, int64_t stride, DenseSystems sys) {
-    const int b = blockIdx.z;
+// R[z] = V - (theta_sys - c) X[z]   (the diagonal part of the residual; the tA X part
+// is subtracted by a GEMM afterwards).  z = instance * nsys + sys.
+__global__ void residual_diag(int n, int kc, DenseIO io, int nsys, const cx<double> *X, cx<double> *R, int64_t stride,
+                              DenseSystems sys) {
+    const int z = blockIdx.z;
+    const int b = z % nsys;
+    const double *V = io.V + (int64_t)(z / nsys) * io.vstride * (io.v_cplx ? 2 : 1);
     const cx<double> sh = {sys.th_re[b] - sys.cshift, sys.th_im[b]};
     const int64_t total = (int64_t)n * kc;
     for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
          idx += (int64_t)gridDim.x * blockDim.x) {
-        const int i = (int)(idx / kc), j = (int)(idx % kc);
+        const int64_t i = idx / kc, j = idx % kc;
         cx<double> v;
-        if (v_cplx) v = {V[2 * (i * ldv + j)], V[2 * (i * ldv + j) + 1]};
-        else v = {V[i * ldv + j], 0.0};
-        R[(int64_t)b * stride + idx] = v - sh * X[(int64_t)b * stride + idx];
+        if (io.v_cplx) v = {V[2 * (i * io.ldv + j)], V[2 * (i * io.ldv + j) + 1]};
+        else v = {V[i * io.ldv + j], 0.0};
+        R[(int64_t)z * stride + idx] = v - sh * X[(int64_t)z * stride + idx];
     }
 }
 
-// Xc (binary32) = R (binary64) and sums of |R|^2, |X|^2 per batch
+// Xc (binary32) = R (binary64) and sums of |R|^2, |X|^2 per batch entry
 __global__ void demote_and_norms(int64_t total, const cx<double> *R, const cx<double> *X, cx<float> *Xc,
                                  int64_t stride, double *rn2, double *xn2) {
     const int b = blockIdx.z;
@@ -98,29 +102,33 @@ __global__ void add_correction(int64_t total, const cx<float> *D, cx<double> *X,
     }
 }
 
-// Residue-weighted sum (a8): Y = sum_b W_b X_b, real part only when real_out.
-// The sum over systems is taken in a fixed order per element (no atomics).
+// Residue-weighted sum (a8) per instance z: Y = sum_sys W_sys X[z, sys], real part
+// only when y_real.  The sum over systems is taken in a fixed order per element.
 __global__ void accumulate(int n, int kc, int nsys, const cx<double> *__restrict__ X, int64_t stride,
-                           DenseSystems sys, int real_out, double *__restrict__ Y, int64_t ldy) {
+                           DenseSystems sys, DenseIO io) {
+    const int z = blockIdx.z;
+    double *Y = io.Y + (int64_t)z * io.ystride * (io.y_real ? 1 : 2);
     const int64_t total = (int64_t)n * kc;
     for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
          idx += (int64_t)gridDim.x * blockDim.x) {
-        const int i = (int)(idx / kc), j = (int)(idx % kc);
+        const int64_t i = idx / kc, j = idx % kc;
         cx<double> acc = {0.0, 0.0};
         for (int b = 0; b < nsys; ++b) {
             const cx<double> w = {sys.w_re[b], sys.w_im[b]};
-            acc = acc + w * X[(int64_t)b * stride + idx];
+            acc = acc + w * X[((int64_t)z * nsys + b) * stride + idx];
         }
-        if (real_out) Y[i * ldy + j] = acc.re;
+        if (io.y_real) Y[i * io.ldy + j] = acc.re;
         else {
-            Y[2 * (i * ldy + j)] = acc.re;
-            Y[2 * (i * ldy + j) + 1] = acc.im;
+            Y[2 * (i * io.ldy + j)] = acc.re;
+            Y[2 * (i * io.ldy + j) + 1] = acc.im;
         }
     }
 }
 
-// sum of |A_ij|^2 (binary64) into *out
-__global__ void frob2(int n, const double *__restrict__ A, int64_t lda, int cplx, double *out) {
+// sum of |A_ij|^2 (binary64) of instance z into out[z]
+__global__ void frob2(int n, const double *__restrict__ A, int64_t lda, int64_t astride, int cplx, double *out) {
+    A += (int64_t)blockIdx.z * astride * (cplx ? 2 : 1);
+    out += blockIdx.z;
     double acc = 0.0;
     const int64_t total = (int64_t)n * n;
     for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
@@ -187,7 +195,7 @@ static cudaError_t lu_blocked(int n, int batch, cx<T> *F, cudaStream_t st, Profi
             dim3 g((rest + 63) / 64, (rest + 63) / 64, batch);
             cgemm<T, cx<T>, false, false><<<g, 256, 0, st>>>(
                 rest, rest, nb, cx<T>{T(-1), T(0)}, T(1), diag + (int64_t)nb * n, n, bs, diag + nb, n, bs,
-                diag + (int64_t)nb * n + nb, n, bs);
+                diag + (int64_t)nb * n + nb, n, bs, 1);
             return cudaGetLastError();
         }));
     }
@@ -220,11 +228,11 @@ static cudaError_t lu_solve(int n, int kc, int batch, const cx<T> *F, int64_t fs
                 if (!conj)  // X[p+nb:] -= L[p+nb:, p:p+nb] X[p:p+nb]
                     cgemm<T, cx<T>, false, false><<<g, 256, 0, st>>>(rest, kc, nb, cx<T>{T(-1), T(0)}, T(1),
                                                                      dg + (int64_t)nb * n, n, fstride, xp, kc, xstride,
-                                                                     xp + (int64_t)nb * kc, kc, xstride);
+                                                                     xp + (int64_t)nb * kc, kc, xstride, 1);
                 else  // X[p+nb:] -= (U[p:p+nb, p+nb:])^H X[p:p+nb]
                     cgemm<T, cx<T>, true, false><<<g, 256, 0, st>>>(rest, kc, nb, cx<T>{T(-1), T(0)}, T(1), dg + nb, n,
                                                                     fstride, xp, kc, xstride, xp + (int64_t)nb * kc, kc,
-                                                                    xstride);
+                                                                    xstride, 1);
             }
         }
         // backward sweep
@@ -239,11 +247,11 @@ static cudaError_t lu_solve(int n, int kc, int batch, const cx<T> *F, int64_t fs
                 dim3 g(cb, (p + 63) / 64, batch);
                 if (!conj)  // X[:p] -= U[:p, p:p+nb] X[p:p+nb]
                     cgemm<T, cx<T>, false, false><<<g, 256, 0, st>>>(p, kc, nb, cx<T>{T(-1), T(0)}, T(1), F + p, n,
-                                                                     fstride, xp, kc, xstride, X, kc, xstride);
+                                                                     fstride, xp, kc, xstride, X, kc, xstride, 1);
                 else  // X[:p] -= (L[p:p+nb, :p])^H X[p:p+nb]
                     cgemm<T, cx<T>, true, false><<<g, 256, 0, st>>>(p, kc, nb, cx<T>{T(-1), T(0)}, T(1),
                                                                     F + (int64_t)p * n, n, fstride, xp, kc, xstride, X,
-                                                                    kc, xstride);
+                                                                    kc, xstride, 1);
             }
         }
         return cudaGetLastError();
@@ -252,21 +260,50 @@ static cudaError_t lu_solve(int n, int kc, int batch, const cx<T> *F, int64_t fs
 
 // ------------------------------------------------------------------ driver
 
-size_t dense_workspace_bytes(const DenseGeom &g) {
-    const size_t nn = (size_t)g.n * g.n, nk = (size_t)g.n * g.kc;
-    const size_t fb = g.mixed ? sizeof(cx<float>) : sizeof(cx<double>);
-    size_t bytes = g.npairs * nn * fb;                                  // factors
-    bytes += (size_t)g.nsys * nk * sizeof(cx<double>);                  // X (binary64)
-    if (g.mixed) bytes += (size_t)g.nsys * nk * (sizeof(cx<double>) + sizeof(cx<float>));  // R, correction
-    bytes += 4096 + 64 * sizeof(double) * 4;
-    return bytes + 8 * 256;
-}
-
+// Workspace = factor part [amax, umax, factors] + solve part [norms, X binary64,
+// R binary64 and D binary32 (mixed)].  The factor part depends only on A, t, c and
+// the poles and can be kept for later right-hand sides.
+struct DenseLayout {
+    size_t amax, umax, F, factor_total;  // factor part
+    size_t rn2, xn2, an2, X, R, D, solve_total;  // solve part (offsets from its own base)
+};
 static inline size_t align_up(size_t x) { return (x + 255) & ~size_t(255); }
 
+static DenseLayout dense_layout(const DenseGeom &g) {
+    DenseLayout L{};
+    const size_t nn = (size_t)g.n * g.n, nk = (size_t)g.n * g.kc;
+    const size_t npz = (size_t)g.ninst * g.npairs, nsz = (size_t)g.ninst * g.nsys;
+    size_t off = 0;
+    L.amax = off; off += align_up(npz * sizeof(unsigned));
+    L.umax = off; off += align_up(npz * sizeof(unsigned));
+    L.F = off; off += align_up(npz * nn * (g.mixed ? sizeof(cx<float>) : sizeof(cx<double>)));
+    L.factor_total = off;
+    off = 0;
+    L.rn2 = off; off += align_up(nsz * sizeof(double));
+    L.xn2 = off; off += align_up(nsz * sizeof(double));
+    L.an2 = off; off += align_up((size_t)g.ninst * sizeof(double));
+    L.X = off; off += align_up(nsz * nk * sizeof(cx<double>));
+    L.R = off;
+    L.D = off;
+    if (g.mixed) {
+        off += align_up(nsz * nk * sizeof(cx<double>));
+        L.D = off;
+        off += align_up(nsz * nk * sizeof(cx<float>));
+    }
+    L.solve_total = off;
+    return L;
+}
+
+size_t dense_factor_bytes(const DenseGeom &g) { return dense_layout(g).factor_total; }
+size_t dense_solve_bytes(const DenseGeom &g) { return dense_layout(g).solve_total; }
+size_t dense_workspace_bytes(const DenseGeom &g) {
+    const DenseLayout L = dense_layout(g);
+    return L.factor_total + L.solve_total;
+}
+
 template <class T>
-static cudaError_t factor_pairs(const DenseGeom &g, const double *A, int64_t lda, const DenseSystems &sys,
-                                cx<T> *F, unsigned *amax, unsigned *umax, cudaStream_t st, Profiler &prof) {
+static cudaError_t factor_pairs(const DenseGeom &g, const DenseIO &io, const DenseSystems &sys, cx<T> *F,
+                                unsigned *amax, unsigned *umax, cudaStream_t st, Profiler &prof) {
     // pair s uses system 2s (complex A) or s (real data); both carry the Im(theta) > 0 member
     DenseSystems pairs = sys;
     for (int s = 0; s < g.npairs; ++s) {
@@ -274,15 +311,17 @@ static cudaError_t factor_pairs(const DenseGeom &g, const double *A, int64_t lda
         pairs.th_re[s] = sys.th_re[b];
         pairs.th_im[s] = sys.th_im[b];
     }
-    EXPM_TRY(cudaMemsetAsync(amax, 0, sizeof(unsigned) * 2 * DENSE_MAXSYS, st));
+    const int batch = g.ninst * g.npairs;
+    EXPM_TRY(cudaMemsetAsync(amax, 0, sizeof(unsigned) * batch, st));
+    EXPM_TRY(cudaMemsetAsync(umax, 0, sizeof(unsigned) * batch, st));
     EXPM_TRY(prof.timed(sizeof(T) == 8 ? "form_shifted<f64>" : "form_shifted<f32>", st, [&] {
-        form_shifted<T><<<dim3(grid1d((int64_t)g.n * g.n), 1, g.npairs), 256, 0, st>>>(
-            g.n, A, (int)lda, g.complex_a, g.t, pairs, F, amax);
+        form_shifted<T><<<dim3(grid1d((int64_t)g.n * g.n), 1, batch), 256, 0, st>>>(
+            g.n, io.A, (int)io.lda, io.astride, g.complex_a, g.npairs, g.t, pairs, F, amax);
         return cudaGetLastError();
     }));
-    EXPM_TRY(lu_blocked<T>(g.n, g.npairs, F, st, prof));
-    max_abs_upper<T><<<dim3(grid1d((int64_t)g.n * g.n), 1, g.npairs), 256, 0, st>>>(g.n, F, g.n,
-                                                                                     (int64_t)g.n * g.n, umax);
+    EXPM_TRY(lu_blocked<T>(g.n, batch, F, st, prof));
+    max_abs_upper<T><<<dim3(grid1d((int64_t)g.n * g.n), 1, batch), 256, 0, st>>>(g.n, F, g.n, (int64_t)g.n * g.n,
+                                                                                  umax);
     return cudaGetLastError();
 }
 
@@ -290,109 +329,143 @@ template <class T>
 static cudaError_t solve_systems(const DenseGeom &g, const cx<T> *F, cx<T> *X, int64_t xstride, cudaStream_t st,
                                  Profiler &prof) {
     const int64_t fs = (int64_t)g.n * g.n;
-    if (!g.complex_a) return lu_solve<T>(g.n, g.kc, g.npairs, F, fs, false, X, xstride, st, prof);
-    // systems 2s (theta) and 2s+1 (conj theta) share factor s: run the two sweeps with
-    // batch stride 2*xstride over the even and the odd systems
-    EXPM_TRY(lu_solve<T>(g.n, g.kc, g.npairs, F, fs, false, X, 2 * xstride, st, prof));
-    return lu_solve<T>(g.n, g.kc, g.npairs, F, fs, true, X + xstride, 2 * xstride, st, prof);
+    const int batch = g.ninst * g.npairs;
+    if (!g.complex_a) return lu_solve<T>(g.n, g.kc, batch, F, fs, false, X, xstride, st, prof);
+    // systems 2s (theta) and 2s+1 (conj theta) of every instance share factor s: the
+    // even and the odd systems each form a batch with stride 2*xstride
+    EXPM_TRY(lu_solve<T>(g.n, g.kc, batch, F, fs, false, X, 2 * xstride, st, prof));
+    return lu_solve<T>(g.n, g.kc, batch, F, fs, true, X + xstride, 2 * xstride, st, prof);
 }
 
-cudaError_t dense_run(const DenseGeom &g, const double *A, int64_t lda, const double *V, int64_t ldv, int v_cplx,
-                      double *Y, int64_t ldy, const DenseSystems &sys, void *work, cudaStream_t st, Profiler &prof,
-                      DenseResult *res) {
+cudaError_t dense_factor(const DenseGeom &g, const DenseIO &io, const DenseSystems &sys, void *fwork, cudaStream_t st,
+                         Profiler &prof) {
+    const DenseLayout L = dense_layout(g);
+    unsigned char *p = (unsigned char *)fwork;
+    unsigned *amax = (unsigned *)(p + L.amax);
+    unsigned *umax = (unsigned *)(p + L.umax);
+    if (g.mixed) return factor_pairs<float>(g, io, sys, (cx<float> *)(p + L.F), amax, umax, st, prof);
+    return factor_pairs<double>(g, io, sys, (cx<double> *)(p + L.F), amax, umax, st, prof);
+}
+
+cudaError_t dense_growth(const DenseGeom &g, const void *fwork, cudaStream_t st, DenseResult *res) {
+    const DenseLayout L = dense_layout(g);
+    const unsigned char *p = (const unsigned char *)fwork;
+    const int npz = g.ninst * g.npairs;
+    std::vector<unsigned> hm(2 * (size_t)npz);
+    EXPM_TRY(cudaMemcpyAsync(hm.data(), p + L.amax, sizeof(unsigned) * npz, cudaMemcpyDeviceToHost, st));
+    EXPM_TRY(cudaMemcpyAsync(hm.data() + npz, p + L.umax, sizeof(unsigned) * npz, cudaMemcpyDeviceToHost, st));
+    EXPM_TRY(cudaStreamSynchronize(st));
+    res->growth_max = 0.0;
+    res->inst_growth.assign(g.ninst, 0.0);
+    for (int z = 0; z < npz; ++z) {
+        float a, u;
+        std::memcpy(&a, &hm[z], 4);
+        std::memcpy(&u, &hm[npz + z], 4);
+        if (a > 0) {
+            const double gz = (double)u / (double)a;
+            res->growth_max = std::max(res->growth_max, gz);
+            res->inst_growth[z / g.npairs] = std::max(res->inst_growth[z / g.npairs], gz);
+        }
+    }
+    return cudaSuccess;
+}
+
+cudaError_t dense_solve(const DenseGeom &g, const DenseIO &io, const DenseSystems &sys, const void *fwork, void *swork,
+                        cudaStream_t st, Profiler &prof, DenseResult *res) {
     const int64_t nk = (int64_t)g.n * g.kc;
-    unsigned char *p = (unsigned char *)work;
-    unsigned *amax = (unsigned *)p;
-    unsigned *umax = amax + DENSE_MAXSYS;
-    double *rn2 = (double *)(p + 1024);
-    double *xn2 = rn2 + DENSE_MAXSYS;
-    p += align_up(4096);
-    const size_t fb = g.mixed ? sizeof(cx<float>) : sizeof(cx<double>);
-    void *F = p;
-    p += align_up((size_t)g.npairs * g.n * g.n * fb);
-    cx<double> *X = (cx<double> *)p;
-    p += align_up((size_t)g.nsys * nk * sizeof(cx<double>));
+    const DenseLayout L = dense_layout(g);
+    const void *F = (const unsigned char *)fwork + L.F;
+    unsigned char *p = (unsigned char *)swork;
+    double *rn2 = (double *)(p + L.rn2);
+    double *xn2 = (double *)(p + L.xn2);
+    double *an2 = (double *)(p + L.an2);
+    cx<double> *X = (cx<double> *)(p + L.X);
+    const int nsz = g.ninst * g.nsys;
     const unsigned gx = grid1d(nk);
     res->iters = 0;
     res->resid_rel_max = 0.0;
+    res->inst_iters.assign(g.ninst, 0);
+    res->inst_resid.assign(g.ninst, 0.0);
     if (!g.mixed) {
-        EXPM_TRY(factor_pairs<double>(g, A, lda, sys, (cx<double> *)F, amax, umax, st, prof));
-        load_rhs<double><<<dim3(gx, 1, g.nsys), 256, 0, st>>>(g.n, g.kc, V, ldv, v_cplx, X, nk);
+        load_rhs<double><<<dim3(gx, 1, nsz), 256, 0, st>>>(g.n, g.kc, io, g.nsys, X, nk);
         EXPM_TRY(cudaGetLastError());
-        EXPM_TRY(solve_systems<double>(g, (cx<double> *)F, X, nk, st, prof));
+        EXPM_TRY(solve_systems<double>(g, (const cx<double> *)F, X, nk, st, prof));
     } else {
-        cx<double> *R = (cx<double> *)p;
-        p += align_up((size_t)g.nsys * nk * sizeof(cx<double>));
-        cx<float> *D = (cx<float> *)p;
-        EXPM_TRY(factor_pairs<float>(g, A, lda, sys, (cx<float> *)F, amax, umax, st, prof));
-        EXPM_TRY(cudaMemsetAsync(X, 0, (size_t)g.nsys * nk * sizeof(cx<double>), st));
-        std::vector<double> h(2 * DENSE_MAXSYS);
-        // ||tA||_F for the relative residual of the stopping test
-        EXPM_TRY(cudaMemsetAsync(rn2, 0, sizeof(double), st));
-        frob2<<<grid1d((int64_t)g.n * g.n), 256, 0, st>>>(g.n, A, lda, g.complex_a, rn2);
+        cx<double> *R = (cx<double> *)(p + L.R);
+        cx<float> *D = (cx<float> *)(p + L.D);
+        EXPM_TRY(cudaMemsetAsync(X, 0, (size_t)nsz * nk * sizeof(cx<double>), st));
+        std::vector<double> h(2 * (size_t)nsz), an(g.ninst);
+        // ||tA||_F of every instance for the relative residual of the stopping test
+        EXPM_TRY(cudaMemsetAsync(an2, 0, sizeof(double) * g.ninst, st));
+        frob2<<<dim3(grid1d((int64_t)g.n * g.n), 1, g.ninst), 256, 0, st>>>(g.n, io.A, io.lda, io.astride,
+                                                                           g.complex_a, an2);
         EXPM_TRY(cudaGetLastError());
-        EXPM_TRY(cudaMemcpyAsync(h.data(), rn2, sizeof(double), cudaMemcpyDeviceToHost, st));
+        EXPM_TRY(cudaMemcpyAsync(an.data(), an2, sizeof(double) * g.ninst, cudaMemcpyDeviceToHost, st));
         EXPM_TRY(cudaStreamSynchronize(st));
-        const double anorm = std::sqrt(h[0]) * std::fabs(g.t);
         // it = 0: initial solve; it = 1 .. max_refine: refinement sweeps; the residual
         // of the current X is checked before every sweep and once after the last one
         for (int it = 0;; ++it) {
             // R = V - (tA - cI + theta I) X, binary64
-            residual_diag<<<dim3(gx, 1, g.nsys), 256, 0, st>>>(g.n, g.kc, V, ldv, v_cplx, X, R, nk, sys);
+            residual_diag<<<dim3(gx, 1, nsz), 256, 0, st>>>(g.n, g.kc, io, g.nsys, X, R, nk, sys);
             EXPM_TRY(cudaGetLastError());
             if (it > 0) {
                 EXPM_TRY(prof.timed("residual_gemm<f64>", st, [&] {
-                    dim3 gg((g.kc + 63) / 64, (g.n + 63) / 64, g.nsys);
+                    dim3 gg((g.kc + 63) / 64, (g.n + 63) / 64, nsz);
                     if (g.complex_a)
                         cgemm<double, cx<double>, false, false><<<gg, 256, 0, st>>>(
-                            g.n, g.kc, g.n, cx<double>{-g.t, 0.0}, 1.0, (const cx<double> *)A, (int)lda, 0, X, g.kc, nk,
-                            R, g.kc, nk);
+                            g.n, g.kc, g.n, cx<double>{-g.t, 0.0}, 1.0, (const cx<double> *)io.A, (int)io.lda,
+                            io.astride, X, g.kc, nk, R, g.kc, nk, g.nsys);
                     else
-                        cgemm<double, double, false, false><<<gg, 256, 0, st>>>(g.n, g.kc, g.n, cx<double>{-g.t, 0.0}, 1.0,
-                                                                                A, (int)lda, 0, X, g.kc, nk, R, g.kc, nk);
+                        cgemm<double, double, false, false><<<gg, 256, 0, st>>>(
+                            g.n, g.kc, g.n, cx<double>{-g.t, 0.0}, 1.0, io.A, (int)io.lda, io.astride, X, g.kc, nk, R,
+                            g.kc, nk, g.nsys);
                     return cudaGetLastError();
                 }));
             }
-            EXPM_TRY(cudaMemsetAsync(rn2, 0, sizeof(double) * 2 * DENSE_MAXSYS, st));
-            demote_and_norms<<<dim3(gx, 1, g.nsys), 256, 0, st>>>(nk, R, X, D, nk, rn2, xn2);
+            EXPM_TRY(cudaMemsetAsync(rn2, 0, sizeof(double) * nsz, st));
+            EXPM_TRY(cudaMemsetAsync(xn2, 0, sizeof(double) * nsz, st));
+            demote_and_norms<<<dim3(gx, 1, nsz), 256, 0, st>>>(nk, R, X, D, nk, rn2, xn2);
             EXPM_TRY(cudaGetLastError());
             if (it > 0) {
-                EXPM_TRY(cudaMemcpyAsync(h.data(), rn2, sizeof(double) * 2 * DENSE_MAXSYS, cudaMemcpyDeviceToHost, st));
+                EXPM_TRY(cudaMemcpyAsync(h.data(), rn2, sizeof(double) * nsz, cudaMemcpyDeviceToHost, st));
+                EXPM_TRY(cudaMemcpyAsync(h.data() + nsz, xn2, sizeof(double) * nsz, cudaMemcpyDeviceToHost, st));
                 EXPM_TRY(cudaStreamSynchronize(st));
                 bool done = true;
                 double worst = 0.0;
-                for (int b = 0; b < g.nsys; ++b) {
+                std::fill(res->inst_resid.begin(), res->inst_resid.end(), 0.0);  // this sweep's residuals
+                for (int z = 0; z < nsz; ++z) {
+                    const int inst = z / g.nsys, b = z % g.nsys;
                     const double shift = std::hypot(sys.th_re[b] - sys.cshift, sys.th_im[b]);
-                    const double den = (anorm + shift) * std::sqrt(h[DENSE_MAXSYS + b]);
-                    const double rel = den > 0 ? std::sqrt(h[b]) / den : 0.0;
+                    const double den = (std::sqrt(an[inst]) * std::fabs(g.t) + shift) * std::sqrt(h[nsz + z]);
+                    const double rel = den > 0 ? std::sqrt(h[z]) / den : 0.0;
                     worst = std::max(worst, rel);
+                    res->inst_resid[inst] = std::max(res->inst_resid[inst], rel);
                     if (!(rel <= g.tol)) done = false;
                 }
                 res->resid_rel_max = worst;
                 res->iters = it - 1;
+                for (int i = 0; i < g.ninst; ++i) res->inst_iters[i] = it - 1;
                 if (done || it > g.max_refine) break;
             }
             EXPM_TRY(solve_systems<float>(g, (const cx<float> *)F, D, nk, st, prof));
-            add_correction<<<dim3(gx, 1, g.nsys), 256, 0, st>>>(nk, D, X, nk);
+            add_correction<<<dim3(gx, 1, nsz), 256, 0, st>>>(nk, D, X, nk);
             EXPM_TRY(cudaGetLastError());
         }
     }
     EXPM_TRY(prof.timed("accumulate", st, [&] {
-        accumulate<<<grid1d(nk), 256, 0, st>>>(g.n, g.kc, g.nsys, X, nk, sys, g.complex_a ? 0 : 1, Y, ldy);
+        accumulate<<<dim3(gx, 1, g.ninst), 256, 0, st>>>(g.n, g.kc, g.nsys, X, nk, sys, io);
         return cudaGetLastError();
     }));
-    // growth factors
-    std::vector<unsigned> hm(2 * DENSE_MAXSYS);
-    EXPM_TRY(cudaMemcpyAsync(hm.data(), amax, sizeof(unsigned) * 2 * DENSE_MAXSYS, cudaMemcpyDeviceToHost, st));
-    EXPM_TRY(cudaStreamSynchronize(st));
-    res->growth_max = 0.0;
-    for (int s = 0; s < g.npairs; ++s) {
-        float a, u;
-        std::memcpy(&a, &hm[s], 4);
-        std::memcpy(&u, &hm[DENSE_MAXSYS + s], 4);
-        if (a > 0) res->growth_max = std::max(res->growth_max, (double)u / (double)a);
-    }
     return cudaSuccess;
+}
+
+cudaError_t dense_run(const DenseGeom &g, const DenseIO &io, const DenseSystems &sys, void *work, cudaStream_t st,
+                      Profiler &prof, DenseResult *res) {
+    const DenseLayout L = dense_layout(g);
+    unsigned char *p = (unsigned char *)work;
+    EXPM_TRY(dense_factor(g, io, sys, p, st, prof));
+    EXPM_TRY(dense_solve(g, io, sys, p, p + L.factor_total, st, prof, res));
+    return dense_growth(g, p, st, res);
 }
 
 }  // namespace expm

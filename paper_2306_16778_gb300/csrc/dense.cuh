@@ -4,6 +4,7 @@
 #include <stdint.h>
 
 #include <algorithm>
+#include <vector>
 
 namespace expm {
 
@@ -20,11 +21,14 @@ struct DenseSystems {
     double cshift;                                    // c
 };
 
+// A batch of `ninst` problems of the same (padded) order n.  Instance i uses
+// A + i*astride, V + i*vstride, Y + i*ystride (strides in elements of each array).
 struct DenseGeom {
     int n;          // matrix order
     int kc;         // complex right-hand-side columns solved per system
-    int npairs;     // factorizations
-    int nsys;       // solved systems
+    int ninst;      // instances
+    int npairs;     // factorizations per instance
+    int nsys;       // solved systems per instance
     int complex_a;  // A complex Hermitian (else real symmetric)
     int mixed;      // binary32 factorization + binary64 refinement
     double t;       // time factor
@@ -32,15 +36,38 @@ struct DenseGeom {
     int max_refine;
 };
 
-struct DenseResult {
-    int iters;
-    double resid_rel_max;
-    double growth_max;
+struct DenseIO {
+    const double *A;
+    int64_t lda, astride;
+    const double *V;
+    int64_t ldv, vstride;  // in loaded elements (real doubles, or complex when v_cplx)
+    int v_cplx;
+    double *Y;
+    int64_t ldy, ystride;  // in stored elements (real when y_real, else complex)
+    int y_real;
 };
 
-size_t dense_workspace_bytes(const DenseGeom &g);
-cudaError_t dense_run(const DenseGeom &g, const double *A, int64_t lda, const double *V, int64_t ldv, int v_cplx,
-                      double *Y, int64_t ldy, const DenseSystems &sys, void *work, cudaStream_t st, Profiler &prof,
-                      DenseResult *res);
+struct DenseResult {
+    int iters;                   // refinement sweeps (max over the batch)
+    double resid_rel_max;        // worst final relative residual
+    double growth_max;           // worst growth factor
+    std::vector<int> inst_iters;         // per instance
+    std::vector<double> inst_resid;      // per instance
+    std::vector<double> inst_growth;     // per instance
+};
+
+size_t dense_workspace_bytes(const DenseGeom &g);  // one call (factor + solve)
+size_t dense_factor_bytes(const DenseGeom &g);     // reusable factor part
+size_t dense_solve_bytes(const DenseGeom &g);      // per-call solve part
+// factor part: tA - cI + theta I per pair, its unpivoted LU and growth data
+cudaError_t dense_factor(const DenseGeom &g, const DenseIO &io, const DenseSystems &sys, void *fwork, cudaStream_t st,
+                         Profiler &prof);
+// solve part (triangular solves, refinement, residue sum) with factors from dense_factor
+cudaError_t dense_solve(const DenseGeom &g, const DenseIO &io, const DenseSystems &sys, const void *fwork, void *swork,
+                        cudaStream_t st, Profiler &prof, DenseResult *res);
+// growth factors of a factor part (synchronises st)
+cudaError_t dense_growth(const DenseGeom &g, const void *fwork, cudaStream_t st, DenseResult *res);
+cudaError_t dense_run(const DenseGeom &g, const DenseIO &io, const DenseSystems &sys, void *work, cudaStream_t st,
+                      Profiler &prof, DenseResult *res);
 
 }  // namespace expm

@@ -40,10 +40,13 @@ template <class T> EXPM_D T cabs2(cx<T> a) { return a.re * a.re + a.im * a.im; }
 // Out[s] (n x n, ld n, precision T) = t A - c I + theta_s I.  A is real (a_cplx = 0)
 // or complex, binary64, leading dimension lda.  amax[s] receives max |Out[s]_ij|
 // (as the bit pattern of a non-negative float, atomicMax-ed).
+// Batch z = instance * npairs + pair; instance i reads A + i * astride elements.
 template <class T>
-__global__ void form_shifted(int n, const double *__restrict__ A, int lda, int a_cplx, double t, DenseSystems ps,
-                             cx<T> *__restrict__ Out, unsigned *amax) {
-    const int s = blockIdx.z;
+__global__ void form_shifted(int n, const double *__restrict__ A, int lda, int64_t astride, int a_cplx, int npairs,
+                             double t, DenseSystems ps, cx<T> *__restrict__ Out, unsigned *amax) {
+    const int z = blockIdx.z;
+    const int s = z % npairs;
+    A += (int64_t)(z / npairs) * astride * (a_cplx ? 2 : 1);
     const int64_t total = (int64_t)n * n;
     float local = 0.f;
     for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
@@ -61,11 +64,11 @@ __global__ void form_shifted(int n, const double *__restrict__ A, int lda, int a
             re += ps.th_re[s] - ps.cshift;
             im += ps.th_im[s];
         }
-        Out[(int64_t)s * total + idx] = {(T)re, (T)im};
+        Out[(int64_t)z * total + idx] = {(T)re, (T)im};
         local = fmaxf(local, (float)sqrt(re * re + im * im));
     }
     for (int o = 16; o > 0; o >>= 1) local = fmaxf(local, __shfl_xor_sync(0xffffffffu, local, o));
-    if ((threadIdx.x & 31) == 0) atomicMax(amax + s, __float_as_uint(local));
+    if ((threadIdx.x & 31) == 0) atomicMax(amax + z, __float_as_uint(local));
 }
 
 // ------------------------------------------------------------------ lu_diag
@@ -167,14 +170,15 @@ __global__ void __launch_bounds__(64) trsm_right_upper(int nb, int nrows, const 
 template <class T> EXPM_D cx<T> as_cx(cx<T> v) { return v; }
 template <class T> EXPM_D cx<T> as_cx(T v) { return {v, T(0)}; }
 
+// Batch z uses A[z / adiv] (adiv > 1 shares one A among consecutive batches).
 template <class T, class AE, bool CONJ_A, bool CONJ_B>
 __global__ void __launch_bounds__(256) cgemm(int m, int n, int K, cx<T> alpha, T beta, const AE *__restrict__ A,
                                              int lda, int64_t sA, const cx<T> *__restrict__ B, int ldb, int64_t sB,
-                                             cx<T> *__restrict__ C, int ldc, int64_t sC) {
+                                             cx<T> *__restrict__ C, int ldc, int64_t sC, int adiv) {
     constexpr int BM = 64, BN = 64, BK = 16;
     __shared__ cx<T> As[BK][BM + 1];
     __shared__ cx<T> Bs[BK][BN + 1];
-    const AE *a = A + (int64_t)blockIdx.z * sA;
+    const AE *a = A + (int64_t)(blockIdx.z / adiv) * sA;
     const cx<T> *b = B + (int64_t)blockIdx.z * sB;
     cx<T> *c = C + (int64_t)blockIdx.z * sC;
     const int i0 = blockIdx.y * BM, j0 = blockIdx.x * BN;

@@ -25,7 +25,8 @@
 //                        reduction in shared memory.
 //   K3 tri_block_solve   one thread per (block, column, system): forward and back
 //                        substitution with the separator values as boundary data;
-//                        Re(W_s x_s) summed over the systems by a shuffle tree.
+//                        Re(W_s x_s) summed over the systems by a reduce-scatter
+//                        across the system lanes, one chunk of rows at a time.
 //   K4 tri_finish        float-float only: the float pairs of Y to binary64.
 //
 // No pivoting: for Im(theta) != 0, (-i sign(Im theta)) M has Hermitian part
@@ -81,13 +82,16 @@ template <> struct Store<f32x2> {
 };
 
 // ------------------------------------------------------------------ K0
+// Either part may be skipped by passing null outputs (dP/eP, or VP).
 template <class R>
 __global__ void tri_prep(TriGeom g, const double *__restrict__ d, const double *__restrict__ e,
                          const double *__restrict__ V, R *__restrict__ dP, R *__restrict__ eP, R *__restrict__ VP) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < g.N; i += stride) {
-        dP[i] = Store<R>::split(g.t * d[i] - g.cshift);
-        eP[i] = Store<R>::split(i + 1 < g.N ? g.t * e[i] : 0.0);
+    if (dP != nullptr) {
+        for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < g.N; i += stride) {
+            dP[i] = Store<R>::split(g.t * d[i] - g.cshift);
+            eP[i] = Store<R>::split(i + 1 < g.N ? g.t * e[i] : 0.0);
+        }
     }
     if (VP != nullptr) {
         const int64_t nv = g.N * g.Rc;
@@ -139,27 +143,36 @@ __global__ void __launch_bounds__(128) tri_block_factor(TriGeom g, const R *__re
         cprev = cp;
         hprev = h;
     }
-    // backward: u = M_b^{-1} eps_first, w = M_b^{-1} eps_last
+    // backward: u = M_b^{-1} eps_first, w = M_b^{-1} eps_last.  The chain per row is
+    // short, so the (h, c') of the next TRI_PF rows are kept in flight.
     const int64_t last = first + len - 1;
     cx<R> un = U[last], wn = F[2 * last + 1];
     const cx<R> uL = un, wL = wn;
     W[last] = wn;
-    cx<R> hnext = cxz<R>(), cnext = cxz<R>();
-    if (len > 1) {
-        hnext = U[last - 1];
-        cnext = F[2 * (last - 1)];
+    cx<R> hq[TRI_PF], cq[TRI_PF];
+#pragma unroll
+    for (int r = 0; r < TRI_PF; ++r) {
+        const int i = len - 2 - r;
+        hq[r] = (i >= 0) ? U[first + i] : cxz<R>();
+        cq[r] = (i >= 0) ? F[2 * (first + i)] : cxz<R>();
     }
-    for (int i = len - 2; i >= 0; --i) {
-        const int64_t q = first + i;
-        const cx<R> h = hnext, cp = cnext;
-        if (i > 0) {
-            hnext = U[q - 1];
-            cnext = F[2 * (q - 1)];
+    for (int i0 = len - 2; i0 >= 0; i0 -= TRI_PF) {
+#pragma unroll
+        for (int r = 0; r < TRI_PF; ++r) {
+            const int i = i0 - r;
+            if (i >= 0) {
+                const cx<R> h = hq[r], cp = cq[r];
+                const int ipf = i - TRI_PF;  // refill this slot for the next round
+                if (ipf >= 0) {
+                    hq[r] = U[first + ipf];
+                    cq[r] = F[2 * (first + ipf)];
+                }
+                un = csub_mul(h, cp, un);
+                wn = -(cp * wn);
+                U[first + i] = un;
+                W[first + i] = wn;
+            }
         }
-        un = h - cp * un;
-        wn = -(cp * wn);
-        U[q] = un;
-        W[q] = wn;
     }
     cx<R> *SP = spk + ((int64_t)s * g.P + b) * 4;
     SP[0] = un;  // u_b[first]
@@ -286,12 +299,13 @@ __global__ void __launch_bounds__(1024) tri_reduced_cr(TriGeom g, const R *__res
 // One thread per (block, column, system).  The systems of one (block, column) sit in
 // LG consecutive lanes (LG = power of two >= S, <= 32); each lane runs the forward
 // and back substitution of its system, and Re(W_s x_s) is summed over the LG lanes
-// by a shuffle tree in a fixed order (the result does not depend on scheduling).
+// by a reduce-scatter over chunks of LG rows in a fixed order (the result does not
+// depend on scheduling).
 // The next row's loads are issued one iteration ahead.  Output: binary64 Y, or for
 // float-float the unrounded pair (hi, lo) stored in Y's 8 bytes, finished by K4.
-template <class T> EXPM_D T shfl_down(unsigned mask, T v, int off) { return __shfl_down_sync(mask, v, off); }
-template <> EXPM_D f32x2 shfl_down<f32x2>(unsigned mask, f32x2 v, int off) {
-    return {__shfl_down_sync(mask, v.hi, off), __shfl_down_sync(mask, v.lo, off)};
+template <class T> EXPM_D T shfl_xor(unsigned mask, T v, int off) { return __shfl_xor_sync(mask, v, off); }
+template <> EXPM_D f32x2 shfl_xor<f32x2>(unsigned mask, f32x2 v, int off) {
+    return {__shfl_xor_sync(mask, v.hi, off), __shfl_xor_sync(mask, v.lo, off)};
 }
 template <class R> EXPM_D void store_out(double *Y, int64_t idx, R v);
 template <> EXPM_D void store_out<double>(double *Y, int64_t idx, double v) { Y[idx] = v; }
@@ -299,13 +313,28 @@ template <> EXPM_D void store_out<f32x2>(double *Y, int64_t idx, f32x2 v) {
     reinterpret_cast<f32x2 *>(Y)[idx] = v;
 }
 
-template <class R>
+// Reduce-scatter of LG values per lane over the LG lanes of a group by recursive
+// halving: afterwards lane l holds the sum over the group of everyone's v[l] in v[0].
+// LG-1 additions per lane for LG rows (instead of log2(LG) per row for a per-row tree).
+template <int LG, class R> EXPM_D void reduce_scatter(unsigned gmask, int sl, R (&v)[LG]) {
+#pragma unroll
+    for (int off = LG / 2; off > 0; off >>= 1) {
+        const bool upper = (sl & off) != 0;
+#pragma unroll
+        for (int idx = 0; idx < off; ++idx) {
+            const R send = upper ? v[idx] : v[idx + off];
+            const R keep = upper ? v[idx + off] : v[idx];
+            v[idx] = keep + shfl_xor(gmask, send, off);
+        }
+    }
+}
+
+template <class R, int LG>
 __global__ void __launch_bounds__(128) tri_block_solve(TriGeom g, const R *__restrict__ eP,
                                                        const R *__restrict__ VP, TriPoles ps,
                                                        const cx<R> *__restrict__ fact,
                                                        const cx<R> *__restrict__ sigma,
                                                        cx<R> *__restrict__ scr, double *__restrict__ Y) {
-    const int LG = g.LG;
     const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int sl = (int)(tid % LG);
     const int64_t bj = tid / LG;
@@ -345,34 +374,43 @@ __global__ void __launch_bounds__(128) tri_block_solve(TriGeom g, const R *__res
             gn = F[2 * (q + 1) + 1];
             en = eP[q];
         }
-        cx<R> rhs = {vq, RealOps<R>::zero()};
+        cx<R> rhs = (i > 0) ? real_minus_scaled(vq, elq, dp) : cx<R>{vq, RealOps<R>::zero()};
         if (i == 0 && has_left) rhs = rhs - scale(eleft, sl_v);
         if (i == len - 1 && has_right) rhs = rhs - scale(eright, sr_v);
-        if (i > 0) rhs = rhs - scale(elq, dp);
         dp = gi * rhs;
         SC[(int64_t)i * sstride] = dp;
     }
-    // back substitution and the weighted sum over systems
+    // back substitution in chunks of LG rows; each chunk's weighted contributions
+    // are reduce-scattered so lane l writes row (i0 - l) of column j
     cx<R> xn = cxz<R>();
     cx<R> scn = SC[(int64_t)(len - 1) * sstride];
     cx<R> cn = (len > 1) ? F[2 * (first + len - 2)] : cxz<R>();  // c' of row last-1
-    for (int i = len - 1; i >= 0; --i) {
-        const int64_t q = first + i;
-        const cx<R> sc = scn;
-        if (i > 0) scn = SC[(int64_t)(i - 1) * sstride];
-        cx<R> x = sc;
-        if (i < len - 1) {
-            x = sc - cn * xn;             // cn is c'[q]
-            if (i > 0) cn = F[2 * (q - 1)];  // c'[q-1] for the next row
+    for (int i0 = len - 1; i0 >= 0; i0 -= LG) {
+        R v[LG];
+#pragma unroll
+        for (int r = 0; r < LG; ++r) {
+            const int i = i0 - r;
+            v[r] = RealOps<R>::zero();
+            if (i >= 0) {
+                const cx<R> sc = scn;
+                if (i > 0) scn = SC[(int64_t)(i - 1) * sstride];
+                cx<R> x = sc;
+                if (i < len - 1) {
+                    x = csub_mul(sc, cn, xn);            // cn is c'[row i]
+                    if (i > 0) cn = F[2 * (first + i - 1)];  // c'[row i-1] for the next row
+                }
+                xn = x;
+                v[r] = re_mul(wgt, x);
+            }
         }
-        xn = x;
-        R acc = re_mul(wgt, x);
-        for (int off = LG / 2; off > 0; off >>= 1) acc = acc + shfl_down(gmask, acc, off);
-        if (sl == 0) store_out<R>(Y, q * g.Rc + j, acc);
+        reduce_scatter<LG>(gmask, sl, v);
+        const int i = i0 - sl;
+        if (i >= 0) store_out<R>(Y, (first + i) * g.Rc + j, v[0]);
     }
     // the separator row that follows this block
     R acc = re_mul(wgt, sr_v);
-    for (int off = LG / 2; off > 0; off >>= 1) acc = acc + shfl_down(gmask, acc, off);
+#pragma unroll
+    for (int off = LG / 2; off > 0; off >>= 1) acc = acc + shfl_xor(gmask, acc, off);
     if (sl == 0 && has_right) store_out<R>(Y, (first + len) * g.Rc + j, acc);
 }
 
@@ -417,67 +455,104 @@ TriGeom tri_geometry(int64_t N, int S, int Rc, bool ff, int sm_count) {
 
 static inline size_t align_up(size_t x) { return (x + 255) & ~size_t(255); }
 
+// Buffers of one evaluation.  The factor part (dP, eP, fact, us, ws, spk) depends
+// only on T, t, c and the poles and can be kept for later right-hand sides; the
+// solve part (VP, yend, sig, scr) is per call.  In a single call scr overlays us/ws,
+// which are dead once K1b has run.
 struct TriLayout {
-    size_t fact, spk, yend, sig, scratch, prepd, prepe, prepv, total;
+    size_t fact, spk, us, prepd, prepe, factor_total;  // factor part
+    size_t yend, sig, scr, prepv, solve_total;          // solve part (offsets from its own base)
 };
 
 static TriLayout tri_layout(const TriGeom &g, bool ff) {
     const size_t c = 16;  // sizeof(cx<double>) == sizeof(cx<f32x2>)
     TriLayout L{};
     size_t off = 0;
-    L.fact = off;
-    off += align_up((size_t)g.S * g.N * 2 * c);
-    L.spk = off;
-    off += align_up((size_t)g.S * g.P * 4 * c);
-    L.yend = off;
-    off += align_up((size_t)g.S * g.P * g.Rc * 2 * c);
-    L.sig = off;
-    off += align_up((size_t)g.S * g.P * g.Rc * c);
-    L.scratch = off;  // K1's spikes and K3's forward values share this region
-    off += align_up(std::max((size_t)g.S * g.N * 2 * c, (size_t)g.N * g.LG * g.Rc * c));
-    L.prepd = off;
-    off += align_up((size_t)g.N * 8);
-    L.prepe = off;
-    off += align_up((size_t)g.N * 8);
-    L.prepv = off;
-    if (ff) off += align_up((size_t)g.N * g.Rc * 8);
-    L.total = off;
+    L.fact = off; off += align_up((size_t)g.S * g.N * 2 * c);
+    L.spk = off; off += align_up((size_t)g.S * g.P * 4 * c);
+    L.prepd = off; off += align_up((size_t)g.N * 8);
+    L.prepe = off; off += align_up((size_t)g.N * 8);
+    L.us = off; off += align_up((size_t)g.S * g.N * 2 * c);  // us then ws
+    L.factor_total = off;
+    off = 0;
+    L.yend = off; off += align_up((size_t)g.S * g.P * g.Rc * 2 * c);
+    L.sig = off; off += align_up((size_t)g.S * g.P * g.Rc * c);
+    L.prepv = off; if (ff) off += align_up((size_t)g.N * g.Rc * 8);
+    L.scr = off; off += align_up((size_t)g.N * g.LG * g.Rc * c);
+    L.solve_total = off;
     return L;
 }
 
-size_t tri_workspace_bytes(const TriGeom &g, bool ff) { return tri_layout(g, ff).total; }
+size_t tri_factor_bytes(const TriGeom &g, bool ff) { return tri_layout(g, ff).factor_total; }
+size_t tri_solve_bytes(const TriGeom &g, bool ff) { return tri_layout(g, ff).solve_total; }
+
+// A single call uses one workspace: [factor part | overflow | yend, sig, prepv].  The K3
+// scratch starts at the spikes (dead after K1b) and runs into the overflow area when
+// it is larger than them.
+static size_t tri_overflow(const TriGeom &g) {
+    const size_t scr = (size_t)g.N * g.LG * g.Rc * 16;
+    const size_t spikes = (size_t)g.S * g.N * 2 * 16;
+    return scr > spikes ? align_up(scr - spikes) : 0;
+}
+
+size_t tri_workspace_bytes(const TriGeom &g, bool ff) {
+    const TriLayout L = tri_layout(g, ff);
+    return L.factor_total + tri_overflow(g) + L.scr;  // L.scr = bytes of yend, sig, prepv
+}
 
 template <class R>
-static cudaError_t tri_run_t(const TriGeom &g, const double *d, const double *e, const double *V,
-                             double *Y, const TriPoles &ps, void *work, cudaStream_t st, Profiler &prof) {
+static cudaError_t tri_factor_t(const TriGeom &g, const double *d, const double *e, const TriPoles &ps,
+                                void *fwork, cudaStream_t st, Profiler &prof) {
     const bool ff = !std::is_same<R, double>::value;
     const TriLayout L = tri_layout(g, ff);
-    unsigned char *p = (unsigned char *)work;
+    unsigned char *p = (unsigned char *)fwork;
     cx<R> *fact = (cx<R> *)(p + L.fact);
     cx<R> *spk = (cx<R> *)(p + L.spk);
-    cx<R> *yend = (cx<R> *)(p + L.yend);
-    cx<R> *sig = (cx<R> *)(p + L.sig);
-    cx<R> *us = (cx<R> *)(p + L.scratch);
+    cx<R> *us = (cx<R> *)(p + L.us);
     cx<R> *wsp = us + (size_t)g.S * g.N;
-    cx<R> *scr = (cx<R> *)(p + L.scratch);
     R *dP = (R *)(p + L.prepd);
     R *eP = (R *)(p + L.prepe);
-    R *VP = ff ? (R *)(p + L.prepv) : nullptr;
-    const R *Vuse = ff ? VP : reinterpret_cast<const R *>(V);
-    const unsigned pgrid = (unsigned)std::min<int64_t>((g.N * (ff ? g.Rc : 1) + 255) / 256, 152 * 8);
-
+    const unsigned pgrid = (unsigned)std::min<int64_t>((g.N + 255) / 256, 152 * 8);
     cudaError_t err = prof.timed(ff ? "tri_prep<f32x2>" : "tri_prep<f64>", st, [&] {
-        tri_prep<R><<<pgrid, 256, 0, st>>>(g, d, e, V, dP, eP, VP);
+        tri_prep<R><<<pgrid, 256, 0, st>>>(g, d, e, nullptr, dP, eP, (R *)nullptr);
         return cudaGetLastError();
     });
     if (err != cudaSuccess) return err;
     const int64_t n1 = (int64_t)g.S * g.P;
-    err = prof.timed(ff ? "tri_block_factor<f32x2>" : "tri_block_factor<f64>", st, [&] {
+    return prof.timed(ff ? "tri_block_factor<f32x2>" : "tri_block_factor<f64>", st, [&] {
         tri_block_factor<R><<<(unsigned)((n1 + 127) / 128), 128, 0, st>>>(g, dP, eP, ps, fact, us, wsp, spk);
         return cudaGetLastError();
     });
-    if (err != cudaSuccess) return err;
-    const int64_t n1b = n1 * g.Rc;
+}
+
+template <class R>
+static cudaError_t tri_solve_t(const TriGeom &g, const double *V, double *Y, const TriPoles &ps, const void *fwork,
+                               void *swork, void *scr_override, cudaStream_t st, Profiler &prof) {
+    const bool ff = !std::is_same<R, double>::value;
+    const TriLayout L = tri_layout(g, ff);
+    const unsigned char *p = (const unsigned char *)fwork;
+    const cx<R> *fact = (const cx<R> *)(p + L.fact);
+    const cx<R> *spk = (const cx<R> *)(p + L.spk);
+    const cx<R> *us = (const cx<R> *)(p + L.us);
+    const cx<R> *wsp = us + (size_t)g.S * g.N;
+    const R *dP = (const R *)(p + L.prepd);
+    const R *eP = (const R *)(p + L.prepe);
+    unsigned char *q = (unsigned char *)swork;
+    cx<R> *yend = (cx<R> *)(q + L.yend);
+    cx<R> *sig = (cx<R> *)(q + L.sig);
+    R *VP = ff ? (R *)(q + L.prepv) : nullptr;
+    cx<R> *scr = scr_override ? (cx<R> *)scr_override : (cx<R> *)(q + L.scr);
+    const R *Vuse = ff ? VP : reinterpret_cast<const R *>(V);
+    cudaError_t err = cudaSuccess;
+    if (ff) {
+        const unsigned pgrid = (unsigned)std::min<int64_t>((g.N * g.Rc + 255) / 256, 152 * 8);
+        err = prof.timed("tri_prep_rhs<f32x2>", st, [&] {
+            tri_prep<R><<<pgrid, 256, 0, st>>>(g, nullptr, nullptr, V, nullptr, nullptr, VP);
+            return cudaGetLastError();
+        });
+        if (err != cudaSuccess) return err;
+    }
+    const int64_t n1b = (int64_t)g.S * g.P * g.Rc;
     err = prof.timed(ff ? "tri_block_dots<f32x2>" : "tri_block_dots<f64>", st, [&] {
         tri_block_dots<R><<<(unsigned)((n1b + 127) / 128), 128, 0, st>>>(g, Vuse, us, wsp, yend);
         return cudaGetLastError();
@@ -495,7 +570,15 @@ static cudaError_t tri_run_t(const TriGeom &g, const double *d, const double *e,
     }
     const int64_t n3 = (int64_t)g.P * g.Rc * g.LG;  // LG divides 128: groups never straddle CTAs
     err = prof.timed(ff ? "tri_block_solve<f32x2>" : "tri_block_solve<f64>", st, [&] {
-        tri_block_solve<R><<<(unsigned)((n3 + 127) / 128), 128, 0, st>>>(g, eP, Vuse, ps, fact, sig, scr, Y);
+        const unsigned grid = (unsigned)((n3 + 127) / 128);
+        switch (g.LG) {
+            case 1: tri_block_solve<R, 1><<<grid, 128, 0, st>>>(g, eP, Vuse, ps, fact, sig, scr, Y); break;
+            case 2: tri_block_solve<R, 2><<<grid, 128, 0, st>>>(g, eP, Vuse, ps, fact, sig, scr, Y); break;
+            case 4: tri_block_solve<R, 4><<<grid, 128, 0, st>>>(g, eP, Vuse, ps, fact, sig, scr, Y); break;
+            case 8: tri_block_solve<R, 8><<<grid, 128, 0, st>>>(g, eP, Vuse, ps, fact, sig, scr, Y); break;
+            case 16: tri_block_solve<R, 16><<<grid, 128, 0, st>>>(g, eP, Vuse, ps, fact, sig, scr, Y); break;
+            default: tri_block_solve<R, 32><<<grid, 128, 0, st>>>(g, eP, Vuse, ps, fact, sig, scr, Y); break;
+        }
         return cudaGetLastError();
     });
     if (err != cudaSuccess || !ff) return err;
@@ -506,10 +589,27 @@ static cudaError_t tri_run_t(const TriGeom &g, const double *d, const double *e,
     });
 }
 
+cudaError_t tri_factor(const TriGeom &g, bool ff, const double *d, const double *e, const TriPoles &ps, void *fwork,
+                       cudaStream_t st, Profiler &prof) {
+    return ff ? tri_factor_t<f32x2>(g, d, e, ps, fwork, st, prof) : tri_factor_t<double>(g, d, e, ps, fwork, st, prof);
+}
+
+cudaError_t tri_solve(const TriGeom &g, bool ff, const double *V, double *Y, const TriPoles &ps, const void *fwork,
+                      void *swork, cudaStream_t st, Profiler &prof) {
+    return ff ? tri_solve_t<f32x2>(g, V, Y, ps, fwork, swork, nullptr, st, prof)
+              : tri_solve_t<double>(g, V, Y, ps, fwork, swork, nullptr, st, prof);
+}
+
 cudaError_t tri_run(const TriGeom &g, bool ff, const double *d, const double *e, const double *V, double *Y,
                     const TriPoles &ps, void *work, cudaStream_t st, Profiler &prof) {
-    return ff ? tri_run_t<f32x2>(g, d, e, V, Y, ps, work, st, prof)
-              : tri_run_t<double>(g, d, e, V, Y, ps, work, st, prof);
+    const TriLayout L = tri_layout(g, ff);
+    unsigned char *p = (unsigned char *)work;
+    void *scr = p + L.us;
+    unsigned char *solve_base = p + L.factor_total + tri_overflow(g);
+    cudaError_t err = ff ? tri_factor_t<f32x2>(g, d, e, ps, p, st, prof) : tri_factor_t<double>(g, d, e, ps, p, st, prof);
+    if (err != cudaSuccess) return err;
+    return ff ? tri_solve_t<f32x2>(g, V, Y, ps, p, solve_base, scr, st, prof)
+              : tri_solve_t<double>(g, V, Y, ps, p, solve_base, scr, st, prof);
 }
 
 }  // namespace expm

@@ -8,6 +8,7 @@ namespace expm {
 
 struct Profiler;
 
+constexpr int TRI_PF = 8;       // rows kept in flight by the factor kernel's backward pass
 constexpr int TRI_PMAX = 3000;  // max blocks: the reduced system (P-1 rows) lives in shared memory
 constexpr int TRI_MMIN = 8;     // min interior rows per block
 constexpr int TRI_MAXSYS = 32;  // real data: one system per conjugate pair, degree <= 64
@@ -33,7 +34,15 @@ struct TriPoles {
 };
 
 TriGeom tri_geometry(int64_t N, int S, int Rc, bool ff, int sm_count);
-size_t tri_workspace_bytes(const TriGeom &g, bool ff);
+size_t tri_workspace_bytes(const TriGeom &g, bool ff);  // one call (factor + solve)
+size_t tri_factor_bytes(const TriGeom &g, bool ff);     // the reusable factor part
+size_t tri_solve_bytes(const TriGeom &g, bool ff);      // the per-call solve part
+// factor part: d' = t d - c, e' = t e, the block LUs and spikes (depends on T, t, c, poles)
+cudaError_t tri_factor(const TriGeom &g, bool ff, const double *d, const double *e, const TriPoles &ps, void *fwork,
+                       cudaStream_t st, Profiler &prof);
+// solve part for a block of right-hand sides, with a factor part made by tri_factor
+cudaError_t tri_solve(const TriGeom &g, bool ff, const double *V, double *Y, const TriPoles &ps, const void *fwork,
+                      void *swork, cudaStream_t st, Profiler &prof);
 cudaError_t tri_run(const TriGeom &g, bool ff, const double *d, const double *e, const double *V, double *Y,
                     const TriPoles &ps, void *work, cudaStream_t st, Profiler &prof);
 

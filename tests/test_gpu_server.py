@@ -1,0 +1,106 @@
+"""The request server (expm_server_*): continuous batching of tridiagonal and dense
+exp(tA)V requests.  Every result must equal the same computation done alone through
+expm_apply_tridiag / expm_apply_dense (bit for bit: the kernels are deterministic and
+nothing is reduced across requests) and match the oracle within the path's tolerance."""
+
+import time
+
+import numpy as np
+import pytest
+
+import workloads
+from oracle import coeffs, matrix
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+import paper_2306_16778_gb300 as P  # noqa: E402
+
+DEV = torch.device("cuda:0")
+
+
+def _wait(server, tickets, timeout=120.0):
+    out = {}
+    t0 = time.time()
+    while len(out) < len(tickets):
+        for tk in tickets:
+            if tk not in out:
+                r = server.poll(tk)
+                if r is not None:
+                    out[tk] = r
+        assert time.time() - t0 < timeout, "server did not finish in time"
+        time.sleep(0.001)
+    return out
+
+
+def test_mixed_stream_same_alone_and_in_the_mix():
+    g = workloads.rng(600)
+    plans = {12: P.Plan(degree=12), 16: P.Plan(degree=16)}
+    server = P.Server(hbm_budget_bytes=8 << 30, max_inflight=4)
+    tri = []
+    for N in (5000, 40_000, 120_001):
+        w = workloads.laplacian_1d(N=N, nrhs=1, offset=600 + N)
+        d, e = (torch.from_numpy(x).to(DEV) for x in (w["d"], w["e"]))
+        tri.append((server.register_tridiag(d, e), d, e, w))
+    den = []
+    for n in (64, 200, 333):
+        A, Q, mu, _ = workloads.dense_symmetric(n, -40.0, 0.0, 1, g, True)
+        dA = torch.from_numpy(A).to(DEV)
+        den.append((server.register_dense(dA), dA, A))
+    reqs = []
+    for i in range(24):
+        deg = 12 if i % 2 else 16
+        if i % 3 == 2:
+            oid, dA, A = den[i % len(den)]
+            V = torch.from_numpy(workloads.request_rhs(A.shape[0], 1 + i % 5, 700 + i, True)).to(DEV)
+            prec = P.EXPM_MIXED_FP32 if i % 4 == 0 else P.EXPM_FP64
+            reqs.append(("dense", oid, dA, None, V, deg, prec, A))
+        else:
+            oid, d, e, w = tri[i % len(tri)]
+            V = torch.from_numpy(workloads.request_rhs(d.shape[0], 1 + i % 4, 700 + i, False)).to(DEV)
+            prec = P.EXPM_MIXED_F32X2 if i % 4 == 1 else P.EXPM_FP64
+            reqs.append(("tri", oid, d, e, V, deg, prec, w))
+    outs = [torch.empty_like(r[4]) for r in reqs]
+    torch.cuda.synchronize()
+    tickets = [server.submit(r[1], plans[r[5]], r[4], y, prec=r[6]) for r, y in zip(reqs, outs)]
+    results = _wait(server, tickets)
+    for r, y, tk in zip(reqs, outs, tickets):
+        st, info, ts = results[tk]
+        assert st == 0, (st, r[0])
+        assert ts[0] <= ts[1] <= ts[2] <= ts[3]
+        alone = torch.empty_like(y)
+        if r[0] == "tri":
+            P.expm_apply_tridiag(plans[r[5]], r[2], r[3], r[4], alone, prec=r[6])
+        else:
+            P.expm_apply_dense(plans[r[5]], r[2], r[4], alone, prec=r[6])
+        torch.cuda.synchronize()
+        assert torch.equal(alone, y), r[0]
+        th, a = coeffs.theta(r[5]), coeffs.residues(r[5])
+        V = r[4].cpu().numpy()
+        if r[0] == "tri":
+            Yo, _ = matrix.apply_tridiag(r[7]["d"], r[7]["e"], V, th, a)
+        else:
+            Yo, _ = matrix.apply_dense(r[7], V, th, a)
+        tol = 1e-12 if r[6] == P.EXPM_FP64 else 1e-8
+        assert matrix.rel_err(y.cpu().numpy(), Yo) <= tol, (r[0], r[6])
+    server.close()
+
+
+def test_server_rejections():
+    server = P.Server(hbm_budget_bytes=1 << 20, max_inflight=1)
+    plan = P.Plan(degree=16)
+    w = workloads.laplacian_1d(N=100_000, nrhs=1, offset=650)
+    d, e, V = (torch.from_numpy(x).to(DEV) for x in (w["d"], w["e"], w["V"]))
+    oid = server.register_tridiag(d, e)
+    with pytest.raises(P.ExpmError) as ei:           # needs far more than 1 MiB
+        server.submit(oid, plan, V, torch.empty_like(V))
+    assert ei.value.status == 2                       # EXPM_ENOMEM
+    with pytest.raises(P.ExpmError) as ei:
+        server.submit(oid + 99, plan, V, torch.empty_like(V))
+    assert ei.value.status == 8                       # EXPM_ENOTFOUND
+    st, _, _ = server.poll(12345)
+    assert st == 8                                    # unknown ticket
+    server.close()
