@@ -71,6 +71,12 @@ def parse():
                     help="rows of the Laplacian (smaller cases are for profiling only)")
     ap.add_argument("--fp64-only", action="store_true",
                     help="time only the binary64 path (profiling runs)")
+    ap.add_argument("--workload", default="laplacian", choices=["laplacian", "dense", "batched", "served"],
+                    help="laplacian: the headline line; the others print their own lines "
+                         "(dense 4096 Hermitian x 256 RHS; 4096-instance uneven batch; served stream)")
+    ap.add_argument("--dense-n", type=int, default=4096)
+    ap.add_argument("--batch-count", type=int, default=4096)
+    ap.add_argument("--served-requests", type=int, default=2000)
     return ap.parse_args()
 
 
@@ -342,10 +348,163 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def _time_calls(fn, steps, warmup):
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(steps):
+        t0 = time.perf_counter()
+        fn()
+        torch.cuda.synchronize()
+        ts.append(time.perf_counter() - t0)
+    return ts
+
+
+def run_dense(args):
+    """Dense complex Hermitian n x n, V n x 256, degree 16: binary64 vs mixed path."""
+    import torch
+    import paper_2306_16778_gb300 as P
+    import workloads
+    dev = torch.device("cuda", 0)
+    w = workloads.dense_hermitian(n=args.dense_n, nrhs=256)
+    plan = P.Plan(degree=16)
+    A, V = (torch.from_numpy(x).to(dev) for x in (w["A"], w["V"]))
+    out = {"workload": f"dense Hermitian n={args.dense_n}, 256 complex RHS, degree 16, spectrum U[-50,0]"}
+    Ys = {}
+    for name, prec in (("fp64", P.EXPM_FP64), ("mixed", P.EXPM_MIXED_FP32), ("mixed_tc", P.EXPM_MIXED_TF32X3)):
+        Y = torch.empty_like(V)
+        info = P.expm_apply_dense(plan, A, V, Y, prec=prec)
+        P.expm_profile_enable(plan, True)
+        ts = _time_calls(lambda: P.expm_apply_dense(plan, A, V, Y, prec=prec), max(1, args.steps), 0)
+        prof = P.expm_profile_read(plan)
+        P.expm_profile_enable(plan, False)
+        Ys[name] = Y.clone()
+        out[name] = {"s_per_eval": round(statistics.median(ts), 5), "evals_per_s": round(1 / statistics.median(ts), 4),
+                     "refine_sweeps": info.refine_iters_max, "resid_rel": info.resid_rel_max,
+                     "growth": info.growth_max_seen,
+                     "kernels_ms_total": {k: round(v[1], 3) for k, v in prof.items()}}
+    for name in ("mixed", "mixed_tc"):
+        d = (Ys[name] - Ys["fp64"]).abs().pow(2).sum().sqrt() / Ys["fp64"].abs().pow(2).sum().sqrt()
+        out[f"{name}_vs_fp64_rel"] = float(d)
+    print(json.dumps(out), flush=True)
+
+
+def run_batched(args):
+    """Uneven batch: sizes log-uniform in [32, 768], one complex RHS, degree 12."""
+    import torch
+    import paper_2306_16778_gb300 as P
+    import workloads
+    dev = torch.device("cuda", 0)
+    w = workloads.uneven_batch(count=args.batch_count)
+    plan = P.Plan(degree=12)
+    As = [torch.from_numpy(i["A"]).to(dev) for i in w["instances"]]
+    Vs = [torch.from_numpy(i["V"]).to(dev) for i in w["instances"]]
+    out = {"workload": f"{args.batch_count} complex Hermitian instances, n log-uniform [32,768], 1 RHS, degree 12",
+           "sum_n3": float(np.sum(w["sizes"].astype(float) ** 3))}
+    Ys = {}
+    for name, prec in (("fp64", P.EXPM_FP64), ("mixed", P.EXPM_MIXED_FP32)):
+        Y = [torch.empty_like(v) for v in Vs]
+        ts = _time_calls(lambda: P.expm_apply_batched(plan, As, Vs, Y, prec=prec), max(1, args.steps), 1)
+        Ys[name] = Y
+        med = statistics.median(ts)
+        out[name] = {"s_per_batch": round(med, 4), "instances_per_s": round(args.batch_count / med, 2)}
+    worst = max(float((a - b).abs().pow(2).sum().sqrt() / b.abs().pow(2).sum().sqrt())
+                for a, b in zip(Ys["mixed"], Ys["fp64"]))
+    out["mixed_vs_fp64_worst_rel"] = worst
+    print(json.dumps(out), flush=True)
+
+
+def run_served(args):
+    """Served stream: Poisson arrivals at swept rates; p50/p99 latency and evals/s."""
+    import torch
+    import paper_2306_16778_gb300 as P
+    import workloads
+    dev = torch.device("cuda", 0)
+    plans = {12: P.Plan(degree=12), 16: P.Plan(degree=16)}
+    reqs_all = workloads.served_stream(args.served_requests, rate=1.0)
+    out = {"workload": "served stream: 70% Laplacian N log-uniform [2^12,2^20] 1-4 RHS, "
+                       "30% dense Hermitian n log-uniform [64,2048] 1-64 RHS, degree 12/16",
+           "requests_per_rate": args.served_requests}
+    for prec_name, ptri, pden in (("fp64", P.EXPM_FP64, P.EXPM_FP64),
+                                  ("mixed", P.EXPM_MIXED_F32X2, P.EXPM_MIXED_FP32)):
+        server = P.Server(hbm_budget_bytes=64 << 30, max_inflight=8)
+        ops = {}
+        for r in reqs_all:
+            key = (r["kind"], r["op"])
+            if key not in ops:
+                op = workloads.served_operator(r["kind"], r["op"])
+                if r["kind"] == "tridiag":
+                    d, e = (torch.from_numpy(x).to(dev) for x in (op["d"], op["e"]))
+                    ops[key] = (server.register_tridiag(d, e), d.shape[0])
+                else:
+                    A = torch.from_numpy(op["A"]).to(dev)
+                    ops[key] = (server.register_dense(A), A.shape[0])
+        bufs = []
+        for r in reqs_all:
+            oid, n = ops[(r["kind"], r["op"])]
+            V = torch.from_numpy(workloads.request_rhs(n, r["nrhs"], r["seed"], r["kind"] == "dense")).to(dev)
+            bufs.append((oid, V, torch.empty_like(V)))
+        # saturation: submit everything at once
+        t0 = time.perf_counter()
+        tk = [server.submit(oid, plans[r["degree"]], V, Y, prec=ptri if r["kind"] == "tridiag" else pden)
+              for r, (oid, V, Y) in zip(reqs_all, bufs)]
+        lat = []
+        pending = set(tk)
+        while pending:
+            for t in list(pending):
+                res = server.poll(t)
+                if res is not None:
+                    pending.discard(t)
+                    lat.append(res[2][3] - res[2][0])
+        sat = len(tk) / (time.perf_counter() - t0)
+        rates = {}
+        for frac in (0.5, 0.9):
+            rate = frac * sat
+            gaps = workloads.rng(77).exponential(1.0 / rate, len(bufs))
+            t_start = time.perf_counter()
+            arrival = t_start + np.cumsum(gaps)
+            tk = []
+            lat = []
+            pending = {}
+            i = 0
+            while i < len(bufs) or pending:
+                now = time.perf_counter()
+                while i < len(bufs) and arrival[i] <= now:
+                    r = reqs_all[i]
+                    oid, V, Y = bufs[i]
+                    t = server.submit(oid, plans[r["degree"]], V, Y, prec=ptri if r["kind"] == "tridiag" else pden)
+                    pending[t] = True
+                    i += 1
+                for t in list(pending):
+                    res = server.poll(t)
+                    if res is not None:
+                        del pending[t]
+                        lat.append(res[2][3] - res[2][0])
+            wall = time.perf_counter() - t_start
+            lat.sort()
+            rates[f"{frac:.1f}xsat"] = {"offered_rps": round(rate, 2), "evals_per_s": round(len(lat) / wall, 2),
+                                       "p50_ms": round(1e3 * lat[len(lat) // 2], 3),
+                                       "p99_ms": round(1e3 * lat[min(len(lat) - 1, int(0.99 * len(lat)))], 3)}
+        out[prec_name] = {"saturation_evals_per_s": round(sat, 2), "rates": rates}
+        server.close()
+    print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse()
     if args.peaks:
         run_peaks()
+        return
+    if args.workload == "dense":
+        run_dense(args)
+        return
+    if args.workload == "batched":
+        run_batched(args)
+        return
+    if args.workload == "served":
+        run_served(args)
         return
     if args.impl == "reference":
         run_reference(args)

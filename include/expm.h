@@ -206,9 +206,11 @@ expm_status expm_apply_tridiag_noalloc(expm_plan plan, int64_t N, const double *
  *   k             1 <= k <= 4096
  *   Y             n x k output, leading dimension ldy >= k; complex when A or V is
  *                 complex, else real.  Must not overlap A or V.
- *   opts          prec: EXPM_FP64 (binary64 throughout) or EXPM_MIXED_FP32 /
- *                 EXPM_MIXED_F32X2 (binary32 factorization, binary64 iterative
- *                 refinement with binary64 residuals until
+ *   opts          prec: EXPM_FP64 (binary64 throughout), EXPM_MIXED_FP32 /
+ *                 EXPM_MIXED_F32X2 (binary32 factorization on the CUDA cores) or
+ *                 EXPM_MIXED_TF32X3 (binary32 factorization whose trailing updates run
+ *                 on the tensor cores, tcgen05 kind::tf32 with the 3xTF32 split), each
+ *                 followed by iterative refinement with binary64-accurate residuals until
  *                 ||R_k||_F <= tol (||tA||_F + |theta_k - c|) ||X_k||_F, at most
  *                 max_refine sweeps); growth_max bounds max|U| / max|tA - cI + theta I|.
  *   info          optional: refinement sweeps, worst relative residual, worst growth.

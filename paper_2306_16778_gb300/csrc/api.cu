@@ -285,8 +285,8 @@ expm_status expm_apply_dense(expm_plan p, int n, const void *A, int lda, int a_i
     if (n < 1 || k < 1 || k > 4096) return set_error(EXPM_EINVAL, "apply_dense: need n >= 1 and 1 <= k <= 4096");
     if (lda < n || ldv < k || ldy < k) return set_error(EXPM_EINVAL, "apply_dense: leading dimension too small");
     if (!A || !V || !Y) return set_error(EXPM_EINVAL, "apply_dense: NULL data pointer");
-    if (opts.prec != EXPM_FP64 && opts.prec != EXPM_MIXED_FP32 && opts.prec != EXPM_MIXED_F32X2)
-        return set_error(EXPM_EINVAL, "apply_dense: precision must be EXPM_FP64, EXPM_MIXED_FP32 or EXPM_MIXED_F32X2");
+    if (opts.prec < EXPM_FP64 || opts.prec > EXPM_MIXED_TF32X3)
+        return set_error(EXPM_EINVAL, "apply_dense: unknown precision");
     if (opts.flags != 0) return set_error(EXPM_EINVAL, "apply_dense: opts.flags must be 0");
     if (!std::isfinite(opts.t) || !std::isfinite(opts.shift_c) || !(opts.tol > 0) || opts.max_refine < 0)
         return set_error(EXPM_EINVAL, "apply_dense: bad t, shift_c, tol or max_refine");
@@ -305,6 +305,7 @@ expm_status expm_apply_dense(expm_plan p, int n, const void *A, int lda, int a_i
     const bool split_v = !complex_a && v_is_complex;
     g.kc = split_v ? 2 * k : k;
     g.mixed = opts.prec != EXPM_FP64;
+    g.tc = opts.prec == EXPM_MIXED_TF32X3;
     g.t = opts.t;
     g.tol = opts.tol;
     g.max_refine = opts.max_refine;
@@ -364,6 +365,7 @@ expm_status expm_apply_dense(expm_plan p, int n, const void *A, int lda, int a_i
         if (err != cudaSuccess) return cuda_error(err, "apply_dense: result copy");
     }
     expm_status out = EXPM_OK;
+    if (res.tc_timeout) return set_error(EXPM_ETIMEOUT, "apply_dense: a bounded wait in the tensor-core kernel gave up");
     if (res.growth_max > opts.growth_max) out = EXPM_EGROWTH;
     else if (g.mixed && !(res.resid_rel_max <= opts.tol)) out = EXPM_ENOCONV;
     if (info) {

@@ -71,6 +71,44 @@ EXPM_D f32x2 to_f32x2(double x) {
 }
 EXPM_D double to_double(f32x2 x) { return (double)x.hi + (double)x.lo; }
 
+// binary64 -> float pair with integer operations only (no FP64-pipe work): hi takes
+// the leading 24 significand bits, lo the remaining 29 bits rounded to 24; the pair
+// is then renormalised.  Values outside [2^-74, 2^128) take the binary64 route.
+EXPM_D f32x2 split_bits(double x) {
+    const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+    const int ex = (int)((u >> 52) & 0x7ff);
+    if (ex < 1023 + 52 - 126 || ex > 1023 + 127) return to_f32x2(x);
+    const unsigned sign = (unsigned)(u >> 63) << 31;
+    const float hi = __uint_as_float(sign | ((unsigned)(ex - 1023 + 127) << 23) | (unsigned)((u >> 29) & 0x7fffffu));
+    const float scalef = __uint_as_float((unsigned)(ex - 1023 - 52 + 127) << 23);
+    float lo = __fmul_rn(__uint2float_rn((unsigned)(u & 0x1fffffffu)), scalef);
+    if (sign) lo = -lo;
+    return fast_two_sum(hi, lo);
+}
+
+// float -> binary64 by bit widening (normal floats; zero and the rest fall back)
+EXPM_D double widen_bits(float f) {
+    const unsigned u = __float_as_uint(f);
+    const unsigned ex = (u >> 23) & 0xff;
+    if (ex == 0 || ex == 0xff) return (double)f;
+    const unsigned long long b = ((unsigned long long)(u >> 31) << 63) |
+                                 ((unsigned long long)(ex - 127 + 1023) << 52) |
+                                 ((unsigned long long)(u & 0x7fffffu) << 29);
+    return __longlong_as_double((long long)b);
+}
+
+// c + a*b in float-float: error-free product of the high parts, the cross terms,
+// then one two-sum with c and a renormalisation (the "sloppy" double-word add).
+EXPM_D f32x2 dd_fma(f32x2 a, f32x2 b, f32x2 c) {
+    const float p = __fmul_rn(a.hi, b.hi);
+    float e = __fmaf_rn(a.hi, b.hi, -p);
+    e = __fmaf_rn(a.hi, b.lo, e);
+    e = __fmaf_rn(a.lo, b.hi, e);
+    const f32x2 s = two_sum(p, c.hi);
+    const float t = __fadd_rn(s.lo, __fadd_rn(e, c.lo));
+    return fast_two_sum(s.hi, t);
+}
+
 // ------------------------------------------------------------------ traits
 template <class R> struct RealOps;
 template <> struct RealOps<double> {

@@ -26,6 +26,7 @@
 #include "dense.cuh"
 #include "dense_kernels.cuh"
 #include "plan.cuh"
+#include "tc_gemm.cuh"
 
 namespace expm {
 
@@ -146,6 +147,48 @@ __global__ void frob2(int n, const double *__restrict__ A, int64_t lda, int64_t 
     if ((threadIdx.x & 31) == 0) atomicAdd(out, acc);
 }
 
+// Operands of the tensor-core trailing update C -= L21 U12 (complex, binary32), laid out
+// for the real K-major product C_real -= A' B'^T with the 3xTF32 split:
+//   L21 (rest x nb complex) is the real rest x 2nb matrix A (re, im interleaved);
+//   U12 (nb x rest complex) becomes the real 2rest x 2nb matrix BT with rows
+//       BT[2j] = (.. ur_kj, -ui_kj ..),  BT[2j+1] = (.. ui_kj, ur_kj ..),
+//   so that (A BT^T)[i][2j] = Re(L21 U12)_ij and [i][2j+1] = Im(L21 U12)_ij;
+//   A' = [A_hi | A_hi | A_lo] and B' = [BT_hi | BT_lo | BT_hi] (K = 6 nb), with x_hi
+//   x rounded to TF32 and x_lo = x - x_hi (exact in binary32).
+// Batch z of A' occupies rows z*rest_a .. of a stacked matrix, likewise B' (2 rest rows).
+EXPM_D float tf32_hi(float x) { return __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u); }
+
+__global__ void split_tc_operands(int rest, int nb, const cx<float> *__restrict__ F, int n, int64_t fstride,
+                                  float *__restrict__ Ap, float *__restrict__ Bp) {
+    const int z = blockIdx.z;
+    const cx<float> *L21 = F + (int64_t)z * fstride + (int64_t)nb * n;  // relative to the diagonal block
+    const cx<float> *U12 = F + (int64_t)z * fstride + nb;
+    const int K6 = 6 * nb;
+    const int64_t na = (int64_t)rest * nb;
+    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < na; idx += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(idx / nb), k = (int)(idx % nb);
+        const cx<float> a = L21[(int64_t)i * n + k];
+        float *row = Ap + ((int64_t)z * rest + i) * K6;
+        const float hr = tf32_hi(a.re), hi = tf32_hi(a.im);
+        row[2 * k] = hr;               row[2 * k + 1] = hi;
+        row[2 * nb + 2 * k] = hr;      row[2 * nb + 2 * k + 1] = hi;
+        row[4 * nb + 2 * k] = a.re - hr; row[4 * nb + 2 * k + 1] = a.im - hi;
+        // the U12 entry (k, i) of the same index range (rest x nb pairs, transposed)
+        const cx<float> u = U12[(int64_t)k * n + i];
+        float *r0 = Bp + ((int64_t)z * 2 * rest + 2 * i) * K6;
+        float *r1 = r0 + K6;
+        const float ur = u.re, ui = -u.im, uh = tf32_hi(ur), vh = tf32_hi(ui);
+        // row 2j: (ur, -ui); row 2j+1: (ui, ur)
+        r0[2 * k] = uh;                r0[2 * k + 1] = vh;
+        r0[2 * nb + 2 * k] = ur - uh;  r0[2 * nb + 2 * k + 1] = ui - vh;
+        r0[4 * nb + 2 * k] = uh;       r0[4 * nb + 2 * k + 1] = vh;
+        const float wr = u.im, wh = tf32_hi(wr);
+        r1[2 * k] = wh;                r1[2 * k + 1] = uh;
+        r1[2 * nb + 2 * k] = wr - wh;  r1[2 * nb + 2 * k + 1] = ur - uh;
+        r1[4 * nb + 2 * k] = wh;       r1[4 * nb + 2 * k + 1] = uh;
+    }
+}
+
 // ------------------------------------------------------------------ host helpers
 
 static unsigned grid1d(int64_t total, int threads = 256) {
@@ -163,9 +206,17 @@ template <class K> static cudaError_t set_smem(K kernel, size_t bytes) {
         if (_e != cudaSuccess) return _e;         \
     } while (0)
 
-// Unpivoted blocked LU of `batch` n x n matrices F (ld n, batch stride n*n).
+// Tensor-core scratch of the trailing update (binary32 LU with the TF32 split).
+struct TcScratch {
+    float *Ap = nullptr, *Bp = nullptr;
+    int *err = nullptr;
+};
+
+// Unpivoted blocked LU of `batch` n x n matrices F (ld n, batch stride n*n).  With
+// tc (binary32 only) the trailing updates run on the tensor cores.
 template <class T>
-static cudaError_t lu_blocked(int n, int batch, cx<T> *F, cudaStream_t st, Profiler &prof) {
+static cudaError_t lu_blocked(int n, int batch, cx<T> *F, cudaStream_t st, Profiler &prof,
+                              const TcScratch *tc = nullptr) {
     const int64_t bs = (int64_t)n * n;
     const size_t sm1 = tri_smem_bytes<T>(), sm2 = 2 * tri_smem_bytes<T>();
     EXPM_TRY(set_smem(lu_diag<T>, sm1));
@@ -190,12 +241,30 @@ static cudaError_t lu_blocked(int n, int batch, cx<T> *F, cudaStream_t st, Profi
                                                                                  diag + (int64_t)nb * n, n, bs);
             return cudaGetLastError();
         }));
+        if (tc != nullptr && sizeof(T) == 4 && rest >= 128) {
+            // A22 -= L21 U12 as one real product per matrix on the tensor cores
+            EXPM_TRY(prof.timed("split_tc_operands", st, [&] {
+                split_tc_operands<<<dim3(grid1d((int64_t)rest * nb), 1, batch), 256, 0, st>>>(
+                    rest, nb, reinterpret_cast<const cx<float> *>(diag), n, bs, tc->Ap, tc->Bp);
+                return cudaGetLastError();
+            }));
+            EXPM_TRY(prof.timed("tc_gemm_tf32x3", st, [&]() -> cudaError_t {
+                for (int z = 0; z < batch; ++z) {
+                    float *Cz = reinterpret_cast<float *>(F + (int64_t)z * bs + (int64_t)(p + nb) * n + p + nb);
+                    cudaError_t e = tc_gemm_tf32_sub(rest, 2 * rest, 6 * nb, tc->Ap + (int64_t)z * rest * 6 * nb,
+                                                     6 * nb, tc->Bp + (int64_t)z * 2 * rest * 6 * nb, 6 * nb, Cz,
+                                                     2 * n, tc->err, st);
+                    if (e != cudaSuccess) return e;
+                }
+                return cudaSuccess;
+            }));
+            continue;
+        }
         EXPM_TRY(prof.timed(sizeof(T) == 8 ? "cgemm_update<f64>" : "cgemm_update<f32>", st, [&] {
             // A22 -= L21 U12
-            dim3 g((rest + 63) / 64, (rest + 63) / 64, batch);
-            cgemm<T, cx<T>, false, false><<<g, 256, 0, st>>>(
-                rest, rest, nb, cx<T>{T(-1), T(0)}, T(1), diag + (int64_t)nb * n, n, bs, diag + nb, n, bs,
-                diag + (int64_t)nb * n + nb, n, bs, 1);
+            cgemm_launch<T, cx<T>, false, false>(rest, rest, nb, cx<T>{T(-1), T(0)}, T(1), diag + (int64_t)nb * n, n,
+                                                 bs, diag + nb, n, bs, diag + (int64_t)nb * n + nb, n, bs, 1, batch,
+                                                 st);
             return cudaGetLastError();
         }));
     }
@@ -224,15 +293,14 @@ static cudaError_t lu_solve(int n, int kc, int batch, const cx<T> *F, int64_t fs
             if (!conj) trsm_left<T, true, true, false><<<dim3(cb, 1, batch), 64, sm2, st>>>(nb, kc, dg, n, fstride, xp, kc, xstride);
             else trsm_left<T, true, false, true><<<dim3(cb, 1, batch), 64, sm2, st>>>(nb, kc, dg, n, fstride, xp, kc, xstride);
             if (rest > 0) {
-                dim3 g(cb, (rest + 63) / 64, batch);
                 if (!conj)  // X[p+nb:] -= L[p+nb:, p:p+nb] X[p:p+nb]
-                    cgemm<T, cx<T>, false, false><<<g, 256, 0, st>>>(rest, kc, nb, cx<T>{T(-1), T(0)}, T(1),
-                                                                     dg + (int64_t)nb * n, n, fstride, xp, kc, xstride,
-                                                                     xp + (int64_t)nb * kc, kc, xstride, 1);
+                    cgemm_launch<T, cx<T>, false, false>(rest, kc, nb, cx<T>{T(-1), T(0)}, T(1), dg + (int64_t)nb * n,
+                                                         n, fstride, xp, kc, xstride, xp + (int64_t)nb * kc, kc,
+                                                         xstride, 1, batch, st);
                 else  // X[p+nb:] -= (U[p:p+nb, p+nb:])^H X[p:p+nb]
-                    cgemm<T, cx<T>, true, false><<<g, 256, 0, st>>>(rest, kc, nb, cx<T>{T(-1), T(0)}, T(1), dg + nb, n,
-                                                                    fstride, xp, kc, xstride, xp + (int64_t)nb * kc, kc,
-                                                                    xstride, 1);
+                    cgemm_launch<T, cx<T>, true, false>(rest, kc, nb, cx<T>{T(-1), T(0)}, T(1), dg + nb, n, fstride,
+                                                        xp, kc, xstride, xp + (int64_t)nb * kc, kc, xstride, 1, batch,
+                                                        st);
             }
         }
         // backward sweep
@@ -244,14 +312,12 @@ static cudaError_t lu_solve(int n, int kc, int batch, const cx<T> *F, int64_t fs
             if (!conj) trsm_left<T, false, false, false><<<dim3(cb, 1, batch), 64, sm2, st>>>(nb, kc, dg, n, fstride, xp, kc, xstride);
             else trsm_left<T, false, true, true><<<dim3(cb, 1, batch), 64, sm2, st>>>(nb, kc, dg, n, fstride, xp, kc, xstride);
             if (p > 0) {
-                dim3 g(cb, (p + 63) / 64, batch);
                 if (!conj)  // X[:p] -= U[:p, p:p+nb] X[p:p+nb]
-                    cgemm<T, cx<T>, false, false><<<g, 256, 0, st>>>(p, kc, nb, cx<T>{T(-1), T(0)}, T(1), F + p, n,
-                                                                     fstride, xp, kc, xstride, X, kc, xstride, 1);
+                    cgemm_launch<T, cx<T>, false, false>(p, kc, nb, cx<T>{T(-1), T(0)}, T(1), F + p, n, fstride, xp,
+                                                         kc, xstride, X, kc, xstride, 1, batch, st);
                 else  // X[:p] -= (L[p:p+nb, :p])^H X[p:p+nb]
-                    cgemm<T, cx<T>, true, false><<<g, 256, 0, st>>>(p, kc, nb, cx<T>{T(-1), T(0)}, T(1),
-                                                                    F + (int64_t)p * n, n, fstride, xp, kc, xstride, X,
-                                                                    kc, xstride, 1);
+                    cgemm_launch<T, cx<T>, true, false>(p, kc, nb, cx<T>{T(-1), T(0)}, T(1), F + (int64_t)p * n, n,
+                                                        fstride, xp, kc, xstride, X, kc, xstride, 1, batch, st);
             }
         }
         return cudaGetLastError();
@@ -264,7 +330,7 @@ static cudaError_t lu_solve(int n, int kc, int batch, const cx<T> *F, int64_t fs
 // R binary64 and D binary32 (mixed)].  The factor part depends only on A, t, c and
 // the poles and can be kept for later right-hand sides.
 struct DenseLayout {
-    size_t amax, umax, F, factor_total;  // factor part
+    size_t amax, umax, F, tcA, tcB, tcflag, factor_total;  // factor part
     size_t rn2, xn2, an2, X, R, D, solve_total;  // solve part (offsets from its own base)
 };
 static inline size_t align_up(size_t x) { return (x + 255) & ~size_t(255); }
@@ -277,6 +343,12 @@ static DenseLayout dense_layout(const DenseGeom &g) {
     L.amax = off; off += align_up(npz * sizeof(unsigned));
     L.umax = off; off += align_up(npz * sizeof(unsigned));
     L.F = off; off += align_up(npz * nn * (g.mixed ? sizeof(cx<float>) : sizeof(cx<double>)));
+    L.tcA = L.tcB = L.tcflag = off;
+    if (g.mixed && g.tc) {  // trailing-update operands for the largest step (rest < n)
+        L.tcA = off; off += align_up(npz * (size_t)g.n * 6 * DN_NB * sizeof(float));
+        L.tcB = off; off += align_up(npz * (size_t)g.n * 2 * 6 * DN_NB * sizeof(float));
+        L.tcflag = off; off += align_up(sizeof(int));
+    }
     L.factor_total = off;
     off = 0;
     L.rn2 = off; off += align_up(nsz * sizeof(double));
@@ -303,7 +375,8 @@ size_t dense_workspace_bytes(const DenseGeom &g) {
 
 template <class T>
 static cudaError_t factor_pairs(const DenseGeom &g, const DenseIO &io, const DenseSystems &sys, cx<T> *F,
-                                unsigned *amax, unsigned *umax, cudaStream_t st, Profiler &prof) {
+                                unsigned *amax, unsigned *umax, cudaStream_t st, Profiler &prof,
+                                const TcScratch *tc = nullptr) {
     // pair s uses system 2s (complex A) or s (real data); both carry the Im(theta) > 0 member
     DenseSystems pairs = sys;
     for (int s = 0; s < g.npairs; ++s) {
@@ -319,7 +392,7 @@ static cudaError_t factor_pairs(const DenseGeom &g, const DenseIO &io, const Den
             g.n, io.A, (int)io.lda, io.astride, g.complex_a, g.npairs, g.t, pairs, F, amax);
         return cudaGetLastError();
     }));
-    EXPM_TRY(lu_blocked<T>(g.n, batch, F, st, prof));
+    EXPM_TRY(lu_blocked<T>(g.n, batch, F, st, prof, tc));
     max_abs_upper<T><<<dim3(grid1d((int64_t)g.n * g.n), 1, batch), 256, 0, st>>>(g.n, F, g.n, (int64_t)g.n * g.n,
                                                                                   umax);
     return cudaGetLastError();
@@ -343,6 +416,11 @@ cudaError_t dense_factor(const DenseGeom &g, const DenseIO &io, const DenseSyste
     unsigned char *p = (unsigned char *)fwork;
     unsigned *amax = (unsigned *)(p + L.amax);
     unsigned *umax = (unsigned *)(p + L.umax);
+    if (g.mixed && g.tc) {
+        TcScratch tc{(float *)(p + L.tcA), (float *)(p + L.tcB), (int *)(p + L.tcflag)};
+        EXPM_TRY(cudaMemsetAsync(tc.err, 0, sizeof(int), st));
+        return factor_pairs<float>(g, io, sys, (cx<float> *)(p + L.F), amax, umax, st, prof, &tc);
+    }
     if (g.mixed) return factor_pairs<float>(g, io, sys, (cx<float> *)(p + L.F), amax, umax, st, prof);
     return factor_pairs<double>(g, io, sys, (cx<double> *)(p + L.F), amax, umax, st, prof);
 }
@@ -352,9 +430,12 @@ cudaError_t dense_growth(const DenseGeom &g, const void *fwork, cudaStream_t st,
     const unsigned char *p = (const unsigned char *)fwork;
     const int npz = g.ninst * g.npairs;
     std::vector<unsigned> hm(2 * (size_t)npz);
+    int tcflag = 0;
     EXPM_TRY(cudaMemcpyAsync(hm.data(), p + L.amax, sizeof(unsigned) * npz, cudaMemcpyDeviceToHost, st));
     EXPM_TRY(cudaMemcpyAsync(hm.data() + npz, p + L.umax, sizeof(unsigned) * npz, cudaMemcpyDeviceToHost, st));
+    if (g.mixed && g.tc) EXPM_TRY(cudaMemcpyAsync(&tcflag, p + L.tcflag, sizeof(int), cudaMemcpyDeviceToHost, st));
     EXPM_TRY(cudaStreamSynchronize(st));
+    res->tc_timeout = tcflag;
     res->growth_max = 0.0;
     res->inst_growth.assign(g.ninst, 0.0);
     for (int z = 0; z < npz; ++z) {
@@ -409,16 +490,27 @@ cudaError_t dense_solve(const DenseGeom &g, const DenseIO &io, const DenseSystem
             residual_diag<<<dim3(gx, 1, nsz), 256, 0, st>>>(g.n, g.kc, io, g.nsys, X, R, nk, sys);
             EXPM_TRY(cudaGetLastError());
             if (it > 0) {
-                EXPM_TRY(prof.timed("residual_gemm<f64>", st, [&] {
+                if (g.kc <= 8) {
+                    EXPM_TRY(prof.timed("resid_gemv<f64>", st, [&] {
+                        dim3 gg((g.n + 7) / 8, 1, nsz);
+                        if (g.complex_a)
+                            resid_gemv<cx<double>><<<gg, 256, 0, st>>>(g.n, g.kc, g.n, g.t, (const cx<double> *)io.A,
+                                                                        (int)io.lda, io.astride, X, g.kc, nk, R, g.kc,
+                                                                        nk, g.nsys);
+                        else
+                            resid_gemv<double><<<gg, 256, 0, st>>>(g.n, g.kc, g.n, g.t, io.A, (int)io.lda, io.astride,
+                                                                    X, g.kc, nk, R, g.kc, nk, g.nsys);
+                        return cudaGetLastError();
+                    }));
+                } else EXPM_TRY(prof.timed("resid_gemm<f32x2>", st, [&] {
                     dim3 gg((g.kc + 63) / 64, (g.n + 63) / 64, nsz);
                     if (g.complex_a)
-                        cgemm<double, cx<double>, false, false><<<gg, 256, 0, st>>>(
-                            g.n, g.kc, g.n, cx<double>{-g.t, 0.0}, 1.0, (const cx<double> *)io.A, (int)io.lda,
-                            io.astride, X, g.kc, nk, R, g.kc, nk, g.nsys);
+                        resid_gemm_f32x2<cx<double>><<<gg, 256, 0, st>>>(g.n, g.kc, g.n, g.t,
+                                                                          (const cx<double> *)io.A, (int)io.lda,
+                                                                          io.astride, X, g.kc, nk, R, g.kc, nk, g.nsys);
                     else
-                        cgemm<double, double, false, false><<<gg, 256, 0, st>>>(
-                            g.n, g.kc, g.n, cx<double>{-g.t, 0.0}, 1.0, io.A, (int)io.lda, io.astride, X, g.kc, nk, R,
-                            g.kc, nk, g.nsys);
+                        resid_gemm_f32x2<double><<<gg, 256, 0, st>>>(g.n, g.kc, g.n, g.t, io.A, (int)io.lda,
+                                                                      io.astride, X, g.kc, nk, R, g.kc, nk, g.nsys);
                     return cudaGetLastError();
                 }));
             }

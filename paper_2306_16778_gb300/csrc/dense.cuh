@@ -31,6 +31,7 @@ struct DenseGeom {
     int nsys;       // solved systems per instance
     int complex_a;  // A complex Hermitian (else real symmetric)
     int mixed;      // binary32 factorization + binary64 refinement
+    int tc;         // mixed only: LU trailing updates on the tensor cores (3xTF32)
     double t;       // time factor
     double tol;     // refinement tolerance
     int max_refine;
@@ -48,6 +49,7 @@ struct DenseIO {
 };
 
 struct DenseResult {
+    int tc_timeout = 0;          // a bounded wait inside the tensor-core kernel gave up
     int iters;                   // refinement sweeps (max over the batch)
     double resid_rel_max;        // worst final relative residual
     double growth_max;           // worst growth factor

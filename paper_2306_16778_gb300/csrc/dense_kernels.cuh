@@ -171,23 +171,27 @@ template <class T> EXPM_D cx<T> as_cx(cx<T> v) { return v; }
 template <class T> EXPM_D cx<T> as_cx(T v) { return {v, T(0)}; }
 
 // Batch z uses A[z / adiv] (adiv > 1 shares one A among consecutive batches).
-template <class T, class AE, bool CONJ_A, bool CONJ_B>
+// Tile BM x BN, BK = 16, 256 threads, each computing TM x TN outputs.  The default
+// 64 x 64 tile serves wide right-hand sides; the 128 x 8 tile serves narrow ones.
+template <class T, class AE, bool CONJ_A, bool CONJ_B, int BM = 64, int BN = 64, int TM = 4, int TN = 4>
 __global__ void __launch_bounds__(256) cgemm(int m, int n, int K, cx<T> alpha, T beta, const AE *__restrict__ A,
                                              int lda, int64_t sA, const cx<T> *__restrict__ B, int ldb, int64_t sB,
                                              cx<T> *__restrict__ C, int ldc, int64_t sC, int adiv) {
-    constexpr int BM = 64, BN = 64, BK = 16;
+    constexpr int BK = 16;
+    constexpr int NTX = BN / TN, NTY = BM / TM;
+    static_assert(NTX * NTY == 256, "256 threads per tile");
     __shared__ cx<T> As[BK][BM + 1];
     __shared__ cx<T> Bs[BK][BN + 1];
     const AE *a = A + (int64_t)(blockIdx.z / adiv) * sA;
     const cx<T> *b = B + (int64_t)blockIdx.z * sB;
     cx<T> *c = C + (int64_t)blockIdx.z * sC;
     const int i0 = blockIdx.y * BM, j0 = blockIdx.x * BN;
-    const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
-    cx<T> acc[4][4];
+    const int tx = threadIdx.x % NTX, ty = threadIdx.x / NTX;
+    cx<T> acc[TM][TN];
 #pragma unroll
-    for (int r = 0; r < 4; ++r)
+    for (int r = 0; r < TM; ++r)
 #pragma unroll
-        for (int q = 0; q < 4; ++q) acc[r][q] = {T(0), T(0)};
+        for (int q = 0; q < TN; ++q) acc[r][q] = {T(0), T(0)};
     for (int l0 = 0; l0 < K; l0 += BK) {
         for (int idx = threadIdx.x; idx < BM * BK; idx += 256) {
             int ii, ll;
@@ -214,28 +218,170 @@ __global__ void __launch_bounds__(256) cgemm(int m, int n, int K, cx<T> alpha, T
         __syncthreads();
 #pragma unroll 4
         for (int l = 0; l < BK; ++l) {
-            cx<T> av[4], bv[4];
+            cx<T> av[TM], bv[TN];
 #pragma unroll
-            for (int r = 0; r < 4; ++r) av[r] = As[l][ty + 16 * r];
+            for (int r = 0; r < TM; ++r) av[r] = As[l][ty + NTY * r];
 #pragma unroll
-            for (int q = 0; q < 4; ++q) bv[q] = Bs[l][tx + 16 * q];
+            for (int q = 0; q < TN; ++q) bv[q] = Bs[l][tx + NTX * q];
 #pragma unroll
-            for (int r = 0; r < 4; ++r)
+            for (int r = 0; r < TM; ++r)
 #pragma unroll
-                for (int q = 0; q < 4; ++q) acc[r][q] = cfma(acc[r][q], av[r], bv[q]);
+                for (int q = 0; q < TN; ++q) acc[r][q] = cfma(acc[r][q], av[r], bv[q]);
         }
         __syncthreads();
     }
 #pragma unroll
-    for (int r = 0; r < 4; ++r)
+    for (int r = 0; r < TM; ++r)
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const int gi = i0 + ty + 16 * r, gj = j0 + tx + 16 * q;
+        for (int q = 0; q < TN; ++q) {
+            const int gi = i0 + ty + NTY * r, gj = j0 + tx + NTX * q;
             if (gi < m && gj < n) {
                 cx<T> *cp = c + (int64_t)gi * ldc + gj;
                 cx<T> out = alpha * acc[r][q];
                 if (beta != T(0)) out = out + scale(beta, *cp);
                 *cp = out;
+            }
+        }
+}
+
+// Launch helper: wide or narrow tile by the number of columns n.
+template <class T, class AE, bool CONJ_A, bool CONJ_B>
+inline void cgemm_launch(int m, int n, int K, cx<T> alpha, T beta, const AE *A, int lda, int64_t sA,
+                         const cx<T> *B, int ldb, int64_t sB, cx<T> *C, int ldc, int64_t sC, int adiv, int batch,
+                         cudaStream_t st) {
+    if (n <= 8) {
+        dim3 g(1, (m + 127) / 128, batch);
+        cgemm<T, AE, CONJ_A, CONJ_B, 128, 8, 4, 1><<<g, 256, 0, st>>>(m, n, K, alpha, beta, A, lda, sA, B, ldb, sB,
+                                                                      C, ldc, sC, adiv);
+    } else {
+        dim3 g((n + 63) / 64, (m + 63) / 64, batch);
+        cgemm<T, AE, CONJ_A, CONJ_B><<<g, 256, 0, st>>>(m, n, K, alpha, beta, A, lda, sA, B, ldb, sB, C, ldc, sC,
+                                                        adiv);
+    }
+}
+
+// ------------------------------------------------------------------ resid_gemv
+// R[z] -= t * A[z / adiv] * X[z] for at most 8 columns, binary64: one warp per row,
+// lanes stride over K, shuffle reduction.  Narrow residuals are memory-bound, so the
+// binary64 pipe suffices here.
+template <class AE>
+__global__ void __launch_bounds__(256) resid_gemv(int m, int n, int K, double t, const AE *__restrict__ A, int lda,
+                                                  int64_t sA, const cx<double> *__restrict__ X, int ldx, int64_t sX,
+                                                  cx<double> *__restrict__ Rm, int ldr, int64_t sR, int adiv) {
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    const int row = blockIdx.x * 8 + warp;
+    if (row >= m) return;
+    const AE *a = A + (int64_t)(blockIdx.z / adiv) * sA + (int64_t)row * lda;
+    const cx<double> *x = X + (int64_t)blockIdx.z * sX;
+    cx<double> acc[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) acc[j] = {0.0, 0.0};
+    for (int l = lane; l < K; l += 32) {
+        const cx<double> av = as_cx<double>(a[l]);
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+            if (j < n) acc[j] = cfma(acc[j], av, x[(int64_t)l * ldx + j]);
+    }
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        if (j < n) {
+            double re = acc[j].re, im = acc[j].im;
+            for (int o = 16; o > 0; o >>= 1) {
+                re += __shfl_xor_sync(0xffffffffu, re, o);
+                im += __shfl_xor_sync(0xffffffffu, im, o);
+            }
+            if (lane == 0) {
+                cx<double> *rp = Rm + (int64_t)blockIdx.z * sR + (int64_t)row * ldr + j;
+                rp->re -= t * re;
+                rp->im -= t * im;
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------------------ resid_gemm_f32x2
+// R[z] = R[z] - t * A[z / adiv] * X[z]  (A: m x K, X: K x n, all binary64 in memory)
+// with binary64-level accuracy on the FP32 pipe.  Inside each K-block of 16 the
+// products are accumulated in float-float (dd_fma); the block sums are added in
+// binary64.  The rounding error of a block is ~16 * 2^-47 of its sum of |products|,
+// and the blocks' errors are independent, so the total stays within a few 1e-15 of
+// sum |a_il x_lj| -- far below what the refinement needs.
+template <class AE> EXPM_D cx<f32x2> split_cx(AE v);
+template <> EXPM_D cx<f32x2> split_cx<double>(double v) { return {split_bits(v), {0.f, 0.f}}; }
+template <> EXPM_D cx<f32x2> split_cx<cx<double>>(cx<double> v) { return {split_bits(v.re), split_bits(v.im)}; }
+
+template <class AE>
+__global__ void __launch_bounds__(256) resid_gemm_f32x2(int m, int n, int K, double t, const AE *__restrict__ A,
+                                                        int lda, int64_t sA, const cx<double> *__restrict__ X, int ldx,
+                                                        int64_t sX, cx<double> *__restrict__ Rm, int ldr, int64_t sR,
+                                                        int adiv) {
+    constexpr int BM = 64, BN = 64, BK = 16;
+    __shared__ cx<f32x2> As[BK][BM + 1];
+    __shared__ cx<f32x2> Bs[BK][BN + 1];
+    const AE *a = A + (int64_t)(blockIdx.z / adiv) * sA;
+    const cx<double> *x = X + (int64_t)blockIdx.z * sX;
+    cx<double> *r = Rm + (int64_t)blockIdx.z * sR;
+    const int i0 = blockIdx.y * BM, j0 = blockIdx.x * BN;
+    const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+    const f32x2 z2 = {0.f, 0.f};
+    cx<double> acc[4][4];
+    cx<f32x2> blk[4][4];
+#pragma unroll
+    for (int rr = 0; rr < 4; ++rr)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[rr][q] = {0.0, 0.0};
+    for (int l0 = 0; l0 < K; l0 += BK) {
+        for (int idx = threadIdx.x; idx < BM * BK; idx += 256) {
+            const int ii = idx / BK, ll = idx % BK;
+            const int gi = i0 + ii, gl = l0 + ll;
+            As[ll][ii] = (gi < m && gl < K) ? split_cx<AE>(a[(int64_t)gi * lda + gl]) : cx<f32x2>{z2, z2};
+        }
+        for (int idx = threadIdx.x; idx < BK * BN; idx += 256) {
+            const int ll = idx / BN, jj = idx % BN;
+            const int gl = l0 + ll, gj = j0 + jj;
+            Bs[ll][jj] = (gl < K && gj < n) ? split_cx<cx<double>>(x[(int64_t)gl * ldx + gj]) : cx<f32x2>{z2, z2};
+        }
+        __syncthreads();
+#pragma unroll
+        for (int rr = 0; rr < 4; ++rr)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) blk[rr][q] = {z2, z2};
+#pragma unroll 2
+        for (int l = 0; l < BK; ++l) {
+            cx<f32x2> av[4], bv[4];
+#pragma unroll
+            for (int rr = 0; rr < 4; ++rr) av[rr] = As[l][ty + 16 * rr];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) bv[q] = Bs[l][tx + 16 * q];
+#pragma unroll
+            for (int rr = 0; rr < 4; ++rr)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    cx<f32x2> &c = blk[rr][q];
+                    c.re = dd_fma(av[rr].re, bv[q].re, c.re);
+                    c.re = dd_fma(-av[rr].im, bv[q].im, c.re);
+                    c.im = dd_fma(av[rr].re, bv[q].im, c.im);
+                    c.im = dd_fma(av[rr].im, bv[q].re, c.im);
+                }
+        }
+#pragma unroll
+        for (int rr = 0; rr < 4; ++rr)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                acc[rr][q].re += widen_bits(blk[rr][q].re.hi) + widen_bits(blk[rr][q].re.lo);
+                acc[rr][q].im += widen_bits(blk[rr][q].im.hi) + widen_bits(blk[rr][q].im.lo);
+            }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int rr = 0; rr < 4; ++rr)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int gi = i0 + ty + 16 * rr, gj = j0 + tx + 16 * q;
+            if (gi < m && gj < n) {
+                cx<double> *rp = r + (int64_t)gi * ldr + gj;
+                rp->re -= t * acc[rr][q].re;
+                rp->im -= t * acc[rr][q].im;
             }
         }
 }

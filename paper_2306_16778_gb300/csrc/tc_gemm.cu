@@ -1,0 +1,315 @@
+// tc_gemm.cu -- C -= A * B^T on the 5th-generation tensor cores (tcgen05, kind::tf32).
+//
+// A is M x K and B is N x K, both K-major (row-major with the K index fastest), fp32 in
+// memory and read by the tensor cores as TF32; C is M x N fp32 row-major, updated in
+// place.  This is the trailing update of the mixed-precision LU: with the operands
+// split into TF32 high and low parts and concatenated along K, one call computes
+// C -= A_hi B_hi^T + A_hi B_lo^T + A_lo B_hi^T (the 3xTF32 scheme), i.e. an update with
+// binary32-level accuracy at three TF32 products per term.
+//
+// One CTA computes one 128 x 128 tile of C: warp 0 issues TMA loads of 128 x 32 fp32
+// tiles of A and B (128-byte rows, 128-byte swizzle) into a 4-stage shared-memory ring;
+// one thread of warp 1 issues tcgen05.mma (M = 128, N = 128, K = 8 per instruction)
+// into a 128 x 128 fp32 accumulator in tensor memory and releases each stage with
+// tcgen05.commit; then all four warps read the accumulator back with tcgen05.ld (warp w
+// owns TMEM lanes 32w..32w+31, i.e. rows 32w..32w+31 of the tile) and subtract it from
+// C.  Every mbarrier wait is bounded: on time-out the kernel records an error flag,
+// stops issuing work, drains what it issued, frees its tensor memory and returns.
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cstring>
+#include <mutex>
+
+#include "plan.cuh"
+#include "tc_gemm.cuh"
+
+namespace expm {
+
+namespace {
+
+constexpr int TC_BM = 128, TC_BN = 128, TC_BK = 32;  // BK fp32 = 128 bytes per tile row
+constexpr int TC_STAGES = 4;
+constexpr int TC_TILE_BYTES = TC_BM * TC_BK * 4;      // 16 KB for A, same for B (BN == BM)
+constexpr int TC_SMEM = TC_STAGES * 2 * TC_TILE_BYTES + 1024 + 256;
+constexpr long long TC_SPIN_LIMIT = 1ll << 26;        // bounded mbarrier waits
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+// true once the phase with the given parity has completed; false after the spin limit
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+    const uint32_t addr = smem_u32(bar);
+    for (long long it = 0; it < TC_SPIN_LIMIT; ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done)
+            : "r"(addr), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+__device__ __forceinline__ void tma_load_2d(const CUtensorMap *map, uint64_t *bar, void *dst, int x, int y) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::"r"(
+            smem_u32(dst)),
+        "l"((uint64_t)map), "r"(smem_u32(bar)), "r"(x), "r"(y)
+        : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major tile, 128-byte rows, 128-byte swizzle,
+// 8-row groups 1024 bytes apart.
+__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFF);         // start address
+    d |= (uint64_t)(1) << 16;                        // leading byte offset (unused for swizzled K-major)
+    d |= (uint64_t)((1024 >> 4) & 0x3FFF) << 32;     // stride byte offset: 8 rows x 128 B
+    d |= (uint64_t)1 << 46;                          // descriptor version
+    d |= (uint64_t)2 << 61;                          // swizzle: 128 B
+    return d;
+}
+
+// Instruction descriptor of kind::tf32: D fp32, A and B TF32, both K-major, M x N.
+__host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
+    return (1u << 4)                       // D format: F32
+           | (2u << 7)                     // A format: TF32
+           | (2u << 10)                    // B format: TF32
+           | ((uint32_t)(N >> 3) << 17)    // N / 8
+           | ((uint32_t)(M >> 4) << 24);   // M / 16
+}
+
+__global__ void __launch_bounds__(128, 1)
+    tc_gemm_tf32_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, int M,
+                        int N, int K, float *__restrict__ C, int ldc, int *__restrict__ err_flag) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    // 1024-byte aligned stage buffers (required by the 128-byte swizzle)
+    unsigned char *base = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    unsigned char *sA = base;
+    unsigned char *sB = base + TC_STAGES * TC_TILE_BYTES;
+    uint64_t *full = (uint64_t *)(sB + TC_STAGES * TC_TILE_BYTES);
+    uint64_t *empty = full + TC_STAGES;
+    uint64_t *accum = empty + TC_STAGES;
+    uint32_t *tmem_slot = (uint32_t *)(accum + 1);
+    __shared__ int abort_flag;
+    __shared__ int consumed;   // k-blocks whose stage the MMA issuer has taken
+    __shared__ int produced;   // k-blocks whose TMA loads were issued
+
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    const int n0 = blockIdx.x * TC_BN, m0 = blockIdx.y * TC_BM;
+    const int nk = (K + TC_BK - 1) / TC_BK;
+
+    if (threadIdx.x == 0) {
+        abort_flag = 0;
+        consumed = 0;
+        produced = 0;
+        for (int s = 0; s < TC_STAGES; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        mbar_init(accum, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {  // allocate 128 TMEM columns (the 128 x 128 fp32 accumulator)
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 128;" ::"r"(smem_u32(tmem_slot))
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 0 && lane == 0) {
+        // TMA producer
+        for (int kb = 0; kb < nk; ++kb) {
+            const int s = kb % TC_STAGES;
+            const uint32_t ph = (uint32_t)(kb / TC_STAGES) & 1u;
+            if (!mbar_wait(&empty[s], ph ^ 1u)) {
+                atomicExch(&abort_flag, 1);
+                break;
+            }
+            if (*(volatile int *)&abort_flag) break;
+            mbar_expect_tx(&full[s], 2 * TC_TILE_BYTES);
+            tma_load_2d(&mapA, &full[s], sA + s * TC_TILE_BYTES, kb * TC_BK, m0);
+            tma_load_2d(&mapB, &full[s], sB + s * TC_TILE_BYTES, kb * TC_BK, n0);
+            produced = kb + 1;
+        }
+    } else if (warp == 1 && lane == 0) {
+        // MMA issuer
+        constexpr uint32_t idesc = idesc_tf32(TC_BM, TC_BN);
+        int issued = 0;
+        for (int kb = 0; kb < nk; ++kb) {
+            const int s = kb % TC_STAGES;
+            const uint32_t ph = (uint32_t)(kb / TC_STAGES) & 1u;
+            if (!mbar_wait(&full[s], ph) || *(volatile int *)&abort_flag) {
+                atomicExch(&abort_flag, 1);
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t a0 = smem_u32(sA + s * TC_TILE_BYTES), b0 = smem_u32(sB + s * TC_TILE_BYTES);
+#pragma unroll
+            for (int kk = 0; kk < TC_BK / 8; ++kk) {  // K = 8 TF32 = 32 bytes per instruction
+                const uint64_t ad = smem_desc_sw128(a0 + kk * 32), bd = smem_desc_sw128(b0 + kk * 32);
+                const uint32_t acc = (kb > 0 || kk > 0) ? 1u : 0u;
+                asm volatile(
+                    "{\n\t.reg .pred p;\n\t"
+                    "setp.ne.u32 p, %4, 0;\n\t"
+                    "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+                    "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+                    : "memory");
+            }
+            // release the stage once these MMAs have read it
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                             smem_u32(&empty[s]))
+                         : "memory");
+            ++issued;
+            consumed = kb + 1;
+        }
+        // accumulator complete (or, after an abort, everything issued has drained)
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                         smem_u32(accum))
+                     : "memory");
+        (void)issued;
+    }
+    __syncwarp();
+
+    // epilogue: all four warps
+    const bool ok = mbar_wait(accum, 0u);
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const int aborted = *(volatile int *)&abort_flag;
+    if (!ok || aborted) {
+        if (threadIdx.x == 0) atomicExch(err_flag, 1);
+    } else {
+        // Each warp owns rows m0 + 32w .. +31.  Per 32-column chunk: tcgen05.ld gives each
+        // lane one row; the chunk is transposed through shared memory (the stage buffers
+        // are free now) so that C is read and written one 128-byte row segment at a time.
+        float *stage = reinterpret_cast<float *>(base) + warp * 32 * 33;
+        const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+#pragma unroll 1
+        for (int c0 = 0; c0 < TC_BN; c0 += 32) {
+            uint32_t v[32];
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
+                "%14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+                : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+                  "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
+                  "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]),
+                  "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]),
+                  "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+                : "r"(tmem + lane_base + (uint32_t)c0));
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+            for (int j = 0; j < 32; ++j) stage[lane * 33 + j] = __uint_as_float(v[j]);  // row lane, column j
+            __syncwarp();
+            const int col = n0 + c0 + lane;
+#pragma unroll 4
+            for (int r = 0; r < 32; ++r) {
+                const int row = m0 + warp * 32 + r;
+                if (row < M && col < N) C[(int64_t)row * ldc + col] -= stage[r * 33 + lane];
+            }
+            __syncwarp();
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (threadIdx.x == 0 && (aborted || !ok)) {
+        // after an abort, wait (bounded) for TMA copies that were issued but not consumed,
+        // so that none lands in shared memory after this CTA has exited
+        for (int kb = consumed; kb < produced; ++kb)
+            mbar_wait(&full[kb % TC_STAGES], (uint32_t)(kb / TC_STAGES) & 1u);
+    }
+    __syncthreads();
+    if (warp == 1) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 128;" ::"r"(tmem) : "memory");
+    }
+}
+
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link to libcuda)
+using EncodeFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                              const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                              CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeFn encode_fn() {
+    static std::once_flag once;
+    static EncodeFn fn = nullptr;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPoint("cuTensorMapEncodeTiled", &p, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (EncodeFn)p;
+    });
+    return fn;
+}
+
+bool make_map(CUtensorMap *map, const float *ptr, int rows, int cols, int ld) {
+    EncodeFn enc = encode_fn();
+    if (!enc) return false;
+    const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)ld * sizeof(float)};
+    const cuuint32_t box[2] = {TC_BK, TC_BM};
+    const cuuint32_t estr[2] = {1, 1};
+    return enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void *)ptr, dims, strides, box, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+}  // namespace
+
+bool tc_gemm_supported(int M, int N, int K, const void *A, int lda, const void *B, int ldb) {
+    if (M < 1 || N < 1 || K < 1) return false;
+    if ((lda % 4) || (ldb % 4) || ((uintptr_t)A % 16) || ((uintptr_t)B % 16)) return false;
+    return encode_fn() != nullptr;
+}
+
+cudaError_t tc_gemm_tf32_sub(int M, int N, int K, const float *A, int lda, const float *B, int ldb, float *C, int ldc,
+                             int *err_flag, cudaStream_t st) {
+    CUtensorMap ma, mb;
+    if (!make_map(&ma, A, M, K, lda) || !make_map(&mb, B, N, K, ldb)) return cudaErrorInvalidValue;
+    static std::once_flag once;
+    static cudaError_t attr = cudaSuccess;
+    std::call_once(once, [] {
+        attr = cudaFuncSetAttribute(tc_gemm_tf32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
+    });
+    if (attr != cudaSuccess) return attr;
+    dim3 grid((N + TC_BN - 1) / TC_BN, (M + TC_BM - 1) / TC_BM, 1);
+    tc_gemm_tf32_kernel<<<grid, 128, TC_SMEM, st>>>(ma, mb, M, N, K, C, ldc, err_flag);
+    return cudaGetLastError();
+}
+
+}  // namespace expm
+
+// Test hook (not part of the documented interface): C -= A B^T with the tensor-core
+// kernel on device buffers; returns 0, or 1 for unsupported arguments / CUDA errors,
+// or 2 when a bounded wait gave up.
+extern "C" int expm_internal_tc_gemm_tf32(int M, int N, int K, const float *A, int lda, const float *B, int ldb,
+                                          float *C, int ldc) {
+    using namespace expm;
+    if (!tc_gemm_supported(M, N, K, A, lda, B, ldb)) return 1;
+    int *flag = nullptr;
+    if (cudaMalloc(&flag, sizeof(int)) != cudaSuccess) return 1;
+    cudaMemset(flag, 0, sizeof(int));
+    cudaError_t e = tc_gemm_tf32_sub(M, N, K, A, lda, B, ldb, C, ldc, flag, 0);
+    int h = 0;
+    if (e == cudaSuccess) e = cudaMemcpy(&h, flag, sizeof(int), cudaMemcpyDeviceToHost);
+    cudaFree(flag);
+    if (e != cudaSuccess) return 1;
+    return h ? 2 : 0;
+}

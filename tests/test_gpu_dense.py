@@ -62,9 +62,9 @@ def test_dense_small_workload(plans):
     assert 0 < info.growth_max_seen < 1e3
 
 
-@pytest.mark.parametrize("prec", [P.EXPM_FP64, P.EXPM_MIXED_FP32])
+@pytest.mark.parametrize("prec", [P.EXPM_FP64, P.EXPM_MIXED_FP32, P.EXPM_MIXED_TF32X3])
 @pytest.mark.parametrize("n,k,deg", [(1, 1, 12), (5, 2, 16), (63, 3, 12), (64, 1, 16), (65, 5, 12),
-                                     (130, 70, 16), (257, 4, 12)])
+                                     (130, 70, 16), (257, 4, 12), (333, 9, 16)])
 def test_complex_hermitian(plans, prec, n, k, deg):
     """Ragged panel widths (n not a multiple of 64), several RHS tiles."""
     g = workloads.rng(300 + n + k)
@@ -99,12 +99,13 @@ def test_time_and_shift(plans):
     assert matrix.rel_err(Y, _oracle(A, V, 16, t=0.5, c=10.0)) <= 1e-12
 
 
-def test_mixed_matches_fp64_path(plans):
-    """Mid-size complex Hermitian: the refined mixed path agrees with the binary64 path."""
+@pytest.mark.parametrize("prec", [P.EXPM_MIXED_FP32, P.EXPM_MIXED_TF32X3])
+def test_mixed_matches_fp64_path(plans, prec):
+    """Mid-size complex Hermitian: the refined mixed paths agree with the binary64 path."""
     g = workloads.rng(312)
     A, Q, mu, V = workloads.dense_symmetric(512, -50.0, 0.0, 32, g, True)
     Y64, _ = _gpu(plans[16], A, V, P.EXPM_FP64)
-    Ymx, info = _gpu(plans[16], A, V, P.EXPM_MIXED_FP32)
+    Ymx, info = _gpu(plans[16], A, V, prec)
     assert matrix.rel_err(Ymx, Y64) <= 1e-10
     assert matrix.rel_err(Y64, _oracle(A, V, 16)) <= 1e-12
     assert info.resid_rel_max <= 1e-14
@@ -139,3 +140,25 @@ def test_growth_limit_is_reported(plans):
     info = P.expm_apply_dense(plans[12], dA, dV, dY, growth_max=0.5, check=False)
     assert info.status_worst == 3 and info.growth_max_seen >= 0.5
     assert matrix.rel_err(dY.cpu().numpy(), _oracle(A, V, 12)) <= 1e-12
+
+
+def test_tensor_core_gemm_against_torch():
+    """The tcgen05 kind::tf32 kernel: C -= A B^T equals the product of the TF32-rounded
+    operands (fp64 reference) to fp32 accumulation accuracy, on ragged tile edges."""
+    import ctypes
+    f = P.lib.expm_internal_tc_gemm_tf32
+    f.restype = ctypes.c_int
+    f.argtypes = [ctypes.c_int] * 3 + [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_int,
+                                       ctypes.c_void_p, ctypes.c_int]
+    gen = torch.Generator(device="cpu").manual_seed(7)
+    for M, N, K in [(128, 128, 32), (200, 72, 96), (1000, 520, 384), (129, 257, 36)]:
+        A = torch.randn(M, K, generator=gen).to(DEV)
+        B = torch.randn(N, K, generator=gen).to(DEV)
+        C = torch.randn(M, N, generator=gen).to(DEV)
+        C0 = C.clone()
+        assert f(M, N, K, A.data_ptr(), K, B.data_ptr(), K, C.data_ptr(), N) == 0
+        torch.cuda.synchronize()
+        tf = lambda x: (x.view(torch.int32) & ~0x1FFF).view(torch.float32).double()
+        ref = C0.double() - tf(A) @ tf(B).T
+        err = (C.double() - ref).abs().max().item() / ref.abs().max().item()
+        assert err < 1e-5, (M, N, K, err)
