@@ -241,7 +241,9 @@ static cudaError_t lu_blocked(int n, int batch, cx<T> *F, cudaStream_t st, Profi
                                                                                  diag + (int64_t)nb * n, n, bs);
             return cudaGetLastError();
         }));
-        if (tc != nullptr && sizeof(T) == 4 && rest >= 128) {
+        if (tc != nullptr && sizeof(T) == 4 && rest >= 128 &&
+            tc_gemm_supported(rest, 2 * rest, 6 * nb, tc->Ap, 6 * nb, tc->Bp, 6 * nb,
+                              F + (int64_t)(p + nb) * n + p + nb, 2 * n)) {
             // A22 -= L21 U12 as one real product per matrix on the tensor cores
             EXPM_TRY(prof.timed("split_tc_operands", st, [&] {
                 split_tc_operands<<<dim3(grid1d((int64_t)rest * nb), 1, batch), 256, 0, st>>>(

@@ -11,9 +11,10 @@
 // tiles of A and B (128-byte rows, 128-byte swizzle) into a 4-stage shared-memory ring;
 // one thread of warp 1 issues tcgen05.mma (M = 128, N = 128, K = 8 per instruction)
 // into a 128 x 128 fp32 accumulator in tensor memory and releases each stage with
-// tcgen05.commit; then all four warps read the accumulator back with tcgen05.ld (warp w
-// owns TMEM lanes 32w..32w+31, i.e. rows 32w..32w+31 of the tile) and subtract it from
-// C.  Every mbarrier wait is bounded: on time-out the kernel records an error flag,
+// tcgen05.commit; the C tile is fetched by TMA into shared memory while the K loop runs.
+// Then all four warps read the accumulator back with tcgen05.ld (warp w owns TMEM lanes
+// 32w..32w+31, i.e. rows 32w..32w+31 of the tile), subtract it from the staged C tile
+// and write the result back with coalesced row stores.  Every mbarrier wait is bounded: on time-out the kernel records an error flag,
 // stops issuing work, drains what it issued, frees its tensor memory and returns.
 #include <cuda.h>
 #include <cuda_runtime.h>
@@ -32,7 +33,8 @@ namespace {
 constexpr int TC_BM = 128, TC_BN = 128, TC_BK = 32;  // BK fp32 = 128 bytes per tile row
 constexpr int TC_STAGES = 4;
 constexpr int TC_TILE_BYTES = TC_BM * TC_BK * 4;      // 16 KB for A, same for B (BN == BM)
-constexpr int TC_SMEM = TC_STAGES * 2 * TC_TILE_BYTES + 1024 + 256;
+constexpr int TC_CTILE_BYTES = TC_BM * TC_BN * 4;     // the C tile, prefetched by TMA
+constexpr int TC_SMEM = TC_STAGES * 2 * TC_TILE_BYTES + TC_CTILE_BYTES + 1024 + 256;
 constexpr long long TC_SPIN_LIMIT = 1ll << 26;        // bounded mbarrier waits
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
@@ -95,17 +97,20 @@ __host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
 }
 
 __global__ void __launch_bounds__(128, 1)
-    tc_gemm_tf32_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, int M,
-                        int N, int K, float *__restrict__ C, int ldc, int *__restrict__ err_flag) {
+    tc_gemm_tf32_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
+                        const __grid_constant__ CUtensorMap mapC, int M, int N, int K, float *__restrict__ C, int ldc,
+                        int *__restrict__ err_flag) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     // 1024-byte aligned stage buffers (required by the 128-byte swizzle)
     unsigned char *base = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     unsigned char *sA = base;
     unsigned char *sB = base + TC_STAGES * TC_TILE_BYTES;
-    uint64_t *full = (uint64_t *)(sB + TC_STAGES * TC_TILE_BYTES);
+    float *sC = reinterpret_cast<float *>(sB + TC_STAGES * TC_TILE_BYTES);  // [TC_BM][TC_BN]
+    uint64_t *full = (uint64_t *)((unsigned char *)sC + TC_CTILE_BYTES);
     uint64_t *empty = full + TC_STAGES;
     uint64_t *accum = empty + TC_STAGES;
-    uint32_t *tmem_slot = (uint32_t *)(accum + 1);
+    uint64_t *cbar = accum + 1;
+    uint32_t *tmem_slot = (uint32_t *)(cbar + 1);
     __shared__ int abort_flag;
     __shared__ int consumed;   // k-blocks whose stage the MMA issuer has taken
     __shared__ int produced;   // k-blocks whose TMA loads were issued
@@ -123,6 +128,7 @@ __global__ void __launch_bounds__(128, 1)
             mbar_init(&empty[s], 1);
         }
         mbar_init(accum, 1);
+        mbar_init(cbar, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 1) {  // allocate 128 TMEM columns (the 128 x 128 fp32 accumulator)
@@ -136,7 +142,9 @@ __global__ void __launch_bounds__(128, 1)
     const uint32_t tmem = *tmem_slot;
 
     if (warp == 0 && lane == 0) {
-        // TMA producer
+        // TMA producer: the C tile first (consumed only by the epilogue), then the K ring
+        mbar_expect_tx(cbar, TC_CTILE_BYTES);
+        tma_load_2d(&mapC, cbar, sC, n0, m0);
         for (int kb = 0; kb < nk; ++kb) {
             const int s = kb % TC_STAGES;
             const uint32_t ph = (uint32_t)(kb / TC_STAGES) & 1u;
@@ -195,11 +203,13 @@ __global__ void __launch_bounds__(128, 1)
     const int aborted = *(volatile int *)&abort_flag;
     if (!ok || aborted) {
         if (threadIdx.x == 0) atomicExch(err_flag, 1);
+    } else if (!mbar_wait(cbar, 0u)) {
+        if (lane == 0) atomicExch(err_flag, 1);
     } else {
         // Each warp owns rows m0 + 32w .. +31.  Per 32-column chunk: tcgen05.ld gives each
-        // lane one row; the chunk is transposed through shared memory (the stage buffers
-        // are free now) so that C is read and written one 128-byte row segment at a time.
-        float *stage = reinterpret_cast<float *>(base) + warp * 32 * 33;
+        // lane one row of the accumulator; it is subtracted from the prefetched C tile in
+        // shared memory, and the chunk is then written back one 128-byte row segment at a
+        // time (lane = column).
         const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
 #pragma unroll 1
         for (int c0 = 0; c0 < TC_BN; c0 += 32) {
@@ -214,14 +224,17 @@ __global__ void __launch_bounds__(128, 1)
                   "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
                 : "r"(tmem + lane_base + (uint32_t)c0));
             asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            // transpose the chunk through a padded per-warp buffer (the K-ring stages are free now)
+            float *stage = reinterpret_cast<float *>(base) + warp * 32 * 33;
 #pragma unroll
-            for (int j = 0; j < 32; ++j) stage[lane * 33 + j] = __uint_as_float(v[j]);  // row lane, column j
+            for (int j = 0; j < 32; ++j) stage[lane * 33 + j] = __uint_as_float(v[j]);
             __syncwarp();
             const int col = n0 + c0 + lane;
-#pragma unroll 4
+#pragma unroll 8
             for (int r = 0; r < 32; ++r) {
                 const int row = m0 + warp * 32 + r;
-                if (row < M && col < N) C[(int64_t)row * ldc + col] -= stage[r * 33 + lane];
+                if (row < M && col < N)
+                    C[(int64_t)row * ldc + col] = sC[(warp * 32 + r) * TC_BN + c0 + lane] - stage[r * 33 + lane];
             }
             __syncwarp();
         }
@@ -259,30 +272,35 @@ EncodeFn encode_fn() {
     return fn;
 }
 
-bool make_map(CUtensorMap *map, const float *ptr, int rows, int cols, int ld) {
+// K-major operand tiles (TC_BK x TC_BM, 128-byte swizzle) or the plain C tile
+// (TC_BN x TC_BM, no swizzle); out-of-range elements read as zero.
+bool make_map(CUtensorMap *map, const float *ptr, int rows, int cols, int ld, bool ctile) {
     EncodeFn enc = encode_fn();
     if (!enc) return false;
     const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
     const cuuint64_t strides[1] = {(cuuint64_t)ld * sizeof(float)};
-    const cuuint32_t box[2] = {TC_BK, TC_BM};
+    const cuuint32_t box[2] = {ctile ? (cuuint32_t)TC_BN : (cuuint32_t)TC_BK, (cuuint32_t)TC_BM};
     const cuuint32_t estr[2] = {1, 1};
     return enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void *)ptr, dims, strides, box, estr,
-               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+               CU_TENSOR_MAP_INTERLEAVE_NONE, ctile ? CU_TENSOR_MAP_SWIZZLE_NONE : CU_TENSOR_MAP_SWIZZLE_128B,
+               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 }  // namespace
 
-bool tc_gemm_supported(int M, int N, int K, const void *A, int lda, const void *B, int ldb) {
+bool tc_gemm_supported(int M, int N, int K, const void *A, int lda, const void *B, int ldb, const void *C, int ldc) {
     if (M < 1 || N < 1 || K < 1) return false;
-    if ((lda % 4) || (ldb % 4) || ((uintptr_t)A % 16) || ((uintptr_t)B % 16)) return false;
+    if ((lda % 4) || (ldb % 4) || (ldc % 4) || ((uintptr_t)A % 16) || ((uintptr_t)B % 16) || ((uintptr_t)C % 16))
+        return false;
     return encode_fn() != nullptr;
 }
 
 cudaError_t tc_gemm_tf32_sub(int M, int N, int K, const float *A, int lda, const float *B, int ldb, float *C, int ldc,
                              int *err_flag, cudaStream_t st) {
-    CUtensorMap ma, mb;
-    if (!make_map(&ma, A, M, K, lda) || !make_map(&mb, B, N, K, ldb)) return cudaErrorInvalidValue;
+    CUtensorMap ma, mb, mc;
+    if (!make_map(&ma, A, M, K, lda, false) || !make_map(&mb, B, N, K, ldb, false) ||
+        !make_map(&mc, C, M, N, ldc, true))
+        return cudaErrorInvalidValue;
     static std::once_flag once;
     static cudaError_t attr = cudaSuccess;
     std::call_once(once, [] {
@@ -290,7 +308,7 @@ cudaError_t tc_gemm_tf32_sub(int M, int N, int K, const float *A, int lda, const
     });
     if (attr != cudaSuccess) return attr;
     dim3 grid((N + TC_BN - 1) / TC_BN, (M + TC_BM - 1) / TC_BM, 1);
-    tc_gemm_tf32_kernel<<<grid, 128, TC_SMEM, st>>>(ma, mb, M, N, K, C, ldc, err_flag);
+    tc_gemm_tf32_kernel<<<grid, 128, TC_SMEM, st>>>(ma, mb, mc, M, N, K, C, ldc, err_flag);
     return cudaGetLastError();
 }
 
@@ -302,7 +320,7 @@ cudaError_t tc_gemm_tf32_sub(int M, int N, int K, const float *A, int lda, const
 extern "C" int expm_internal_tc_gemm_tf32(int M, int N, int K, const float *A, int lda, const float *B, int ldb,
                                           float *C, int ldc) {
     using namespace expm;
-    if (!tc_gemm_supported(M, N, K, A, lda, B, ldb)) return 1;
+    if (!tc_gemm_supported(M, N, K, A, lda, B, ldb, C, ldc)) return 1;
     int *flag = nullptr;
     if (cudaMalloc(&flag, sizeof(int)) != cudaSuccess) return 1;
     cudaMemset(flag, 0, sizeof(int));
