@@ -49,10 +49,12 @@ SM_MAX_MHZ = 2070.0
 # algorithmic flops per (system, column, row) of the dominant kernel (tri_block_solve):
 # forward 9 (t = v - e d' : 3, d' = g t : 6), back 8 (x = d' - c' x+ : 8), sum Re(W x) 4
 FLOPS_K3 = 21
-# dram bytes per launch of tri_block_solve<f64> from one ncu capture, valid while the
-# kernel source hashes to TRAFFIC_SRC_SHA (otherwise reported as null)
-TRAFFIC_K3 = None
-TRAFFIC_SRC_SHA = None
+# dram bytes (read + write) per launch of tri_block_solve<f64> at N = 2^20: one ncu
+# capture at N = 2^19 (1.2923 GB: 729.9 MB read + 562.3 MB write) scaled by 2, the
+# traffic being proportional to N; valid while the kernel's source text hashes to
+# TRAFFIC_SRC_SHA (otherwise reported as null)
+TRAFFIC_K3 = 2.5845e9
+TRAFFIC_SRC_SHA = "3d4a93a079644dc8"
 
 
 def log(*a):
@@ -143,8 +145,12 @@ class ClockSampler:
 
 
 def kernel_sha() -> str:
-    src = os.path.join(ROOT, "paper_2306_16778_gb300", "csrc", "tridiag.cu")
-    return hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    """Hash of the source text of the tri_block_solve kernel template."""
+    src = open(os.path.join(ROOT, "paper_2306_16778_gb300", "csrc", "tridiag.cu")).read()
+    i = src.index("__global__ void __launch_bounds__(128) tri_block_solve(")
+    i = src.rindex("template <class R, int LG>", 0, i)
+    j = src.index("\n}\n", i) + 3
+    return hashlib.sha256(src[i:j].encode()).hexdigest()[:16]
 
 
 def run_peaks():
