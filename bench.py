@@ -49,6 +49,21 @@ SM_MAX_MHZ = 2070.0
 # algorithmic flops per (system, column, row) of the dominant kernel (tri_block_solve):
 # forward 9 (t = v - e d' : 3, d' = g t : 6), back 8 (x = d' - c' x+ : 8), sum Re(W x) 4
 FLOPS_K3 = 21
+
+
+def _hbm_peak() -> float:
+    """Measured copy bandwidth of this GPU pool (GB/s), else the recipe's fallback."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"])
+    except (OSError, ValueError, KeyError):
+        return 6800.0
+
+
+HBM_GBS = _hbm_peak()
+# the binary32 + refinement path: one correction pass at most, stopping test 1e-10
+MIXED_OPTS = dict(tol=1e-10, max_refine=1)
+# algorithmic HBM bytes of one evaluation: d, e, V read, Y written (binary64)
 # dram bytes (read + write) per launch of tri_block_solve<f64> at N = 2^20: one ncu
 # capture at N = 2^19 (1.2923 GB: 729.9 MB read + 562.3 MB write) scaled by 2, the
 # traffic being proportional to N; valid while the kernel's source text hashes to
@@ -73,6 +88,8 @@ def parse():
                     help="rows of the Laplacian (smaller cases are for profiling only)")
     ap.add_argument("--fp64-only", action="store_true",
                     help="time only the binary64 path (profiling runs)")
+    ap.add_argument("--mixed-only", action="store_true",
+                    help="time only the binary32 + refinement path (profiling runs)")
     ap.add_argument("--workload", default="laplacian", choices=["laplacian", "dense", "batched", "served"],
                     help="laplacian: the headline line; the others print their own lines "
                          "(dense 4096 Hermitian x 256 RHS; 4096-instance uneven batch; served stream)")
@@ -201,9 +218,9 @@ def run_ours(args):
     S = DEGREE // 2
     K, W = args.steps, args.warmup
 
-    def timed_loop(prec, steps):
+    def timed_loop(prec, steps, **kw):
         for _ in range(W):
-            P.expm_apply_tridiag(plan, d, e, V, Y, prec=prec)
+            P.expm_apply_tridiag(plan, d, e, V, Y, prec=prec, want_info=False, **kw)
         torch.cuda.synchronize()
         P.expm_profile_enable(plan, True)
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
@@ -212,7 +229,7 @@ def run_ours(args):
         for a, b in ev:
             flush.zero_()
             a.record()
-            P.expm_apply_tridiag(plan, d, e, V, Y, prec=prec)
+            P.expm_apply_tridiag(plan, d, e, V, Y, prec=prec, want_info=False, **kw)
             b.record()
         torch.cuda.synchronize()
         barrier()
@@ -221,6 +238,13 @@ def run_ours(args):
         P.expm_profile_enable(plan, False)
         return ms, prof
 
+    if args.mixed_only:
+        msmx, profmx = timed_loop(P.EXPM_MIXED_FP32, K, **MIXED_OPTS)
+        if rank == 0:
+            print(json.dumps({"mixed_only": True, "rows": rows, "ms_per_step": sum(msmx) / K,
+                              "kernels_ms": {k: v[1] / v[0] for k, v in profmx.items()}}), flush=True)
+        plan.close()
+        return
     sampler = ClockSampler(local) if rank == 0 else None
     if sampler:
         sampler.start()
@@ -235,6 +259,11 @@ def run_ours(args):
         return
     msff, profff = timed_loop(P.EXPM_MIXED_F32X2, K)
     Yff = Y.cpu().numpy() if rank == 0 else None
+    # binary32 factors + refinement: the asynchronous timed calls do not read the
+    # refinement state back; one call with info afterwards reports it
+    msmx, profmx = timed_loop(P.EXPM_MIXED_FP32, K, **MIXED_OPTS)
+    infomx = P.expm_apply_tridiag(plan, d, e, V, Y, prec=P.EXPM_MIXED_FP32, check=False, **MIXED_OPTS)
+    Ymx = Y.cpu().numpy() if rank == 0 else None
 
     # end to end through the C interface with pinned host buffers (synchronous call)
     hd, he, hV = (torch.from_numpy(x).pin_memory() for x in (w["d"], w["e"], w["V"]))
@@ -251,11 +280,12 @@ def run_ours(args):
 
     tot64 = sum(ms64) / 1e3
     totff = sum(msff) / 1e3
+    totmx = sum(msmx) / 1e3
     if world > 1:
         import torch.distributed as dist
-        t = torch.tensor([tot64, totff, e2e_s], dtype=torch.float64, device=dev)
+        t = torch.tensor([tot64, totff, totmx, e2e_s], dtype=torch.float64, device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        tot64, totff, e2e_s = (float(x) for x in t.tolist())
+        tot64, totff, totmx, e2e_s = (float(x) for x in t.tolist())
     if rank != 0:
         return
 
@@ -272,6 +302,7 @@ def run_ours(args):
     achieved = flops / kavg_s / 1e12
     peak = SMS * FP64_FLOP_PER_CLK_SM * SM_MAX_MHZ * 1e6 / 1e12
     traffic = TRAFFIC_K3 if (TRAFFIC_K3 is not None and TRAFFIC_SRC_SHA == kernel_sha()) else None
+    hbm_bytes = 8 * (rows + (rows - 1) + 2 * rows * NRHS)
 
     line = {
         "metric": METRIC,
@@ -291,10 +322,23 @@ def run_ours(args):
                    "l2": "256 MB buffer rewritten between timed steps (outside the step events)",
                    "parallelism": f"replicas{world}"},
         "latency_ms": {"p50": round(pct(ms64, 50), 4), "p99": round(pct(ms64, 99), 4)},
-        "mixed": {"prec": "float-float (EXPM_MIXED_F32X2)", "value": round(world * K / totff, 3),
-                  "unit": "evals/s", "ms_per_step": round(totff * 1e3 / K, 4),
-                  "latency_ms": {"p50": round(pct(msff, 50), 4), "p99": round(pct(msff, 99), 4)},
-                  "kernels_ms": {k: round(v[1] / v[0], 4) for k, v in profff.items()}},
+        "mixed": {"prec": "binary32 factors and solves + float-float-residual refinement (EXPM_MIXED_FP32, "
+                          f"tol {MIXED_OPTS['tol']:g}, max_refine {MIXED_OPTS['max_refine']})",
+                  "value": round(world * K / totmx, 3), "unit": "evals/s", "ms_per_step": round(totmx * 1e3 / K, 4),
+                  "latency_ms": {"p50": round(pct(msmx, 50), 4), "p99": round(pct(msmx, 99), 4)},
+                  "speedup_vs_fp64": round(tot64 / totmx, 3),
+                  "refine_passes": infomx.refine_iters_max, "resid_rel": infomx.resid_rel_max,
+                  "status": infomx.status_worst,
+                  "hbm_effective": {"achieved_gbs": round(hbm_bytes * K / totmx / 1e9, 2), "peak_gbs": HBM_GBS,
+                                    "frac": round(hbm_bytes * K / totmx / 1e9 / HBM_GBS, 5)},
+                  "kernels_ms": {k: round(v[1] / v[0], 4) for k, v in profmx.items()}},
+        "mixed_f32x2": {"prec": "float-float (EXPM_MIXED_F32X2)", "value": round(world * K / totff, 3),
+                        "unit": "evals/s", "ms_per_step": round(totff * 1e3 / K, 4),
+                        "latency_ms": {"p50": round(pct(msff, 50), 4), "p99": round(pct(msff, 99), 4)},
+                        "kernels_ms": {k: round(v[1] / v[0], 4) for k, v in profff.items()}},
+        "hbm_effective": {"achieved_gbs": round(hbm_bytes * K / tot64 / 1e9, 2), "peak_gbs": HBM_GBS,
+                          "frac": round(hbm_bytes * K / tot64 / 1e9 / HBM_GBS, 5),
+                          "bytes_per_eval": hbm_bytes, "note": "algorithmic bytes (d, e, V in; Y out) / step time"},
         "kernels_ms": {k: round(v[1] / v[0], 4) for k, v in prof64.items()},
         "roofline": {"kernel": kname, "bound": "alu", "achieved": round(achieved, 4),
                      "peak": round(peak, 4), "unit": "TFLOP/s", "frac": round(achieved / peak, 4),
@@ -314,7 +358,8 @@ def run_ours(args):
         line["cpu_baseline"] = {"value": round(1.0 / t, 5), "unit": "evals/s", "cores": workers, "kind": "oracle",
                                 "sample": f"one full evaluation (N=2^20, 8 RHS, all 16 poles, LAPACK banded LU "
                                           f"per pole on {workers} threads): {t:.2f} s"}
-        line["parity"] = {"fp64_rel_err": matrix.rel_err(Y64, Yo), "mixed_rel_err": matrix.rel_err(Yff, Yo),
+        line["parity"] = {"fp64_rel_err": matrix.rel_err(Y64, Yo), "mixed_rel_err": matrix.rel_err(Ymx, Yo),
+                          "mixed_f32x2_rel_err": matrix.rel_err(Yff, Yo),
                           "tolerance": {"fp64": 1e-12, "mixed": 1e-8}}
     print(json.dumps(line), flush=True)
     plan.close()

@@ -67,7 +67,9 @@ typedef enum expm_precision {
     EXPM_FP64 = 0,        /* binary64 arithmetic throughout                         */
     EXPM_MIXED_F32X2 = 1, /* tridiagonal: float-float (pairs of binary32, ~48-bit
                              significand) on the FP32 pipe; dense: as EXPM_MIXED_FP32 */
-    EXPM_MIXED_FP32 = 2,  /* dense: binary32 LU + binary64-residual refinement       */
+    EXPM_MIXED_FP32 = 2,  /* dense: binary32 LU + binary64-residual refinement;
+                             tridiagonal: binary32 factors and solves + refinement
+                             with float-float residuals (FP32 pipe only)            */
     EXPM_MIXED_TF32X3 = 3 /* dense: LU trailing updates on the tensor cores with a
                              3-term TF32 split, + binary64-residual refinement      */
 } expm_precision;
@@ -82,8 +84,13 @@ typedef struct expm_opts {
     double growth_max;  /* allowed growth max|U|/max|A - lambda I| of the unpivoted LU
                            (dense paths; default 1e6)                              */
     void *stream;       /* cudaStream_t to enqueue on (NULL = legacy default stream) */
-    int flags;          /* reserved, must be 0                                      */
+    int flags;          /* 0, or EXPM_FLAG_SKIP_FINAL_RESIDUAL (see below)          */
 } expm_opts;
+
+/* EXPM_MIXED_FP32 tridiagonal path only: do not form the residual after the last
+ * correction pass.  Saves one residual evaluation per call; info.resid_rel_max then
+ * reports the residual before the last pass and EXPM_ENOCONV is never returned. */
+#define EXPM_FLAG_SKIP_FINAL_RESIDUAL 1
 
 typedef struct expm_info {
     int refine_iters_max;   /* largest number of refinement sweeps any pole used   */
@@ -147,8 +154,24 @@ expm_status expm_plan_destroy(expm_plan plan);
  *   r             number of right-hand sides, 1 <= r <= 64
  *   Y             N x r output, row-major; complex when V or e is complex, else real.
  *                 Must not overlap V, d or e.
- *   opts          precision EXPM_FP64 or EXPM_MIXED_F32X2; t, shift_c, stream
- *   info          optional (may be NULL); refine/growth fields are not used here
+ *   opts          precision EXPM_FP64, EXPM_MIXED_F32X2 or EXPM_MIXED_FP32; t, shift_c,
+ *                 stream; for EXPM_MIXED_FP32 also tol, max_refine and flags
+ *   info          optional (may be NULL).  EXPM_FP64 / EXPM_MIXED_F32X2: not used
+ *                 (zeroed).  EXPM_MIXED_FP32: when info is given the call waits for
+ *                 the result and reports refine_iters_max (correction passes applied)
+ *                 and resid_rel_max (the last residual formed, see below); without
+ *                 info the call stays asynchronous and reports nothing.
+ * EXPM_MIXED_FP32 (binary32 + refinement): the shifted matrices are factored and
+ * solved in binary32; pass 0 solves with V, and each of at most max_refine further
+ * passes solves with the residual r = V - (tT - cI + theta I) X of the running
+ * solution X and adds the correction.  Residuals are formed in float-float from
+ * the binary64 entries.  The passes stop once every system meets
+ *   ||r_s||_F <= tol (beta + |theta_s|) ||X_s||_F,  beta = max_i |d'_i| + |e'_{i-1}| + |e'_i|
+ * (d' = t d - c, e' = t e: beta bounds ||tT - cI||_2).  EXPM_ENOCONV (with info)
+ * when the residual after the last pass still exceeds tol.  Scratch: about
+ * 16 S N + 8 S r' N (max_refine >= 1) + 8 S r' N (max_refine >= 2) bytes, S = degree/2
+ * rounded up to a power of two, r' = real columns.  Not available in
+ * expm_apply_tridiag_noalloc.
  * Method: the rows are split into blocks separated by single separator rows;
  * each block is factored (unpivoted LU; (A - lambda I) scaled by a unit complex
  * number has a positive-definite Hermitian part when Im lambda != 0, so no pivot

@@ -14,6 +14,7 @@ EXPM_FP64 = 0
 EXPM_MIXED_F32X2 = 1
 EXPM_MIXED_FP32 = 2
 EXPM_MIXED_TF32X3 = 3
+EXPM_FLAG_SKIP_FINAL_RESIDUAL = 1
 
 STATUS = {0: "EXPM_OK", 1: "EXPM_EINVAL", 2: "EXPM_ENOMEM", 3: "EXPM_EGROWTH", 4: "EXPM_ENOCONV",
           5: "EXPM_ETIMEOUT", 6: "EXPM_EAGAIN", 7: "EXPM_ECUDA", 8: "EXPM_ENOTFOUND", 9: "EXPM_ENOTSUP"}
@@ -269,17 +270,25 @@ def expm_apply_batched(plan: Plan, As, Vs, Ys, prec=EXPM_FP64, t=1.0, shift_c=0.
     return list(infos)[:cnt]
 
 
-def expm_apply_tridiag(plan: Plan, d, e, V, Y, prec=EXPM_FP64, t=1.0, shift_c=0.0, stream=None) -> expm_info:
-    """Y = e^c R_n(tT - cI) V for the Hermitian tridiagonal T = (d, e); see include/expm.h."""
+def expm_apply_tridiag(plan: Plan, d, e, V, Y, prec=EXPM_FP64, t=1.0, shift_c=0.0, stream=None, tol=None,
+                       max_refine=None, flags=0, want_info=True, check=True):
+    """Y = e^c R_n(tT - cI) V for the Hermitian tridiagonal T = (d, e); see include/expm.h.
+
+    Returns the ``expm_info`` (or None with ``want_info=False``, which keeps the
+    EXPM_MIXED_FP32 path asynchronous).  With ``check=False`` EXPM_ENOCONV is left in
+    ``info.status_worst`` instead of raising."""
     N = int(d.shape[0])
     r = int(V.shape[1]) if len(V.shape) == 2 else 1
     if stream is None:
         stream = _default_stream(d, e, V, Y)
-    o = make_opts(prec, t, shift_c, stream)
-    info = expm_info()
-    _check(lib.expm_apply_tridiag(plan.handle, N, _ptr(d), _ptr(e), int(_is_complex(e)), _ptr(V), r,
-                                  int(_is_complex(V)), _ptr(Y), ctypes.byref(o), ctypes.byref(info)),
-           "expm_apply_tridiag")
+    o = make_opts(prec, t, shift_c, stream, tol, max_refine)
+    o.flags = int(flags)
+    info = expm_info() if want_info else None
+    st = lib.expm_apply_tridiag(plan.handle, N, _ptr(d), _ptr(e), int(_is_complex(e)), _ptr(V), r,
+                                int(_is_complex(V)), _ptr(Y), ctypes.byref(o),
+                                ctypes.byref(info) if info is not None else None)
+    if st != 0 and not (not check and st == 4):
+        _check(st, "expm_apply_tridiag")
     return info
 
 

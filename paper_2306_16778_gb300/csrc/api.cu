@@ -216,9 +216,13 @@ expm_status expm_apply_tridiag(expm_plan p, int64_t N, const double *d, const vo
     if (N < 1) return set_error(EXPM_EINVAL, "apply_tridiag: N must be >= 1");
     if (r < 1 || r > 64) return set_error(EXPM_EINVAL, "apply_tridiag: r must be in 1..64");
     if (!d || !V || !Y || (N > 1 && !e)) return set_error(EXPM_EINVAL, "apply_tridiag: NULL data pointer");
-    if (opts.prec != EXPM_FP64 && opts.prec != EXPM_MIXED_F32X2)
-        return set_error(EXPM_EINVAL, "apply_tridiag: precision must be EXPM_FP64 or EXPM_MIXED_F32X2");
-    if (opts.flags != 0) return set_error(EXPM_EINVAL, "apply_tridiag: opts.flags must be 0");
+    if (opts.prec != EXPM_FP64 && opts.prec != EXPM_MIXED_F32X2 && opts.prec != EXPM_MIXED_FP32)
+        return set_error(EXPM_EINVAL, "apply_tridiag: precision must be EXPM_FP64, EXPM_MIXED_F32X2 or EXPM_MIXED_FP32");
+    const bool mixed = opts.prec == EXPM_MIXED_FP32;
+    if (opts.flags != 0 && !(mixed && opts.flags == EXPM_FLAG_SKIP_FINAL_RESIDUAL))
+        return set_error(EXPM_EINVAL, "apply_tridiag: opts.flags must be 0 (or EXPM_FLAG_SKIP_FINAL_RESIDUAL with EXPM_MIXED_FP32)");
+    if (mixed && (opts.max_refine < 0 || opts.max_refine > 64 || !(opts.tol >= 0.0)))
+        return set_error(EXPM_EINVAL, "apply_tridiag: need 0 <= max_refine <= 64 and tol >= 0");
     if (!std::isfinite(opts.t) || !std::isfinite(opts.shift_c))
         return set_error(EXPM_EINVAL, "apply_tridiag: t and shift_c must be finite");
     if (e_is_complex) return set_error(EXPM_ENOTSUP, "apply_tridiag: complex off-diagonal not implemented");
@@ -236,12 +240,14 @@ expm_status expm_apply_tridiag(expm_plan p, int64_t N, const double *d, const vo
         ps.w_re[s] = 2.0 * ec * p->w[4 * s];
         ps.w_im[s] = 2.0 * ec * p->w[4 * s + 1];
     }
-    TriGeom g = tri_geometry(N, S, Rc, ff, p->sm_count);
+    TriGeom g = mixed ? tri_mixed_geometry(N, S, Rc, p->sm_count) : tri_geometry(N, S, Rc, ff, p->sm_count);
     g.t = opts.t;
     g.cshift = opts.shift_c;
     cudaStream_t st = (cudaStream_t)opts.stream;
+    const MixOpts mo{opts.max_refine, (opts.flags & EXPM_FLAG_SKIP_FINAL_RESIDUAL) ? 0 : 1, opts.tol};
+    const size_t mix_factor = mixed ? tri_mixed_factor_bytes(g) : 0;
 
-    const size_t need = tri_workspace_bytes(g, ff);
+    const size_t need = mixed ? mix_factor + tri_mixed_solve_bytes(g, mo.max_refine) : tri_workspace_bytes(g, ff);
     expm_status s = plan_reserve(p, &p->work, &p->work_bytes, need);
     if (s != EXPM_OK) return s;
 
@@ -267,13 +273,31 @@ expm_status expm_apply_tridiag(expm_plan p, int64_t N, const double *d, const vo
         if (!dy) dY = sY;
         if (err != cudaSuccess) return cuda_error(err, "apply_tridiag: staging copy");
     }
-    cudaError_t err = tri_run(g, ff, dD, dE, dV, dY, ps, p->work, st, p->prof);
-    if (err != cudaSuccess) return cuda_error(err, "apply_tridiag: kernel launch");
+    cudaError_t err;
+    if (mixed) {
+        void *swork = (unsigned char *)p->work + mix_factor;
+        err = tri_mixed_factor(g, dD, dE, ps, p->work, st, p->prof);
+        if (err == cudaSuccess) err = tri_mixed_solve(g, dV, dY, ps, p->work, swork, mo, st, p->prof);
+        if (err != cudaSuccess) return cuda_error(err, "apply_tridiag: kernel launch");
+        if (info) {
+            MixResult mr{};
+            err = tri_mixed_read_state(g, swork, mo.max_refine, &mr, st);
+            if (err != cudaSuccess) return cuda_error(err, "apply_tridiag: refinement state");
+            info->refine_iters_max = mr.iters;
+            info->resid_rel_max = mr.resid;
+            if (mo.verify && !mr.converged) info->status_worst = EXPM_ENOCONV;
+        }
+    } else {
+        err = tri_run(g, ff, dD, dE, dV, dY, ps, p->work, st, p->prof);
+        if (err != cudaSuccess) return cuda_error(err, "apply_tridiag: kernel launch");
+    }
     if (staged) {
         if (!dy) err = cudaMemcpyAsync(Y, dY, sizeof(double) * nV, cudaMemcpyDeviceToHost, st);
         if (err == cudaSuccess) err = cudaStreamSynchronize(st);
         if (err != cudaSuccess) return cuda_error(err, "apply_tridiag: result copy");
     }
+    if (info && info->status_worst == EXPM_ENOCONV)
+        return set_error(EXPM_ENOCONV, "apply_tridiag: refinement did not reach tol");
     return EXPM_OK;
 }
 

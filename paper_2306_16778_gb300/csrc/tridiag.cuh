@@ -46,4 +46,26 @@ cudaError_t tri_solve(const TriGeom &g, bool ff, const double *V, double *Y, con
 cudaError_t tri_run(const TriGeom &g, bool ff, const double *d, const double *e, const double *V, double *Y,
                     const TriPoles &ps, void *work, cudaStream_t st, Profiler &prof);
 
+// binary32 factors + refinement (EXPM_MIXED_FP32), tridiag_mixed.cu.  The factor part
+// (prep + binary32 block LUs and spikes) depends on T, t, c and the poles only.
+struct MixOpts {
+    int max_refine;  // correction passes at most (0: the binary32 solve alone)
+    int verify;      // form the residual after the last pass too (stopping test / report)
+    double tol;      // stop when max_s ||r_s|| / ((beta + |theta_s|) ||x_s||) <= tol
+};
+struct MixResult {
+    bool converged;  // the last residual formed met tol
+    int iters;       // correction passes applied
+    double resid;    // the last relative residual formed
+};
+TriGeom tri_mixed_geometry(int64_t N, int S, int Rc, int sm_count);
+size_t tri_mixed_factor_bytes(const TriGeom &g);
+size_t tri_mixed_solve_bytes(const TriGeom &g, int max_refine);
+cudaError_t tri_mixed_factor(const TriGeom &g, const double *d, const double *e, const TriPoles &ps, void *fwork,
+                             cudaStream_t st, Profiler &prof);
+cudaError_t tri_mixed_solve(const TriGeom &g, const double *V, double *Y, const TriPoles &ps, const void *fwork,
+                            void *swork, const MixOpts &mo, cudaStream_t st, Profiler &prof);
+// copies the device-side refinement state back (synchronises the stream)
+cudaError_t tri_mixed_read_state(const TriGeom &g, const void *swork, int max_refine, MixResult *out, cudaStream_t st);
+
 }  // namespace expm

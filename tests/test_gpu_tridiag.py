@@ -2,8 +2,9 @@
 the oracle, through the C-ABI.
 
 Tolerances: relative Frobenius error <= 1e-12 for the binary64 path (the
-configured FP64 tolerance) and <= 1e-8 for the float-float path (the mixed-path
-tolerance), each against the oracle's pivoted banded solves on the same inputs.
+configured FP64 tolerance) and <= 1e-8 for the float-float and the binary32 +
+refinement paths (the mixed-path tolerance), each against the oracle's pivoted
+banded solves on the same inputs.
 """
 
 import numpy as np
@@ -20,8 +21,10 @@ if not torch.cuda.is_available():
 
 import paper_2306_16778_gb300 as P  # noqa: E402
 
-TOL = {P.EXPM_FP64: 1e-12, P.EXPM_MIXED_F32X2: 1e-8}
-UNIT = {P.EXPM_FP64: 2.0 ** -53, P.EXPM_MIXED_F32X2: 2.0 ** -48}
+TOL = {P.EXPM_FP64: 1e-12, P.EXPM_MIXED_F32X2: 1e-8, P.EXPM_MIXED_FP32: 1e-8}
+# rounding unit of the arithmetic that forms Y (binary64; float pairs for both mixed paths)
+UNIT = {P.EXPM_FP64: 2.0 ** -53, P.EXPM_MIXED_F32X2: 2.0 ** -48, P.EXPM_MIXED_FP32: 2.0 ** -46}
+ALL = [P.EXPM_FP64, P.EXPM_MIXED_F32X2, P.EXPM_MIXED_FP32]
 DEV = torch.device("cuda:0")
 
 
@@ -40,12 +43,12 @@ def _oracle(d, e, V, n, t=1.0, c=0.0):
     return Y
 
 
-def _gpu(plan, d, e, V, prec, t=1.0, c=0.0):
+def _gpu(plan, d, e, V, prec, t=1.0, c=0.0, **kw):
     dd = torch.from_numpy(d).to(DEV)
     de = torch.from_numpy(e).to(DEV) if e.size else torch.zeros(1, dtype=torch.float64, device=DEV)
     dv = torch.from_numpy(np.ascontiguousarray(V)).to(DEV)
     dy = torch.empty_like(dv)
-    P.expm_apply_tridiag(plan, dd, de, dv, dy, prec=prec, t=t, shift_c=c)
+    P.expm_apply_tridiag(plan, dd, de, dv, dy, prec=prec, t=t, shift_c=c, **kw)
     torch.cuda.synchronize()
     return dy.cpu().numpy()
 
@@ -65,7 +68,7 @@ def plans():
     return {n: P.Plan(degree=n) for n in (12, 16)}
 
 
-@pytest.mark.parametrize("prec", [P.EXPM_FP64, P.EXPM_MIXED_F32X2])
+@pytest.mark.parametrize("prec", ALL)
 @pytest.mark.parametrize("N,r,n", [(1, 1, 12), (2, 3, 16), (7, 2, 12), (100, 1, 16), (433, 8, 16),
                                    (4096 + 13, 5, 12), (50_000, 8, 16), (200_003, 3, 12)])
 def test_random_tridiag_parity(plans, prec, N, r, n):
@@ -79,7 +82,7 @@ def test_random_tridiag_parity(plans, prec, N, r, n):
         assert rel <= TOL[prec]
 
 
-@pytest.mark.parametrize("prec", [P.EXPM_FP64, P.EXPM_MIXED_F32X2])
+@pytest.mark.parametrize("prec", ALL)
 def test_laplacian_mid_size(plans, prec):
     w = workloads.laplacian_1d(N=65_537, nrhs=8, offset=201)
     Y = _gpu(plans[16], w["d"], w["e"], w["V"], prec)
@@ -95,11 +98,16 @@ def full_size():
     return w, Yo
 
 
-@pytest.mark.parametrize("prec", [P.EXPM_FP64, P.EXPM_MIXED_F32X2])
+# the benchmark's settings for the binary32 + refinement path
+BENCH_MIXED = dict(tol=1e-10, max_refine=1)
+
+
+@pytest.mark.parametrize("prec", ALL)
 def test_laplacian_full_size(plans, full_size, prec):
     """Full-size parity in the launch configuration the benchmark times."""
     w, Yo = full_size
-    Y = _gpu(plans[16], w["d"], w["e"], w["V"], prec)
+    kw = BENCH_MIXED if prec == P.EXPM_MIXED_FP32 else {}
+    Y = _gpu(plans[16], w["d"], w["e"], w["V"], prec, **kw)
     err = matrix.rel_err(Y, Yo)
     print(f"full-size rel err prec={prec}: {err:.3e}")
     assert err <= TOL[prec]
@@ -162,3 +170,91 @@ def test_invalid_arguments(plans):
     with pytest.raises(P.ExpmError) as ei:
         P.expm_apply_tridiag(plans[12], dd, de, dv, dy, prec=P.EXPM_MIXED_TF32X3)
     assert ei.value.status == 1                        # EXPM_EINVAL
+
+
+# ------------------------------------------------------------------ binary32 + refinement
+
+def _dev(d, e, V):
+    dd, de, dv = (torch.from_numpy(np.ascontiguousarray(x)).to(DEV) for x in (d, e, V))
+    return dd, de, dv, torch.empty_like(dv)
+
+
+def test_mixed_refinement_info(plans):
+    """The stopping test is met after at least one correction and reported in info."""
+    d, e, V = _random_tridiag(60_000, 4, 208)
+    dd, de, dv, dy = _dev(d, e, V)
+    info = P.expm_apply_tridiag(plans[16], dd, de, dv, dy, prec=P.EXPM_MIXED_FP32, tol=1e-12, max_refine=4)
+    assert info.status_worst == 0
+    assert 1 <= info.refine_iters_max <= 4
+    assert 0.0 <= info.resid_rel_max <= 1e-12
+    assert matrix.rel_err(dy.cpu().numpy(), _oracle(d, e, V, 16)) <= 1e-10
+
+
+def test_mixed_default_tolerance_is_tight(plans):
+    """With the default tol (1e-14) the refined result is close to the binary64 floor."""
+    w = workloads.laplacian_1d(N=30_011, nrhs=3, offset=209)
+    Y = _gpu(plans[16], w["d"], w["e"], w["V"], P.EXPM_MIXED_FP32)
+    assert matrix.rel_err(Y, _oracle(w["d"], w["e"], w["V"], 16)) <= 1e-11
+
+
+def test_mixed_without_refinement_reports_enoconv(plans):
+    """max_refine = 0 is the binary32 solve alone: its residual misses tol (EXPM_ENOCONV,
+    left in info with check=False) and its error is binary32-sized."""
+    d, e, V = _random_tridiag(20_000, 2, 210)
+    dd, de, dv, dy = _dev(d, e, V)
+    info = P.expm_apply_tridiag(plans[12], dd, de, dv, dy, prec=P.EXPM_MIXED_FP32, max_refine=0, check=False)
+    assert info.status_worst == 4
+    assert info.refine_iters_max == 0
+    err = matrix.rel_err(dy.cpu().numpy(), _oracle(d, e, V, 12))
+    assert 1e-9 < err < 1e-3
+    with pytest.raises(P.ExpmError) as ei:
+        P.expm_apply_tridiag(plans[12], dd, de, dv, dy, prec=P.EXPM_MIXED_FP32, max_refine=0)
+    assert ei.value.status == 4
+
+
+def test_mixed_early_stop(plans):
+    """A loose tol is met by the binary32 solve: no correction pass runs."""
+    d, e, V = _random_tridiag(20_000, 2, 211)
+    dd, de, dv, dy = _dev(d, e, V)
+    info = P.expm_apply_tridiag(plans[12], dd, de, dv, dy, prec=P.EXPM_MIXED_FP32, tol=1e-3, max_refine=3)
+    assert info.status_worst == 0 and info.refine_iters_max == 0
+    y0 = dy.clone()
+    P.expm_apply_tridiag(plans[12], dd, de, dv, dy, prec=P.EXPM_MIXED_FP32, max_refine=0, check=False)
+    assert torch.equal(dy, y0)
+
+
+def test_mixed_async_and_skip_flag_give_identical_results(plans):
+    """Without info the call stays asynchronous; skipping the final residual changes
+    only the report.  All three runs produce bit-identical Y."""
+    w = workloads.laplacian_1d(N=100_003, nrhs=8, offset=212)
+    dd, de, dv, dy = _dev(w["d"], w["e"], w["V"])
+    kw = dict(prec=P.EXPM_MIXED_FP32, tol=1e-10, max_refine=1)
+    info = P.expm_apply_tridiag(plans[16], dd, de, dv, dy, **kw)
+    ya = dy.clone()
+    assert P.expm_apply_tridiag(plans[16], dd, de, dv, dy, want_info=False, **kw) is None
+    torch.cuda.synchronize()
+    yb = dy.clone()
+    info2 = P.expm_apply_tridiag(plans[16], dd, de, dv, dy, flags=P.EXPM_FLAG_SKIP_FINAL_RESIDUAL, **kw)
+    assert torch.equal(ya, yb) and torch.equal(ya, dy)
+    assert info.refine_iters_max == 1 and info.resid_rel_max <= 1e-10
+    assert info2.status_worst == 0 and info2.resid_rel_max > info.resid_rel_max   # residual before the last pass
+
+
+def test_mixed_complex_rhs_time_shift(plans):
+    """Complex V, t != 1 and c != 0 on the refined path."""
+    d, e, V = _random_tridiag(12_000, 2, 213, complex_v=True)
+    d = d + 12.0
+    Y = _gpu(plans[16], d, e, V, P.EXPM_MIXED_FP32, t=0.5, c=6.5, tol=1e-12)
+    assert matrix.rel_err(Y, _oracle(d, e, V, 16, t=0.5, c=6.5)) <= 1e-9
+
+
+def test_mixed_invalid_options(plans):
+    d, e, V = _random_tridiag(100, 2, 214)
+    dd, de, dv, dy = _dev(d, e, V)
+    for kw in (dict(max_refine=-1), dict(tol=-1.0), dict(flags=2)):
+        with pytest.raises(P.ExpmError) as ei:
+            P.expm_apply_tridiag(plans[12], dd, de, dv, dy, prec=P.EXPM_MIXED_FP32, **kw)
+        assert ei.value.status == 1
+    with pytest.raises(P.ExpmError) as ei:            # the flag belongs to the refined path only
+        P.expm_apply_tridiag(plans[12], dd, de, dv, dy, flags=P.EXPM_FLAG_SKIP_FINAL_RESIDUAL)
+    assert ei.value.status == 1
