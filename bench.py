@@ -478,8 +478,14 @@ def run_served(args):
     out = {"workload": "served stream: 70% Laplacian N log-uniform [2^12,2^20] 1-4 RHS, "
                        "30% dense Hermitian n log-uniform [64,2048] 1-64 RHS, degree 12/16",
            "requests_per_rate": args.served_requests}
+    def sub_opts(kind, ptri, pden):
+        # tridiagonal binary32 + refinement with the headline settings; dense with its defaults
+        if kind == "tridiag":
+            return dict(prec=ptri, **(MIXED_OPTS if ptri == P.EXPM_MIXED_FP32 else {}))
+        return dict(prec=pden)
+
     for prec_name, ptri, pden in (("fp64", P.EXPM_FP64, P.EXPM_FP64),
-                                  ("mixed", P.EXPM_MIXED_F32X2, P.EXPM_MIXED_FP32)):
+                                  ("mixed", P.EXPM_MIXED_FP32, P.EXPM_MIXED_FP32)):
         server = P.Server(hbm_budget_bytes=64 << 30, max_inflight=8)
         ops = {}
         for r in reqs_all:
@@ -499,7 +505,7 @@ def run_served(args):
             bufs.append((oid, V, torch.empty_like(V)))
         # saturation: submit everything at once
         t0 = time.perf_counter()
-        tk = [server.submit(oid, plans[r["degree"]], V, Y, prec=ptri if r["kind"] == "tridiag" else pden)
+        tk = [server.submit(oid, plans[r["degree"]], V, Y, **sub_opts(r["kind"], ptri, pden))
               for r, (oid, V, Y) in zip(reqs_all, bufs)]
         lat = []
         pending = set(tk)
@@ -525,7 +531,7 @@ def run_served(args):
                 while i < len(bufs) and arrival[i] <= now:
                     r = reqs_all[i]
                     oid, V, Y = bufs[i]
-                    t = server.submit(oid, plans[r["degree"]], V, Y, prec=ptri if r["kind"] == "tridiag" else pden)
+                    t = server.submit(oid, plans[r["degree"]], V, Y, **sub_opts(r["kind"], ptri, pden))
                     pending[t] = True
                     i += 1
                 for t in list(pending):

@@ -315,10 +315,11 @@ class Server:
         return int(oid.value)
 
     def submit(self, op_id: int, plan: "Plan", V, Y, prec=EXPM_FP64, t=1.0, shift_c=0.0, tol=None,
-               max_refine=None) -> int:
+               max_refine=None, flags=0) -> int:
         """Queue a request; V and Y must stay alive until poll() reports it finished."""
         k = int(V.shape[1]) if len(V.shape) == 2 else 1
         o = make_opts(prec, t, shift_c, None, tol, max_refine)
+        o.flags = int(flags)
         tk = ctypes.c_uint64()
         _check(lib.expm_server_submit(self._h, int(op_id), plan.handle, _ptr(V), k, int(_is_complex(V)), _ptr(Y),
                                       ctypes.byref(o), ctypes.byref(tk)), "expm_server_submit")

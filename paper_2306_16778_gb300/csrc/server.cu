@@ -188,7 +188,32 @@ void run_request(expm_server_s *sv, Worker &w, Request &r, FactorEntry &fe, bool
     cudaError_t err = cudaSuccess;
     r.ts[2] = sv->now();
     const bool ff = r.opts.prec != EXPM_FP64;
-    if (op.kind == EXPM_OP_TRIDIAG) {
+    if (op.kind == EXPM_OP_TRIDIAG && r.opts.prec == EXPM_MIXED_FP32) {
+        // binary32 factors + refinement: the factor part is cached like the others
+        const int Rc = r.k * (r.v_cplx ? 2 : 1);
+        TriGeom g = tri_mixed_geometry(op.n, r.plan->degree / 2, Rc, sv->sm_count);
+        g.t = r.opts.t;
+        g.cshift = r.opts.shift_c;
+        const TriPoles ps = tri_poles(r.plan, r.opts.shift_c);
+        const MixOpts mo{r.opts.max_refine, (r.opts.flags & EXPM_FLAG_SKIP_FINAL_RESIDUAL) ? 0 : 1, r.opts.tol};
+        const double *d = (const double *)op.data;
+        if (build) {
+            err = tri_mixed_factor(g, d, d + op.n, ps, fe.buf, w.stream, off);
+            if (err == cudaSuccess) err = cudaEventRecord(fe.done, w.stream);
+            publish(sv, fe, err != cudaSuccess);
+        } else {
+            err = fe.failed ? cudaErrorUnknown : cudaStreamWaitEvent(w.stream, fe.done, 0);
+        }
+        if (err == cudaSuccess)
+            err = tri_mixed_solve(g, (const double *)r.V, (double *)r.Y, ps, fe.buf, w.work, mo, w.stream, off);
+        MixResult mr{};
+        if (err == cudaSuccess) err = tri_mixed_read_state(g, w.work, mo.max_refine, &mr, w.stream);  // synchronises
+        if (err == cudaSuccess) {
+            r.info.refine_iters_max = mr.iters;
+            r.info.resid_rel_max = mr.resid;
+            if (mo.verify && !mr.converged) st = EXPM_ENOCONV;
+        }
+    } else if (op.kind == EXPM_OP_TRIDIAG) {
         const int Rc = r.k * (r.v_cplx ? 2 : 1);
         TriGeom g = tri_geometry(op.n, r.plan->degree / 2, Rc, ff, sv->sm_count);
         g.t = r.opts.t;
@@ -241,7 +266,11 @@ void run_request(expm_server_s *sv, Worker &w, Request &r, FactorEntry &fe, bool
 Request *admit(expm_server_s *sv, Worker &w, FactorEntry **fe_out, bool *build_out) {
     for (auto it = sv->queue.begin(); it != sv->queue.end(); ++it) {
         Request *r = *it;
-        const FactorKey key{r->op, (const void *)r->plan, r->opts.prec == EXPM_FP64 ? 0 : 1, r->opts.t, r->opts.shift_c};
+        // factor parts differ by precision: binary64; float-float; binary32 (the dense mixed
+        // precisions share one binary32 LU; the tridiagonal binary32 factors are their own)
+        const int fprec = r->opts.prec == EXPM_FP64 ? 0
+                          : (r->opv.kind == EXPM_OP_TRIDIAG && r->opts.prec == EXPM_MIXED_FP32) ? 2 : 1;
+        const FactorKey key{r->op, (const void *)r->plan, fprec, r->opts.t, r->opts.shift_c};
         auto ce = sv->cache.find(key);
         const bool cached = ce != sv->cache.end();
         if (cached && !ce->second.ready) continue;  // its factor is being built: wait for it
@@ -395,7 +424,9 @@ expm_status expm_server_submit(expm_server sv, uint64_t op_id, const expm_plan p
     if (k < 1 || k > 64) return set_error(EXPM_EINVAL, "server_submit: k must be in 1..64");
     expm_opts opts;
     if (opts_in) opts = *opts_in; else expm_opts_default(&opts);
-    if (opts.flags != 0 || !std::isfinite(opts.t) || !std::isfinite(opts.shift_c))
+    const bool tri_mixed = opts.prec == EXPM_MIXED_FP32;  // meaningful for tridiagonal operators
+    if ((opts.flags != 0 && opts.flags != EXPM_FLAG_SKIP_FINAL_RESIDUAL) || !std::isfinite(opts.t) ||
+        !std::isfinite(opts.shift_c))
         return set_error(EXPM_EINVAL, "server_submit: bad options");
     auto r = std::make_unique<Request>();
     r->op = op_id;
@@ -412,14 +443,24 @@ expm_status expm_server_submit(expm_server sv, uint64_t op_id, const expm_plan p
     r->opv = op;
     const bool ff = opts.prec != EXPM_FP64;
     if (op.kind == EXPM_OP_TRIDIAG) {
-        if (opts.prec != EXPM_FP64 && opts.prec != EXPM_MIXED_F32X2)
-            return set_error(EXPM_EINVAL, "server_submit: tridiagonal precision must be FP64 or MIXED_F32X2");
-        const TriGeom g = tri_geometry(op.n, plan->degree / 2, k * (v_is_complex ? 2 : 1), ff, sv->sm_count);
-        r->solve_bytes = tri_solve_bytes(g, ff);
-        r->factor_bytes = tri_factor_bytes(g, ff);
+        if (opts.prec != EXPM_FP64 && opts.prec != EXPM_MIXED_F32X2 && opts.prec != EXPM_MIXED_FP32)
+            return set_error(EXPM_EINVAL, "server_submit: tridiagonal precision must be FP64, MIXED_F32X2 or MIXED_FP32");
+        if (tri_mixed && (opts.max_refine < 0 || opts.max_refine > 64 || !(opts.tol >= 0.0)))
+            return set_error(EXPM_EINVAL, "server_submit: need 0 <= max_refine <= 64 and tol >= 0");
+        const int Rc = k * (v_is_complex ? 2 : 1);
+        if (tri_mixed) {
+            const TriGeom g = tri_mixed_geometry(op.n, plan->degree / 2, Rc, sv->sm_count);
+            r->solve_bytes = tri_mixed_solve_bytes(g, opts.max_refine);
+            r->factor_bytes = tri_mixed_factor_bytes(g);
+        } else {
+            const TriGeom g = tri_geometry(op.n, plan->degree / 2, Rc, ff, sv->sm_count);
+            r->solve_bytes = tri_solve_bytes(g, ff);
+            r->factor_bytes = tri_factor_bytes(g, ff);
+        }
     } else {
         if (opts.prec != EXPM_FP64 && opts.prec != EXPM_MIXED_FP32 && opts.prec != EXPM_MIXED_F32X2)
             return set_error(EXPM_EINVAL, "server_submit: dense precision must be FP64 or mixed");
+        if (opts.flags != 0) return set_error(EXPM_EINVAL, "server_submit: flags apply to tridiagonal operators only");
         const DenseGeom g = dense_geom(op, plan, opts, k, v_is_complex);
         r->solve_bytes = dense_solve_bytes(g);
         r->factor_bytes = dense_factor_bytes(g);

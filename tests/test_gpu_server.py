@@ -61,7 +61,7 @@ def test_mixed_stream_same_alone_and_in_the_mix():
         else:
             oid, d, e, w = tri[i % len(tri)]
             V = torch.from_numpy(workloads.request_rhs(d.shape[0], 1 + i % 4, 700 + i, False)).to(DEV)
-            prec = P.EXPM_MIXED_F32X2 if i % 4 == 1 else P.EXPM_FP64
+            prec = (P.EXPM_FP64, P.EXPM_MIXED_F32X2, P.EXPM_FP64, P.EXPM_MIXED_FP32)[i % 4]
             reqs.append(("tri", oid, d, e, V, deg, prec, w))
     outs = [torch.empty_like(r[4]) for r in reqs]
     torch.cuda.synchronize()
