@@ -247,6 +247,21 @@ expm_status expm_apply_dense(expm_plan plan, int n, const void *A, int lda, int 
                              expm_info *info);
 
 /*
+ * expm_apply_dense_full -- the full matrix Y = e^c R_n(tA - cI) (eq. ExpoMatRat: R_n(A) =
+ * sum_k a_k (A + theta_k I)^{-1}), the approximation of exp(tA) itself.
+ * Equivalent to expm_apply_dense with V = I; the per-pair LUs are formed once and the
+ * identity passes through the solve part in blocks of 512 columns.
+ *   n, A, lda, a_is_complex   as expm_apply_dense
+ *   Y             n x n row-major, leading dimension ldy >= n (elements); real for
+ *                 real symmetric A (Remark 5.1), interleaved complex for complex A
+ *   opts, info    as expm_apply_dense (info over all column blocks)
+ * A and Y may be host or device memory (host buffers are staged; the call then
+ * synchronises).  Returns as expm_apply_dense.
+ */
+expm_status expm_apply_dense_full(expm_plan plan, int n, const void *A, int lda, int a_is_complex, void *Y, int ldy,
+                                  const expm_opts *opts, expm_info *info);
+
+/*
  * expm_apply_batched -- Y_i = e^c R_n(tA_i - cI) V_i for `count` independent dense
  * Hermitian problems of uneven sizes (eq. expAx per instance, Sec. 3).
  *   count            number of instances (0 is a no-op)

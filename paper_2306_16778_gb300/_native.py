@@ -66,6 +66,8 @@ def _load() -> ctypes.CDLL:
     L.expm_plan_create.restype = i
     L.expm_plan_destroy.argtypes = [vp]
     L.expm_plan_destroy.restype = i
+    L.expm_apply_dense_full.argtypes = [vp, i, vp, i, i, vp, i, ctypes.POINTER(expm_opts), ctypes.POINTER(expm_info)]
+    L.expm_apply_dense_full.restype = i
     L.expm_apply_tridiag.argtypes = [vp, i64, vp, vp, i, vp, i, i, vp, ctypes.POINTER(expm_opts),
                                      ctypes.POINTER(expm_info)]
     L.expm_apply_tridiag.restype = i
@@ -246,6 +248,21 @@ def expm_apply_dense(plan: Plan, A, V, Y, prec=EXPM_FP64, t=1.0, shift_c=0.0, st
                               _ptr(Y), k, ctypes.byref(o), ctypes.byref(info))
     if check or st not in (3, 4):
         _check(st, "expm_apply_dense")
+    return info
+
+
+def expm_apply_dense_full(plan: Plan, A, Y, prec=EXPM_FP64, t=1.0, shift_c=0.0, stream=None, tol=None,
+                          max_refine=None, growth_max=None, check=True) -> expm_info:
+    """Y = e^c R_n(tA - cI), the full matrix (n x n; real for real A, complex128 for complex A)."""
+    n = int(A.shape[0])
+    if stream is None:
+        stream = _default_stream(A, Y)
+    o = make_opts(prec, t, shift_c, stream, tol, max_refine, growth_max)
+    info = expm_info()
+    st = lib.expm_apply_dense_full(plan.handle, n, _ptr(A), n, int(_is_complex(A)), _ptr(Y), n, ctypes.byref(o),
+                                   ctypes.byref(info))
+    if st != 0 and not (not check and st in (3, 4)):
+        _check(st, "expm_apply_dense_full")
     return info
 
 
