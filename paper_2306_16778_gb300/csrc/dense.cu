@@ -131,10 +131,9 @@ __global__ void frob2(int n, const double *__restrict__ A, int64_t lda, int64_t 
     A += (int64_t)blockIdx.z * astride * (cplx ? 2 : 1);
     out += blockIdx.z;
     double acc = 0.0;
-    const int64_t total = (int64_t)n * n;
-    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
-         idx += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t i = idx / n, j = idx % n;
+    // rows blockIdx.x, blockIdx.x + gridDim.x, ...; threads over the columns
+    for (int64_t i = blockIdx.x; i < n; i += gridDim.x)
+    for (int64_t j = threadIdx.x; j < n; j += blockDim.x) {
         if (cplx) {
             const double re = A[2 * (i * lda + j)], im = A[2 * (i * lda + j) + 1];
             acc += re * re + im * im;
@@ -280,6 +279,18 @@ static cudaError_t lu_blocked(int n, int batch, cx<T> *F, cudaStream_t st, Profi
 template <class T>
 static cudaError_t lu_solve(int n, int kc, int batch, const cx<T> *F, int64_t fstride, bool conj, cx<T> *X,
                             int64_t xstride, cudaStream_t st, Profiler &prof) {
+    const size_t smn = narrow_smem_bytes<T>(n, kc);
+    if (kc <= 8 && smn <= (200u << 10)) {  // few right-hand sides: one fused kernel per batch entry
+        // the attribute is a ceiling, set to the largest size used so that concurrent
+        // callers (server workers) never lower it under one another's launch
+        EXPM_TRY(set_smem(lu_solve_narrow<T, false>, 200u << 10));
+        EXPM_TRY(set_smem(lu_solve_narrow<T, true>, 200u << 10));
+        return prof.timed(sizeof(T) == 8 ? "lu_solve<f64>" : "lu_solve<f32>", st, [&]() -> cudaError_t {
+            if (conj) lu_solve_narrow<T, true><<<batch, 256, smn, st>>>(n, kc, F, fstride, X, xstride);
+            else lu_solve_narrow<T, false><<<batch, 256, smn, st>>>(n, kc, F, fstride, X, xstride);
+            return cudaGetLastError();
+        });
+    }
     const size_t sm2 = 2 * tri_smem_bytes<T>();
     const int cb = (kc + 63) / 64;
     EXPM_TRY(set_smem(trsm_left<T, true, true, false>, sm2));
@@ -390,13 +401,12 @@ static cudaError_t factor_pairs(const DenseGeom &g, const DenseIO &io, const Den
     EXPM_TRY(cudaMemsetAsync(amax, 0, sizeof(unsigned) * batch, st));
     EXPM_TRY(cudaMemsetAsync(umax, 0, sizeof(unsigned) * batch, st));
     EXPM_TRY(prof.timed(sizeof(T) == 8 ? "form_shifted<f64>" : "form_shifted<f32>", st, [&] {
-        form_shifted<T><<<dim3(grid1d((int64_t)g.n * g.n), 1, batch), 256, 0, st>>>(
+        form_shifted<T><<<dim3((g.n + 7) / 8, 1, g.ninst), 256, 0, st>>>(
             g.n, io.A, (int)io.lda, io.astride, g.complex_a, g.npairs, g.t, pairs, F, amax);
         return cudaGetLastError();
     }));
     EXPM_TRY(lu_blocked<T>(g.n, batch, F, st, prof, tc));
-    max_abs_upper<T><<<dim3(grid1d((int64_t)g.n * g.n), 1, batch), 256, 0, st>>>(g.n, F, g.n, (int64_t)g.n * g.n,
-                                                                                  umax);
+    max_abs_upper<T><<<dim3((g.n + 7) / 8, 1, batch), 256, 0, st>>>(g.n, F, g.n, (int64_t)g.n * g.n, umax);
     return cudaGetLastError();
 }
 
@@ -480,7 +490,7 @@ cudaError_t dense_solve(const DenseGeom &g, const DenseIO &io, const DenseSystem
         std::vector<double> h(2 * (size_t)nsz), an(g.ninst);
         // ||tA||_F of every instance for the relative residual of the stopping test
         EXPM_TRY(cudaMemsetAsync(an2, 0, sizeof(double) * g.ninst, st));
-        frob2<<<dim3(grid1d((int64_t)g.n * g.n), 1, g.ninst), 256, 0, st>>>(g.n, io.A, io.lda, io.astride,
+        frob2<<<dim3((unsigned)std::min(g.n, 1024), 1, g.ninst), 256, 0, st>>>(g.n, io.A, io.lda, io.astride,
                                                                            g.complex_a, an2);
         EXPM_TRY(cudaGetLastError());
         EXPM_TRY(cudaMemcpyAsync(an.data(), an2, sizeof(double) * g.ninst, cudaMemcpyDeviceToHost, st));
@@ -494,14 +504,14 @@ cudaError_t dense_solve(const DenseGeom &g, const DenseIO &io, const DenseSystem
             if (it > 0) {
                 if (g.kc <= 8) {
                     EXPM_TRY(prof.timed("resid_gemv<f64>", st, [&] {
-                        dim3 gg((g.n + 7) / 8, 1, nsz);
+                        dim3 gg((g.n + 7) / 8, (g.nsys * g.kc + 15) / 16, g.ninst);
                         if (g.complex_a)
-                            resid_gemv<cx<double>><<<gg, 256, 0, st>>>(g.n, g.kc, g.n, g.t, (const cx<double> *)io.A,
-                                                                        (int)io.lda, io.astride, X, g.kc, nk, R, g.kc,
-                                                                        nk, g.nsys);
+                            resid_gemv_multi<cx<double>><<<gg, 256, 0, st>>>(g.n, g.kc, g.nsys, g.t,
+                                                                              (const cx<double> *)io.A, (int)io.lda,
+                                                                              io.astride, X, nk, R);
                         else
-                            resid_gemv<double><<<gg, 256, 0, st>>>(g.n, g.kc, g.n, g.t, io.A, (int)io.lda, io.astride,
-                                                                    X, g.kc, nk, R, g.kc, nk, g.nsys);
+                            resid_gemv_multi<double><<<gg, 256, 0, st>>>(g.n, g.kc, g.nsys, g.t, io.A, (int)io.lda,
+                                                                          io.astride, X, nk, R);
                         return cudaGetLastError();
                     }));
                 } else EXPM_TRY(prof.timed("resid_gemm<f32x2>", st, [&] {

@@ -37,38 +37,45 @@ template <class T> EXPM_D cx<T> cdiv(cx<T> a, cx<T> b) { return a * cinv(b); }
 template <class T> EXPM_D T cabs2(cx<T> a) { return a.re * a.re + a.im * a.im; }
 
 // ------------------------------------------------------------------ form_shifted
-// Out[s] (n x n, ld n, precision T) = t A - c I + theta_s I.  A is real (a_cplx = 0)
-// or complex, binary64, leading dimension lda.  amax[s] receives max |Out[s]_ij|
-// (as the bit pattern of a non-negative float, atomicMax-ed).
-// Batch z = instance * npairs + pair; instance i reads A + i * astride elements.
+// Out[z] (n x n, ld n, precision T) = t A - c I + theta_s I for every pair s of every
+// instance, z = instance * npairs + s.  A is real (a_cplx = 0) or complex, binary64,
+// leading dimension lda; instance i reads A + i * astride elements.  One warp per row
+// (grid.x = ceil(n / 8) blocks of 8 warps, grid.z = instances): A is read once and
+// every pair's row written from it.  amax[z] receives max |Out[z]_ij| (as the bit
+// pattern of a non-negative float, atomicMax-ed): the off-diagonal part is common to
+// all pairs, only the diagonal entry differs.
 template <class T>
-__global__ void form_shifted(int n, const double *__restrict__ A, int lda, int64_t astride, int a_cplx, int npairs,
-                             double t, DenseSystems ps, cx<T> *__restrict__ Out, unsigned *amax) {
-    const int z = blockIdx.z;
-    const int s = z % npairs;
-    A += (int64_t)(z / npairs) * astride * (a_cplx ? 2 : 1);
-    const int64_t total = (int64_t)n * n;
-    float local = 0.f;
-    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
-         idx += (int64_t)gridDim.x * blockDim.x) {
-        const int i = (int)(idx / n), j = (int)(idx % n);
-        double re, im;
-        if (a_cplx) {
-            re = t * A[2 * ((int64_t)i * lda + j)];
-            im = t * A[2 * ((int64_t)i * lda + j) + 1];
+__global__ void __launch_bounds__(256) form_shifted(int n, const double *__restrict__ A, int lda, int64_t astride,
+                                                    int a_cplx, int npairs, double t, DenseSystems ps,
+                                                    cx<T> *__restrict__ Out, unsigned *amax) {
+    const int inst = blockIdx.z;
+    const int i = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    if (i >= n) return;
+    const int64_t esz = a_cplx ? 2 : 1;
+    const double *arow = A + (int64_t)inst * astride * esz + (int64_t)i * lda * esz;
+    const int64_t nn = (int64_t)n * n;
+    cx<T> *out0 = Out + (int64_t)inst * npairs * nn + (int64_t)i * n;
+    float offmax = 0.f;
+    for (int j = lane; j < n; j += 32) {
+        const double re = t * arow[esz * j], im = a_cplx ? t * arow[2 * j + 1] : 0.0;
+        if (j != i) {
+            const cx<T> v = {(T)re, (T)im};
+            for (int s = 0; s < npairs; ++s) out0[s * nn + j] = v;
+            offmax = fmaxf(offmax, sqrtf((float)(re * re + im * im)));
         } else {
-            re = t * A[(int64_t)i * lda + j];
-            im = 0.0;
+            for (int s = 0; s < npairs; ++s)
+                out0[s * nn + j] = {(T)(re + ps.th_re[s] - ps.cshift), (T)(im + ps.th_im[s])};
         }
-        if (i == j) {
-            re += ps.th_re[s] - ps.cshift;
-            im += ps.th_im[s];
-        }
-        Out[(int64_t)z * total + idx] = {(T)re, (T)im};
-        local = fmaxf(local, (float)sqrt(re * re + im * im));
     }
-    for (int o = 16; o > 0; o >>= 1) local = fmaxf(local, __shfl_xor_sync(0xffffffffu, local, o));
-    if ((threadIdx.x & 31) == 0) atomicMax(amax + z, __float_as_uint(local));
+    for (int o = 16; o > 0; o >>= 1) offmax = fmaxf(offmax, __shfl_xor_sync(0xffffffffu, offmax, o));
+    if (lane == 0) {
+        const double re = t * arow[esz * i], im = a_cplx ? t * arow[2 * i + 1] : 0.0;
+        for (int s = 0; s < npairs; ++s) {
+            const double dr = re + ps.th_re[s] - ps.cshift, di = im + ps.th_im[s];
+            const float m = fmaxf(offmax, sqrtf((float)(dr * dr + di * di)));
+            atomicMax(amax + (int64_t)inst * npairs + s, __float_as_uint(m));
+        }
+    }
 }
 
 // ------------------------------------------------------------------ lu_diag
@@ -299,6 +306,195 @@ __global__ void __launch_bounds__(256) resid_gemv(int m, int n, int K, double t,
     }
 }
 
+// ------------------------------------------------------------------ lu_solve_narrow
+// X <- (L U)^{-1} X (CONJ = false) or (L U)^{-H} X = U^{-H} L^{-H} X (CONJ = true) for an
+// LU stored in place (unit L below the diagonal, U on and above), at most 8 columns.
+// One CTA per batch entry b: X_b (n x kc, row-major) lives in shared memory for the
+// whole solve.  Per 64-row block: the update from the rows already solved (a GEMV on
+// the factor, read once; row-wise when the needed triangle is stored by rows, column-
+// wise -- lanes over the block's rows -- when it is the conjugate transpose), then the
+// 64 x 64 diagonal block staged in shared memory and solved right-looking by one warp.
+// Dynamic shared memory: n * kc complex entries, then DN_NB x (DN_NB + 1), then the
+// cross-group partial sums 4 x DN_NB x 8.
+template <class T, bool CONJ>
+__global__ void __launch_bounds__(256) lu_solve_narrow(int n, int kc, const cx<T> *__restrict__ F, int64_t fstride,
+                                                       cx<T> *X, int64_t xstride) {
+    constexpr int NB = DN_NB;
+    cx<T> *xs = reinterpret_cast<cx<T> *>(dyn_smem);                       // [n][kc]
+    cx<T>(*D)[NB + 1] = reinterpret_cast<cx<T>(*)[NB + 1]>(xs + (size_t)n * kc);  // diagonal block
+    cx<T> *red = reinterpret_cast<cx<T> *>(D + NB);                        // [4][NB][8]
+    const int64_t b = blockIdx.x;
+    const cx<T> *Fb = F + b * fstride;
+    cx<T> *Xb = X + b * xstride;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    for (int e = tid; e < n * kc; e += blockDim.x) xs[e] = Xb[e];
+    __syncthreads();
+    // element (i, j) of the triangle used: row-stored for !CONJ, conjugate of (j, i) for CONJ
+    auto elem = [&](int i, int j) -> cx<T> { return CONJ ? conj(Fb[(int64_t)j * n + i]) : Fb[(int64_t)i * n + j]; };
+    // xs[p + r] -= sum_{j in [j0, j1)} M(p + r, j) xs[j]  for r < nb
+    auto offdiag = [&](int p, int nb, int j0, int j1) {
+        if (j1 <= j0) return;
+        if (!CONJ) {  // rows of F: one warp per row, lanes over j
+            for (int r = warp; r < nb; r += 8) {
+                cx<T> acc[8];
+#pragma unroll
+                for (int c = 0; c < 8; ++c) acc[c] = {T(0), T(0)};
+                const cx<T> *frow = Fb + (int64_t)(p + r) * n;
+                for (int j = j0 + lane; j < j1; j += 32) {
+                    const cx<T> f = frow[j];
+#pragma unroll
+                    for (int c = 0; c < 8; ++c)
+                        if (c < kc) acc[c] = cfma(acc[c], f, xs[(int64_t)j * kc + c]);
+                }
+#pragma unroll
+                for (int c = 0; c < 8; ++c) {
+                    if (c < kc) {
+                        T re = acc[c].re, im = acc[c].im;
+                        for (int o = 16; o > 0; o >>= 1) {
+                            re += __shfl_xor_sync(0xffffffffu, re, o);
+                            im += __shfl_xor_sync(0xffffffffu, im, o);
+                        }
+                        if (lane == 0) {
+                            xs[(int64_t)(p + r) * kc + c].re -= re;
+                            xs[(int64_t)(p + r) * kc + c].im -= im;
+                        }
+                    }
+                }
+            }
+        } else {  // columns of F: 64 lanes over the block's rows, 4 groups over j
+            const int r = tid & (NB - 1), grp = tid / NB;
+            cx<T> acc[8];
+#pragma unroll
+            for (int c = 0; c < 8; ++c) acc[c] = {T(0), T(0)};
+            if (r < nb) {
+                for (int j = j0 + grp; j < j1; j += 4) {
+                    const cx<T> f = conj(Fb[(int64_t)j * n + p + r]);
+#pragma unroll
+                    for (int c = 0; c < 8; ++c)
+                        if (c < kc) acc[c] = cfma(acc[c], f, xs[(int64_t)j * kc + c]);
+                }
+            }
+#pragma unroll
+            for (int c = 0; c < 8; ++c)
+                if (c < kc) red[(grp * NB + r) * 8 + c] = acc[c];
+            __syncthreads();
+            if (grp == 0 && r < nb) {
+                for (int c = 0; c < kc; ++c) {
+                    cx<T> sum = red[r * 8 + c];
+                    for (int q = 1; q < 4; ++q) sum = sum + red[(q * NB + r) * 8 + c];
+                    xs[(int64_t)(p + r) * kc + c] = xs[(int64_t)(p + r) * kc + c] - sum;
+                }
+            }
+        }
+    };
+    // stage the diagonal block M(p .. p+nb, p .. p+nb) into D
+    auto stage = [&](int p, int nb) {
+        for (int e = tid; e < nb * nb; e += blockDim.x) {
+            const int a = e / nb, c = e % nb;  // reads run along rows of F
+            if (CONJ) D[c][a] = conj(Fb[(int64_t)(p + a) * n + p + c]);
+            else D[a][c] = Fb[(int64_t)(p + a) * n + p + c];
+        }
+    };
+    // right-looking solve of the staged block by warp 0: lower (forward) or upper (backward)
+    auto diag_solve = [&](int p, int nb, bool lower, bool unit) {
+        if (warp != 0) return;
+        for (int step = 0; step < nb; ++step) {
+            const int i = lower ? step : nb - 1 - step;
+            if (!unit) {
+                if (lane < kc) xs[(int64_t)(p + i) * kc + lane] = cdiv(xs[(int64_t)(p + i) * kc + lane], D[i][i]);
+                __syncwarp();
+            }
+            const int cnt = lower ? nb - 1 - i : i;  // rows still to update
+            for (int e = lane; e < cnt * kc; e += 32) {
+                const int jj = e / kc, c = e % kc;
+                const int j = lower ? i + 1 + jj : jj;
+                xs[(int64_t)(p + j) * kc + c] = cfms(xs[(int64_t)(p + j) * kc + c], D[j][i], xs[(int64_t)(p + i) * kc + c]);
+            }
+            __syncwarp();
+        }
+    };
+    // forward: lower triangle (L unit, or U^H with diagonal conj(U_ii))
+    for (int p = 0; p < n; p += NB) {
+        const int nb = min(NB, n - p);
+        offdiag(p, nb, 0, p);
+        stage(p, nb);
+        __syncthreads();
+        diag_solve(p, nb, true, !CONJ);
+        __syncthreads();
+    }
+    // backward: upper triangle (U, or L^H with unit diagonal)
+    for (int p = ((n - 1) / NB) * NB; p >= 0; p -= NB) {
+        const int nb = min(NB, n - p);
+        offdiag(p, nb, p + nb, n);
+        stage(p, nb);
+        __syncthreads();
+        diag_solve(p, nb, false, CONJ);
+        __syncthreads();
+    }
+    for (int e = tid; e < n * kc; e += blockDim.x) Xb[e] = xs[e];
+}
+
+template <class T> constexpr size_t narrow_smem_bytes(int n, int kc) {
+    return sizeof(cx<T>) * ((size_t)n * kc + (size_t)DN_NB * (DN_NB + 1) + 4 * (size_t)DN_NB * 8);
+}
+
+// ------------------------------------------------------------------ resid_gemv_multi
+// R[inst, sys] -= t * A[inst] * X[inst, sys] for every system of an instance and at most
+// 8 columns, binary64.  The nsys * kc (system, column) pairs are taken 16 at a time
+// (grid.y), so A is read once per 16 pairs instead of once per system; a block holds 8
+// rows of A (one warp per row, lanes over K) and stages the X rows of the pairs in
+// shared memory in chunks of 128, transposed so that lanes read consecutive rows.
+// X and R of (inst, sys) start at (inst * nsys + sys) * sX, row-major n x kc.
+template <class AE>
+__global__ void __launch_bounds__(256) resid_gemv_multi(int n, int kc, int nsys, double t, const AE *__restrict__ A,
+                                                        int lda, int64_t sA, const cx<double> *__restrict__ X,
+                                                        int64_t sX, cx<double> *__restrict__ Rm) {
+    constexpr int CB = 16, KCH = 128;
+    __shared__ cx<double> xs[CB][KCH];
+    const int inst = blockIdx.z;
+    const int cb0 = blockIdx.y * CB, ncomb = nsys * kc;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int row = blockIdx.x * 8 + warp;
+    const AE *arow = A + (int64_t)inst * sA + (int64_t)row * lda;
+    const cx<double> *Xi = X + (int64_t)inst * nsys * sX;
+    cx<double> acc[CB];
+#pragma unroll
+    for (int c = 0; c < CB; ++c) acc[c] = {0.0, 0.0};
+    for (int k0 = 0; k0 < n; k0 += KCH) {
+        __syncthreads();
+        for (int e = threadIdx.x; e < CB * KCH; e += blockDim.x) {
+            const int c = e / KCH, l = e % KCH, comb = cb0 + c, k = k0 + l;
+            cx<double> v = {0.0, 0.0};
+            if (comb < ncomb && k < n) v = Xi[(int64_t)(comb / kc) * sX + (int64_t)k * kc + comb % kc];
+            xs[c][l] = v;
+        }
+        __syncthreads();
+        if (row < n) {
+            const int lim = min(KCH, n - k0);
+            for (int l = lane; l < lim; l += 32) {
+                const cx<double> av = as_cx<double>(arow[k0 + l]);
+#pragma unroll
+                for (int c = 0; c < CB; ++c) acc[c] = cfma(acc[c], av, xs[c][l]);
+            }
+        }
+    }
+    if (row >= n) return;
+#pragma unroll
+    for (int c = 0; c < CB; ++c) {
+        double re = acc[c].re, im = acc[c].im;
+        for (int o = 16; o > 0; o >>= 1) {
+            re += __shfl_xor_sync(0xffffffffu, re, o);
+            im += __shfl_xor_sync(0xffffffffu, im, o);
+        }
+        const int comb = cb0 + c;
+        if (lane == 0 && comb < ncomb) {
+            cx<double> *rp = Rm + (int64_t)(inst * nsys + comb / kc) * sX + (int64_t)row * kc + comb % kc;
+            rp->re -= t * re;
+            rp->im -= t * im;
+        }
+    }
+}
+
 // ------------------------------------------------------------------ resid_gemm_f32x2
 // R[z] = R[z] - t * A[z / adiv] * X[z]  (A: m x K, X: K x n, all binary64 in memory)
 // with binary64-level accuracy on the FP32 pipe.  Inside each K-block of 16 the
@@ -388,22 +584,19 @@ __global__ void __launch_bounds__(256) resid_gemm_f32x2(int m, int n, int K, dou
 
 // ------------------------------------------------------------------ max_abs
 // out[batch] = max |M_ij| over the upper triangle (j >= i) of an n x n matrix
-// (as float bits, atomicMax) -- max |U| of an LU stored in place.
+// (as float bits, atomicMax) -- max |U| of an LU stored in place.  One warp per row.
 template <class T>
-__global__ void max_abs_upper(int n, const cx<T> *M, int ld, int64_t bstride, unsigned *out) {
-    const cx<T> *m = M + (int64_t)blockIdx.z * bstride;
+__global__ void __launch_bounds__(256) max_abs_upper(int n, const cx<T> *M, int ld, int64_t bstride, unsigned *out) {
+    const int i = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    if (i >= n) return;
+    const cx<T> *m = M + (int64_t)blockIdx.z * bstride + (int64_t)i * ld;
     float local = 0.f;
-    const int64_t total = (int64_t)n * n;
-    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
-         idx += (int64_t)gridDim.x * blockDim.x) {
-        const int i = (int)(idx / n), j = (int)(idx % n);
-        if (j >= i) {
-            const cx<T> v = m[(int64_t)i * ld + j];
-            local = fmaxf(local, (float)sqrt((double)(v.re * v.re + v.im * v.im)));
-        }
+    for (int j = i + lane; j < n; j += 32) {
+        const cx<T> v = m[j];
+        local = fmaxf(local, sqrtf((float)(v.re * v.re + v.im * v.im)));
     }
     for (int o = 16; o > 0; o >>= 1) local = fmaxf(local, __shfl_xor_sync(0xffffffffu, local, o));
-    if ((threadIdx.x & 31) == 0) atomicMax(out + blockIdx.z, __float_as_uint(local));
+    if (lane == 0) atomicMax(out + blockIdx.z, __float_as_uint(local));
 }
 
 }  // namespace expm
