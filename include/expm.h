@@ -287,6 +287,43 @@ expm_status expm_apply_batched(expm_plan plan, int count, const int *n, const vo
                                const expm_opts *opts, expm_info *per_instance);
 
 /*
+ * Captured batched evaluation (no counterpart in the paper: a launch pattern around
+ * eq. expAx for many instances).  expm_batched_capture records the whole of an
+ * expm_apply_batched call -- per size bucket the padding gather, the per-pair LUs, the
+ * refinement with its stopping test decided on the device (every sweep is recorded
+ * and skips itself once all instances of the bucket have converged), the residue sums
+ * and the scatter -- into one CUDA graph over the given buffers; expm_batched_replay
+ * then evaluates the batch again with a single graph launch, reading whatever A_i and
+ * V_i hold at that time and writing Y_i.
+ *   count, n, A, a_is_complex, V, k, v_is_complex, Y, opts   as expm_apply_batched,
+ *                 except 1 <= k[i] <= 8 and every padded order must fit the fused
+ *                 narrow triangular solve (n[i] up to about 1500 for k = 1); the
+ *                 pointer arrays are read during the call only
+ *   scheme        padded orders of the size buckets: 0 (multiples of 32 up to 128, then
+ *                 steps of about a quarter; the expm_apply_batched default), 1 (all
+ *                 multiples of 32), 2 (powers of two and midpoints), or -1: capture all
+ *                 three, time two launches of each and keep the fastest (autotuning)
+ *   out           the graph; it owns its device memory (workspace, staging copies of
+ *                 the padded instances, pointer tables, per-instance results)
+ * The call runs the evaluation once outside the capture (so Y holds a result on return)
+ * and synchronises.  EXPM_EINVAL for bad arguments, EXPM_ENOMEM when the graph memory
+ * cannot be allocated, EXPM_ECUDA when the capture fails.
+ *   expm_batched_replay      enqueues the graph on stream; with per_instance (host
+ *                 array of count entries) the call waits and reports each instance as
+ *                 expm_apply_batched does, returning EXPM_EGROWTH / EXPM_ENOCONV likewise.
+ *   expm_batched_graph_info  chosen scheme, number of launch groups (bucket chunks),
+ *                 device bytes, and the timed ms per scheme (-1 where not timed).
+ */
+typedef struct expm_batch_graph_s *expm_batch_graph;
+expm_status expm_batched_capture(expm_plan plan, int count, const int *n, const void *const *A, int a_is_complex,
+                                 const void *const *V, const int *k, int v_is_complex, void *const *Y,
+                                 const expm_opts *opts, int scheme, expm_batch_graph *out);
+expm_status expm_batched_replay(expm_batch_graph graph, void *stream, expm_info *per_instance);
+expm_status expm_batched_graph_info(expm_batch_graph graph, int *scheme, int *launch_groups, size_t *device_bytes,
+                                    double ms_per_scheme[3]);
+expm_status expm_batched_graph_destroy(expm_batch_graph graph);
+
+/*
  * Request server (no counterpart in the paper: a serving pattern around eq. expAx).
  * Operators are registered once and copied into server-owned device memory; requests
  * bring device buffers V (n x k, row-major, ld k; real or complex) and Y and are

@@ -81,6 +81,17 @@ def _load() -> ctypes.CDLL:
                                      ctypes.POINTER(vp), ctypes.POINTER(ctypes.c_int), i, ctypes.POINTER(vp),
                                      ctypes.POINTER(expm_opts), ctypes.POINTER(expm_info)]
     L.expm_apply_batched.restype = i
+    L.expm_batched_capture.argtypes = [vp, i, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(vp), i,
+                                       ctypes.POINTER(vp), ctypes.POINTER(ctypes.c_int), i, ctypes.POINTER(vp),
+                                       ctypes.POINTER(expm_opts), i, ctypes.POINTER(vp)]
+    L.expm_batched_capture.restype = i
+    L.expm_batched_replay.argtypes = [vp, vp, ctypes.POINTER(expm_info)]
+    L.expm_batched_replay.restype = i
+    L.expm_batched_graph_info.argtypes = [vp, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(ctypes.c_size_t),
+                                          ctypes.POINTER(ctypes.c_double)]
+    L.expm_batched_graph_info.restype = i
+    L.expm_batched_graph_destroy.argtypes = [vp]
+    L.expm_batched_graph_destroy.restype = i
     u64 = ctypes.c_uint64
     L.expm_server_create.argtypes = [ctypes.c_size_t, i, ctypes.POINTER(vp)]
     L.expm_server_create.restype = i
@@ -307,6 +318,55 @@ def expm_apply_tridiag(plan: Plan, d, e, V, Y, prec=EXPM_FP64, t=1.0, shift_c=0.
     if st != 0 and not (not check and st == 4):
         _check(st, "expm_apply_tridiag")
     return info
+
+
+class BatchGraph:
+    """A captured batched evaluation (expm_batched_capture): replay() runs the whole batch
+    with one graph launch over the same tensors.  scheme=-1 autotunes the bucket scheme."""
+
+    def __init__(self, plan: Plan, As, Vs, Ys, prec=EXPM_FP64, t=1.0, shift_c=0.0, tol=None, max_refine=None,
+                 growth_max=None, scheme=-1):
+        cnt = len(As)
+        n_arr = (ctypes.c_int * cnt)(*[int(a.shape[0]) for a in As])
+        k_arr = (ctypes.c_int * cnt)(*[int(v.shape[1]) if len(v.shape) == 2 else 1 for v in Vs])
+        a_arr = (ctypes.c_void_p * cnt)(*[_ptr(a) for a in As])
+        v_arr = (ctypes.c_void_p * cnt)(*[_ptr(v) for v in Vs])
+        y_arr = (ctypes.c_void_p * cnt)(*[_ptr(y) for y in Ys])
+        o = make_opts(prec, t, shift_c, None, tol, max_refine, growth_max)
+        self._h = ctypes.c_void_p()
+        self.count = cnt
+        self._keep = (As, Vs, Ys, plan)        # the graph reads and writes these tensors
+        _check(lib.expm_batched_capture(plan.handle, cnt, n_arr, a_arr, int(_is_complex(As[0])), v_arr, k_arr,
+                                        int(_is_complex(Vs[0])), y_arr, ctypes.byref(o), int(scheme),
+                                        ctypes.byref(self._h)), "expm_batched_capture")
+
+    def replay(self, stream=None, want_info=False, check=True):
+        if stream is None:
+            stream = _default_stream(*self._keep[0][:1])
+        infos = (expm_info * self.count)() if want_info else None
+        st = lib.expm_batched_replay(self._h, stream, infos)
+        if st != 0 and not (not check and st in (3, 4)):
+            _check(st, "expm_batched_replay")
+        return list(infos) if want_info else None
+
+    def info(self) -> dict:
+        sc, groups, nbytes = ctypes.c_int(), ctypes.c_int(), ctypes.c_size_t()
+        ms = (ctypes.c_double * 3)()
+        _check(lib.expm_batched_graph_info(self._h, ctypes.byref(sc), ctypes.byref(groups), ctypes.byref(nbytes), ms),
+               "expm_batched_graph_info")
+        return {"scheme": sc.value, "launch_groups": groups.value, "device_bytes": nbytes.value,
+                "ms_per_scheme": list(ms)}
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            lib.expm_batched_graph_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Server:

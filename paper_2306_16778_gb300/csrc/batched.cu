@@ -59,8 +59,18 @@ __global__ void scatter_unpad(const InstPtr *__restrict__ ip, int nb, int kb, in
     }
 }
 
-// Padded order of a bucket: multiples of 32 up to 128, then steps of about 1/4.
-int bucket_order(int n) {
+// Padded order of a bucket.  Scheme 0 (the default): multiples of 32 up to 128, then
+// steps of about 1/4.  Scheme 1 (fine): multiples of 32 throughout -- least padding,
+// most buckets.  Scheme 2 (coarse): powers of two and their midpoints -- fewest,
+// largest launches.  The graph path can time all three and keep the fastest.
+int bucket_order(int n, int scheme = 0) {
+    if (scheme == 1) return (n + 31) / 32 * 32;
+    if (scheme == 2) {
+        static const int edges2[] = {64, 128, 192, 256, 384, 512, 768, 1024, 1536, 2048};
+        for (int e : edges2)
+            if (n <= e) return e;
+        return (n + 511) / 512 * 512;
+    }
     static const int edges[] = {32, 64, 96, 128, 160, 192, 256, 320, 384, 448, 512, 640, 768, 896, 1024,
                                 1280, 1536, 1792, 2048};
     for (int e : edges)
@@ -205,5 +215,371 @@ extern "C" expm_status expm_apply_batched(expm_plan p, int count, const int *n, 
     }
     if (worst == EXPM_EGROWTH) return set_error(worst, "apply_batched: LU growth exceeds opts.growth_max");
     if (worst == EXPM_ENOCONV) return set_error(worst, "apply_batched: refinement did not reach opts.tol");
+    return EXPM_OK;
+}
+
+// ------------------------------------------------------------------ captured graph
+// expm_batched_capture records the whole batched evaluation -- every bucket's gather,
+// factorization, device-controlled refinement and scatter -- into one CUDA graph over
+// the caller's buffers; expm_batched_replay launches it with a single call.  The graph
+// owns its device memory (workspace, staging, pointer tables, per-instance results).
+
+namespace expm {
+namespace {
+
+struct GraphChunk {
+    DenseGeom g;
+    int nb, kb;
+    std::vector<int> inst;  // original instance indices, in batch order
+    size_t ptr_off, res_off;  // offsets of the pointer table and of the results in the graph memory
+};
+
+struct BatchSpec {
+    int count, complex_a, v_cplx, aw, vw, yw, nsys, S;
+    const int *n, *k;
+    const void *const *A;
+    const void *const *V;
+    void *const *Y;
+    expm_opts opts;
+    DenseSystems sys;
+};
+
+std::vector<GraphChunk> plan_chunks(const BatchSpec &b, int scheme) {
+    std::vector<int> order(b.count);
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int x, int y) { return bucket_order(b.n[x], scheme) > bucket_order(b.n[y], scheme); });
+    std::vector<GraphChunk> out;
+    size_t pos = 0;
+    while (pos < order.size()) {
+        const int nb = bucket_order(b.n[order[pos]], scheme);
+        size_t end = pos;
+        int kb = 1;
+        while (end < order.size() && bucket_order(b.n[order[end]], scheme) == nb) kb = std::max(kb, b.k[order[end++]]);
+        DenseGeom g{};
+        g.n = nb;
+        g.kc = kb;
+        g.npairs = b.S;
+        g.nsys = b.nsys;
+        g.complex_a = b.complex_a;
+        g.mixed = b.opts.prec != EXPM_FP64;
+        g.t = b.opts.t;
+        g.tol = b.opts.tol;
+        g.max_refine = b.opts.max_refine;
+        g.devctl = 1;
+        g.ninst = 1;
+        const size_t per_inst = dense_workspace_bytes(g) + sizeof(double) * ((size_t)nb * nb * b.aw + 2 * (size_t)nb * kb * 2);
+        size_t chunk = std::max<size_t>(1, ((size_t)8 << 30) / per_inst);
+        chunk = std::min<size_t>(chunk, 65535 / b.nsys);
+        for (size_t c0 = pos; c0 < end; c0 += chunk) {
+            GraphChunk c;
+            c.nb = nb;
+            c.kb = kb;
+            c.g = g;
+            c.g.ninst = (int)(std::min(end, c0 + chunk) - c0);
+            for (size_t z = c0; z < c0 + (size_t)c.g.ninst; ++z) c.inst.push_back(order[z]);
+            out.push_back(std::move(c));
+        }
+        pos = end;
+    }
+    return out;
+}
+
+}  // namespace
+}  // namespace expm
+
+struct expm_batch_graph_s {
+    int device = 0;
+    int scheme = 0;
+    double ms_per_scheme[3] = {-1.0, -1.0, -1.0};
+    expm::BatchSpec spec{};
+    std::vector<expm::GraphChunk> chunks;
+    void *mem = nullptr;
+    size_t mem_bytes = 0, work_off = 0, stage_off = 0, res_bytes = 0, res_base = 0;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
+
+namespace expm {
+namespace {
+
+static inline size_t al256(size_t x) { return (x + 255) & ~size_t(255); }
+
+// Enqueues the whole evaluation of graph object G on st (used for the warm-up run and
+// inside the capture).
+cudaError_t enqueue_batched(expm_batch_graph_s *G, cudaStream_t st) {
+    Profiler off;
+    const BatchSpec &b = G->spec;
+    unsigned char *m = (unsigned char *)G->mem;
+    for (const GraphChunk &c : G->chunks) {
+        const int nb = c.nb, kb = c.kb, ni = c.g.ninst;
+        const size_t bytesA = sizeof(double) * (size_t)ni * nb * nb * b.aw;
+        const size_t bytesV = sizeof(double) * (size_t)ni * nb * kb * b.vw;
+        double *Apad = (double *)(m + G->stage_off);
+        double *Vpad = (double *)(m + G->stage_off + bytesA);
+        double *Ypad = (double *)(m + G->stage_off + bytesA + bytesV);
+        const InstPtr *dptr = (const InstPtr *)(m + c.ptr_off);
+        const unsigned gx = (unsigned)std::min<int64_t>(((int64_t)nb * nb * b.aw + 255) / 256, 1024);
+        gather_pad<<<dim3(gx, 1, ni), 256, 0, st>>>(dptr, nb, kb, b.aw, b.vw, Apad, Vpad);
+        cudaError_t err = cudaGetLastError();
+        if (err != cudaSuccess) return err;
+        DenseIO io{};
+        io.A = Apad;
+        io.lda = nb;
+        io.astride = (int64_t)nb * nb;
+        io.V = Vpad;
+        io.ldv = kb;
+        io.vstride = (int64_t)nb * kb;
+        io.v_cplx = b.v_cplx;
+        io.Y = Ypad;
+        io.ldy = kb;
+        io.ystride = (int64_t)nb * kb;
+        io.y_real = b.yw == 1 ? 1 : 0;
+        unsigned char *r = m + c.res_off;
+        DenseDevOut out{(int *)r, (double *)(r + 256), (double *)(r + 256 + al256(sizeof(double) * ni))};
+        err = dense_run_devctl(c.g, io, b.sys, m + G->work_off, st, off, out);
+        if (err != cudaSuccess) return err;
+        scatter_unpad<<<dim3((unsigned)std::min<int64_t>(((int64_t)nb * kb * b.yw + 255) / 256, 1024), 1, ni), 256, 0,
+                        st>>>(dptr, nb, kb, b.yw, Ypad);
+        if ((err = cudaGetLastError()) != cudaSuccess) return err;
+    }
+    return cudaSuccess;
+}
+
+void destroy_graph(expm_batch_graph_s *G) {
+    if (!G) return;
+    DeviceGuard guard(G->device);
+    if (G->exec) cudaGraphExecDestroy(G->exec);
+    if (G->graph) cudaGraphDestroy(G->graph);
+    if (G->mem) cudaFree(G->mem);
+    delete G;
+}
+
+// Builds, warms up and captures the graph for one bucket scheme.
+expm_status build_graph(const BatchSpec &b, int scheme, int device, expm_batch_graph_s **out) {
+    auto G = new expm_batch_graph_s();
+    G->device = device;
+    G->scheme = scheme;
+    G->spec = b;
+    G->chunks = plan_chunks(b, scheme);
+    size_t work = 0, stage = 0, ptrs = 0, res = 0;
+    for (GraphChunk &c : G->chunks) {
+        const int ni = c.g.ninst;
+        work = std::max(work, dense_workspace_bytes(c.g));
+        stage = std::max(stage, sizeof(double) * ((size_t)ni * c.nb * c.nb * b.aw + (size_t)ni * c.nb * c.kb * (b.vw + b.yw)));
+        c.ptr_off = ptrs;
+        ptrs += al256(sizeof(InstPtr) * ni);
+        c.res_off = res;
+        res += 256 + 2 * al256(sizeof(double) * ni);
+    }
+    G->work_off = 0;
+    G->stage_off = al256(work);
+    const size_t ptr_base = G->stage_off + al256(stage);
+    G->res_base = ptr_base + ptrs;
+    G->res_bytes = res;
+    G->mem_bytes = G->res_base + res;
+    for (GraphChunk &c : G->chunks) {
+        c.ptr_off += ptr_base;
+        c.res_off += G->res_base;
+    }
+    cudaError_t err = cudaMalloc(&G->mem, G->mem_bytes);
+    if (err != cudaSuccess) {
+        cudaGetLastError();
+        G->mem = nullptr;
+        destroy_graph(G);
+        return set_error(EXPM_ENOMEM, "batched_capture: device memory for the graph");
+    }
+    for (const GraphChunk &c : G->chunks) {  // pointer tables, uploaded once (outside the graph)
+        std::vector<InstPtr> hp(c.g.ninst);
+        for (int z = 0; z < c.g.ninst; ++z) {
+            const int i = c.inst[z];
+            hp[z] = InstPtr{(const double *)b.A[i], (const double *)b.V[i], (double *)b.Y[i], b.n[i], b.k[i]};
+        }
+        err = cudaMemcpy((unsigned char *)G->mem + c.ptr_off, hp.data(), sizeof(InstPtr) * hp.size(),
+                         cudaMemcpyHostToDevice);
+        if (err != cudaSuccess) break;
+    }
+    cudaStream_t st = nullptr;
+    if (err == cudaSuccess) err = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    // one plain run first: sets kernel attributes and checks every launch outside capture
+    if (err == cudaSuccess) err = enqueue_batched(G, st);
+    if (err == cudaSuccess) err = cudaStreamSynchronize(st);
+    if (err == cudaSuccess) err = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+    if (err == cudaSuccess) {
+        cudaError_t e1 = enqueue_batched(G, st);
+        cudaError_t e2 = cudaStreamEndCapture(st, &G->graph);
+        err = e1 != cudaSuccess ? e1 : e2;
+    }
+    if (err == cudaSuccess) err = cudaGraphInstantiate(&G->exec, G->graph, 0);
+    if (st) cudaStreamDestroy(st);
+    if (err != cudaSuccess) {
+        cudaGetLastError();
+        destroy_graph(G);
+        return cuda_error(err, "batched_capture");
+    }
+    *out = G;
+    return EXPM_OK;
+}
+
+// Average time of `reps` launches after one untimed launch (ms).
+double time_graph(expm_batch_graph_s *G, int reps) {
+    cudaStream_t st;
+    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) return 1e30;
+    cudaEvent_t a, b;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    cudaGraphLaunch(G->exec, st);
+    cudaEventRecord(a, st);
+    for (int r = 0; r < reps; ++r) cudaGraphLaunch(G->exec, st);
+    cudaEventRecord(b, st);
+    float ms = 0.f;
+    const bool ok = cudaEventSynchronize(b) == cudaSuccess && cudaEventElapsedTime(&ms, a, b) == cudaSuccess;
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    cudaStreamDestroy(st);
+    return ok ? ms / reps : 1e30;
+}
+
+}  // namespace
+}  // namespace expm
+
+extern "C" expm_status expm_batched_capture(expm_plan p, int count, const int *n, const void *const *A,
+                                            int a_is_complex, const void *const *V, const int *k, int v_is_complex,
+                                            void *const *Y, const expm_opts *opts_in, int scheme,
+                                            expm_batch_graph *out) {
+    if (!p || !out) return set_error(EXPM_EINVAL, "batched_capture: NULL plan or output");
+    *out = nullptr;
+    if (count < 1 || !n || !A || !V || !k || !Y) return set_error(EXPM_EINVAL, "batched_capture: empty or NULL arrays");
+    if (scheme < -1 || scheme > 2) return set_error(EXPM_EINVAL, "batched_capture: scheme must be -1 (tune), 0, 1 or 2");
+    expm_opts opts;
+    if (opts_in) opts = *opts_in; else expm_opts_default(&opts);
+    if (opts.prec != EXPM_FP64 && opts.prec != EXPM_MIXED_FP32 && opts.prec != EXPM_MIXED_F32X2)
+        return set_error(EXPM_EINVAL, "batched_capture: precision must be EXPM_FP64, EXPM_MIXED_FP32 or EXPM_MIXED_F32X2");
+    if (opts.flags != 0) return set_error(EXPM_EINVAL, "batched_capture: opts.flags must be 0");
+    if (!std::isfinite(opts.t) || !std::isfinite(opts.shift_c) || !(opts.tol > 0) || opts.max_refine < 0 ||
+        opts.max_refine > 64)
+        return set_error(EXPM_EINVAL, "batched_capture: bad t, shift_c, tol or max_refine");
+    const bool complex_a = a_is_complex != 0;
+    if (!complex_a && v_is_complex)
+        return set_error(EXPM_ENOTSUP, "batched_capture: complex V with real A (use complex A or split V)");
+    DeviceGuard guard(p->device);
+    for (int i = 0; i < count; ++i) {
+        if (n[i] < 1 || k[i] < 1 || k[i] > 8) return set_error(EXPM_EINVAL, "batched_capture: need n[i] >= 1, 1 <= k[i] <= 8");
+        if (!A[i] || !V[i] || !Y[i] || !is_device_ptr(A[i]) || !is_device_ptr(V[i]) || !is_device_ptr(Y[i]))
+            return set_error(EXPM_EINVAL, "batched_capture: instance data must be device memory");
+        if (!dense_narrow_fits(bucket_order(n[i], 2), k[i]))
+            return set_error(EXPM_EINVAL, "batched_capture: an instance is too large for the graph path");
+    }
+    BatchSpec b{};
+    b.count = count;
+    b.complex_a = complex_a;
+    b.v_cplx = v_is_complex ? 1 : 0;
+    b.aw = complex_a ? 2 : 1;
+    b.vw = v_is_complex ? 2 : 1;
+    b.yw = (complex_a || v_is_complex) ? 2 : 1;
+    b.S = p->degree / 2;
+    b.nsys = complex_a ? 2 * b.S : b.S;
+    b.n = n;
+    b.k = k;
+    b.A = A;
+    b.V = V;
+    b.Y = Y;
+    b.opts = opts;
+    b.sys.cshift = opts.shift_c;
+    const double ec = std::exp(opts.shift_c);
+    for (int s = 0; s < b.S; ++s) {
+        const double tr = -p->lam[4 * s], ti = -p->lam[4 * s + 1];
+        const double ar = p->w[4 * s], ai = p->w[4 * s + 1];
+        if (complex_a) {
+            b.sys.th_re[2 * s] = tr; b.sys.th_im[2 * s] = ti; b.sys.w_re[2 * s] = ec * ar; b.sys.w_im[2 * s] = ec * ai;
+            b.sys.th_re[2 * s + 1] = tr; b.sys.th_im[2 * s + 1] = -ti;
+            b.sys.w_re[2 * s + 1] = ec * ar; b.sys.w_im[2 * s + 1] = -ec * ai;
+        } else {
+            b.sys.th_re[s] = tr; b.sys.th_im[s] = ti; b.sys.w_re[s] = 2 * ec * ar; b.sys.w_im[s] = 2 * ec * ai;
+        }
+    }
+    // the pointer arrays are read again at capture time only: keep nothing of the caller's
+    // host arrays (the graph captured their values)
+    if (scheme >= 0) {
+        expm_batch_graph_s *G = nullptr;
+        expm_status s = build_graph(b, scheme, p->device, &G);
+        if (s != EXPM_OK) return s;
+        G->spec.n = G->spec.k = nullptr;
+        G->spec.A = G->spec.V = nullptr;
+        G->spec.Y = nullptr;
+        *out = G;
+        return EXPM_OK;
+    }
+    // autotune: capture every scheme, time each, keep the fastest
+    expm_batch_graph_s *best = nullptr;
+    double ms[3] = {-1.0, -1.0, -1.0};
+    for (int sc = 0; sc < 3; ++sc) {
+        expm_batch_graph_s *G = nullptr;
+        expm_status s = build_graph(b, sc, p->device, &G);
+        if (s != EXPM_OK) {
+            if (best) destroy_graph(best);
+            return s;
+        }
+        ms[sc] = time_graph(G, 2);
+        if (!best || ms[sc] < ms[best->scheme]) {
+            if (best) destroy_graph(best);
+            best = G;
+        } else {
+            destroy_graph(G);
+        }
+    }
+    for (int sc = 0; sc < 3; ++sc) best->ms_per_scheme[sc] = ms[sc];
+    best->spec.n = best->spec.k = nullptr;
+    best->spec.A = best->spec.V = nullptr;
+    best->spec.Y = nullptr;
+    *out = best;
+    return EXPM_OK;
+}
+
+extern "C" expm_status expm_batched_replay(expm_batch_graph G, void *stream, expm_info *per_instance) {
+    if (!G) return set_error(EXPM_EINVAL, "batched_replay: NULL graph");
+    DeviceGuard guard(G->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t err = cudaGraphLaunch(G->exec, st);
+    if (err != cudaSuccess) return cuda_error(err, "batched_replay: launch");
+    if (!per_instance) return EXPM_OK;
+    std::vector<unsigned char> h(G->res_bytes);
+    err = cudaMemcpyAsync(h.data(), (unsigned char *)G->mem + G->res_base, G->res_bytes, cudaMemcpyDeviceToHost, st);
+    if (err == cudaSuccess) err = cudaStreamSynchronize(st);
+    if (err != cudaSuccess) return cuda_error(err, "batched_replay: results");
+    const expm_opts &o = G->spec.opts;
+    expm_status worst = EXPM_OK;
+    for (const GraphChunk &c : G->chunks) {
+        const unsigned char *r = h.data() + (c.res_off - G->res_base);
+        int iters;
+        std::memcpy(&iters, r, sizeof(int));
+        const double *resid = (const double *)(r + 256);
+        const double *growth = (const double *)(r + 256 + al256(sizeof(double) * c.g.ninst));
+        for (int z = 0; z < c.g.ninst; ++z) {
+            expm_status si = EXPM_OK;
+            if (growth[z] > o.growth_max) si = EXPM_EGROWTH;
+            else if (c.g.mixed && !(resid[z] <= o.tol)) si = EXPM_ENOCONV;
+            if (si != EXPM_OK && worst == EXPM_OK) worst = si;
+            per_instance[c.inst[z]] = expm_info{iters, growth[z], resid[z], si};
+        }
+    }
+    if (worst == EXPM_EGROWTH) return set_error(worst, "batched_replay: LU growth exceeds opts.growth_max");
+    if (worst == EXPM_ENOCONV) return set_error(worst, "batched_replay: refinement did not reach opts.tol");
+    return EXPM_OK;
+}
+
+extern "C" expm_status expm_batched_graph_info(expm_batch_graph G, int *scheme, int *launch_groups,
+                                               size_t *device_bytes, double ms_per_scheme[3]) {
+    if (!G) return set_error(EXPM_EINVAL, "batched_graph_info: NULL graph");
+    if (scheme) *scheme = G->scheme;
+    if (launch_groups) *launch_groups = (int)G->chunks.size();
+    if (device_bytes) *device_bytes = G->mem_bytes;
+    if (ms_per_scheme)
+        for (int i = 0; i < 3; ++i) ms_per_scheme[i] = G->ms_per_scheme[i];
+    return EXPM_OK;
+}
+
+extern "C" expm_status expm_batched_graph_destroy(expm_batch_graph G) {
+    destroy_graph(G);
     return EXPM_OK;
 }

@@ -52,7 +52,8 @@ __global__ void load_rhs(int n, int kc, DenseIO io, int per_inst, cx<T> *X, int6
 // R[z] = V - (theta_sys - c) X[z]   (the diagonal part of the residual; the tA X part
 // is subtracted by a GEMM afterwards).  z = instance * nsys + sys.
 __global__ void residual_diag(int n, int kc, DenseIO io, int nsys, const cx<double> *X, cx<double> *R, int64_t stride,
-                              DenseSystems sys) {
+                              DenseSystems sys, const int *skip) {
+    if (skip != nullptr && *skip) return;
     const int z = blockIdx.z;
     const int b = z % nsys;
     const double *V = io.V + (int64_t)(z / nsys) * io.vstride * (io.v_cplx ? 2 : 1);
@@ -70,7 +71,8 @@ __global__ void residual_diag(int n, int kc, DenseIO io, int nsys, const cx<doub
 
 // Xc (binary32) = R (binary64) and sums of |R|^2, |X|^2 per batch entry
 __global__ void demote_and_norms(int64_t total, const cx<double> *R, const cx<double> *X, cx<float> *Xc,
-                                 int64_t stride, double *rn2, double *xn2) {
+                                 int64_t stride, double *rn2, double *xn2, const int *skip) {
+    if (skip != nullptr && *skip) return;
     const int b = blockIdx.z;
     double r2 = 0.0, x2 = 0.0;
     for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
@@ -92,7 +94,8 @@ __global__ void demote_and_norms(int64_t total, const cx<double> *R, const cx<do
 }
 
 // X (binary64) += D (binary32 correction)
-__global__ void add_correction(int64_t total, const cx<float> *D, cx<double> *X, int64_t stride) {
+__global__ void add_correction(int64_t total, const cx<float> *D, cx<double> *X, int64_t stride, const int *skip) {
+    if (skip != nullptr && *skip) return;
     const int b = blockIdx.z;
     for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
          idx += (int64_t)gridDim.x * blockDim.x) {
@@ -100,6 +103,44 @@ __global__ void add_correction(int64_t total, const cx<float> *D, cx<double> *X,
         cx<double> &x = X[(int64_t)b * stride + idx];
         x.re += (double)d.re;
         x.im += (double)d.im;
+    }
+}
+
+// Device-side stopping test after sweep `it` (devctl): per instance the largest
+// ||R||_F / ((||tA||_F + |theta - c|) ||X||_F) over its systems; all <= tol sets *done.
+// One block; z = instance * nsys + system.
+__global__ void refine_check(int ninst, int nsys, const double *rn2, const double *xn2, const double *an2, double t,
+                             DenseSystems sys, double tol, int it, int *done, int *iters, double *inst_resid) {
+    if (*done) return;
+    int bad = 0;
+    for (int inst = threadIdx.x; inst < ninst; inst += blockDim.x) {
+        double worst = 0.0;
+        for (int b = 0; b < nsys; ++b) {
+            const int z = inst * nsys + b;
+            const double shift = hypot(sys.th_re[b] - sys.cshift, sys.th_im[b]);
+            const double den = (sqrt(an2[inst]) * fabs(t) + shift) * sqrt(xn2[z]);
+            const double rel = den > 0.0 ? sqrt(rn2[z]) / den : 0.0;
+            worst = fmax(worst, rel);
+            if (!(rel <= tol)) bad = 1;
+        }
+        inst_resid[inst] = worst;
+    }
+    bad = __syncthreads_or(bad);
+    if (threadIdx.x == 0) {
+        *iters = it - 1;
+        if (!bad) *done = 1;
+    }
+}
+
+// Per instance the largest growth max|U| / max|M| over its pairs (devctl); one block.
+__global__ void growth_dev(int ninst, int npairs, const unsigned *amax, const unsigned *umax, double *inst_growth) {
+    for (int inst = threadIdx.x; inst < ninst; inst += blockDim.x) {
+        double gmax = 0.0;
+        for (int s = 0; s < npairs; ++s) {
+            const float a = __uint_as_float(amax[inst * npairs + s]), u = __uint_as_float(umax[inst * npairs + s]);
+            if (a > 0.f) gmax = fmax(gmax, (double)u / (double)a);
+        }
+        inst_growth[inst] = gmax;
     }
 }
 
@@ -278,7 +319,7 @@ static cudaError_t lu_blocked(int n, int batch, cx<T> *F, cudaStream_t st, Profi
 // Factor of system b is F[fidx[b]] -- systems of one pair share a factor.
 template <class T>
 static cudaError_t lu_solve(int n, int kc, int batch, const cx<T> *F, int64_t fstride, bool conj, cx<T> *X,
-                            int64_t xstride, cudaStream_t st, Profiler &prof) {
+                            int64_t xstride, cudaStream_t st, Profiler &prof, const int *skip = nullptr) {
     const size_t smn = narrow_smem_bytes<T>(n, kc);
     if (kc <= 8 && smn <= (200u << 10)) {  // few right-hand sides: one fused kernel per batch entry
         // the attribute is a ceiling, set to the largest size used so that concurrent
@@ -286,11 +327,12 @@ static cudaError_t lu_solve(int n, int kc, int batch, const cx<T> *F, int64_t fs
         EXPM_TRY(set_smem(lu_solve_narrow<T, false>, 200u << 10));
         EXPM_TRY(set_smem(lu_solve_narrow<T, true>, 200u << 10));
         return prof.timed(sizeof(T) == 8 ? "lu_solve<f64>" : "lu_solve<f32>", st, [&]() -> cudaError_t {
-            if (conj) lu_solve_narrow<T, true><<<batch, 256, smn, st>>>(n, kc, F, fstride, X, xstride);
-            else lu_solve_narrow<T, false><<<batch, 256, smn, st>>>(n, kc, F, fstride, X, xstride);
+            if (conj) lu_solve_narrow<T, true><<<batch, 256, smn, st>>>(n, kc, F, fstride, X, xstride, skip);
+            else lu_solve_narrow<T, false><<<batch, 256, smn, st>>>(n, kc, F, fstride, X, xstride, skip);
             return cudaGetLastError();
         });
     }
+    if (skip != nullptr) return cudaErrorInvalidValue;  // device-side control needs the narrow kernel
     const size_t sm2 = 2 * tri_smem_bytes<T>();
     const int cb = (kc + 63) / 64;
     EXPM_TRY(set_smem(trsm_left<T, true, true, false>, sm2));
@@ -344,7 +386,7 @@ static cudaError_t lu_solve(int n, int kc, int batch, const cx<T> *F, int64_t fs
 // the poles and can be kept for later right-hand sides.
 struct DenseLayout {
     size_t amax, umax, F, tcA, tcB, tcflag, factor_total;  // factor part
-    size_t rn2, xn2, an2, X, R, D, solve_total;  // solve part (offsets from its own base)
+    size_t rn2, xn2, an2, ctl, X, R, D, solve_total;  // solve part (offsets from its own base)
 };
 static inline size_t align_up(size_t x) { return (x + 255) & ~size_t(255); }
 
@@ -367,6 +409,7 @@ static DenseLayout dense_layout(const DenseGeom &g) {
     L.rn2 = off; off += align_up(nsz * sizeof(double));
     L.xn2 = off; off += align_up(nsz * sizeof(double));
     L.an2 = off; off += align_up((size_t)g.ninst * sizeof(double));
+    L.ctl = off; off += align_up(sizeof(int));
     L.X = off; off += align_up(nsz * nk * sizeof(cx<double>));
     L.R = off;
     L.D = off;
@@ -412,14 +455,14 @@ static cudaError_t factor_pairs(const DenseGeom &g, const DenseIO &io, const Den
 
 template <class T>
 static cudaError_t solve_systems(const DenseGeom &g, const cx<T> *F, cx<T> *X, int64_t xstride, cudaStream_t st,
-                                 Profiler &prof) {
+                                 Profiler &prof, const int *skip = nullptr) {
     const int64_t fs = (int64_t)g.n * g.n;
     const int batch = g.ninst * g.npairs;
-    if (!g.complex_a) return lu_solve<T>(g.n, g.kc, batch, F, fs, false, X, xstride, st, prof);
+    if (!g.complex_a) return lu_solve<T>(g.n, g.kc, batch, F, fs, false, X, xstride, st, prof, skip);
     // systems 2s (theta) and 2s+1 (conj theta) of every instance share factor s: the
     // even and the odd systems each form a batch with stride 2*xstride
-    EXPM_TRY(lu_solve<T>(g.n, g.kc, batch, F, fs, false, X, 2 * xstride, st, prof));
-    return lu_solve<T>(g.n, g.kc, batch, F, fs, true, X + xstride, 2 * xstride, st, prof);
+    EXPM_TRY(lu_solve<T>(g.n, g.kc, batch, F, fs, false, X, 2 * xstride, st, prof, skip));
+    return lu_solve<T>(g.n, g.kc, batch, F, fs, true, X + xstride, 2 * xstride, st, prof, skip);
 }
 
 cudaError_t dense_factor(const DenseGeom &g, const DenseIO &io, const DenseSystems &sys, void *fwork, cudaStream_t st,
@@ -499,7 +542,7 @@ cudaError_t dense_solve(const DenseGeom &g, const DenseIO &io, const DenseSystem
         // of the current X is checked before every sweep and once after the last one
         for (int it = 0;; ++it) {
             // R = V - (tA - cI + theta I) X, binary64
-            residual_diag<<<dim3(gx, 1, nsz), 256, 0, st>>>(g.n, g.kc, io, g.nsys, X, R, nk, sys);
+            residual_diag<<<dim3(gx, 1, nsz), 256, 0, st>>>(g.n, g.kc, io, g.nsys, X, R, nk, sys, nullptr);
             EXPM_TRY(cudaGetLastError());
             if (it > 0) {
                 if (g.kc <= 8) {
@@ -508,10 +551,10 @@ cudaError_t dense_solve(const DenseGeom &g, const DenseIO &io, const DenseSystem
                         if (g.complex_a)
                             resid_gemv_multi<cx<double>><<<gg, 256, 0, st>>>(g.n, g.kc, g.nsys, g.t,
                                                                               (const cx<double> *)io.A, (int)io.lda,
-                                                                              io.astride, X, nk, R);
+                                                                              io.astride, X, nk, R, nullptr);
                         else
                             resid_gemv_multi<double><<<gg, 256, 0, st>>>(g.n, g.kc, g.nsys, g.t, io.A, (int)io.lda,
-                                                                          io.astride, X, nk, R);
+                                                                          io.astride, X, nk, R, nullptr);
                         return cudaGetLastError();
                     }));
                 } else EXPM_TRY(prof.timed("resid_gemm<f32x2>", st, [&] {
@@ -528,7 +571,7 @@ cudaError_t dense_solve(const DenseGeom &g, const DenseIO &io, const DenseSystem
             }
             EXPM_TRY(cudaMemsetAsync(rn2, 0, sizeof(double) * nsz, st));
             EXPM_TRY(cudaMemsetAsync(xn2, 0, sizeof(double) * nsz, st));
-            demote_and_norms<<<dim3(gx, 1, nsz), 256, 0, st>>>(nk, R, X, D, nk, rn2, xn2);
+            demote_and_norms<<<dim3(gx, 1, nsz), 256, 0, st>>>(nk, R, X, D, nk, rn2, xn2, nullptr);
             EXPM_TRY(cudaGetLastError());
             if (it > 0) {
                 EXPM_TRY(cudaMemcpyAsync(h.data(), rn2, sizeof(double) * nsz, cudaMemcpyDeviceToHost, st));
@@ -552,7 +595,7 @@ cudaError_t dense_solve(const DenseGeom &g, const DenseIO &io, const DenseSystem
                 if (done || it > g.max_refine) break;
             }
             EXPM_TRY(solve_systems<float>(g, (const cx<float> *)F, D, nk, st, prof));
-            add_correction<<<dim3(gx, 1, nsz), 256, 0, st>>>(nk, D, X, nk);
+            add_correction<<<dim3(gx, 1, nsz), 256, 0, st>>>(nk, D, X, nk, nullptr);
             EXPM_TRY(cudaGetLastError());
         }
     }
@@ -561,6 +604,88 @@ cudaError_t dense_solve(const DenseGeom &g, const DenseIO &io, const DenseSystem
         return cudaGetLastError();
     }));
     return cudaSuccess;
+}
+
+bool dense_narrow_fits(int n, int kc) { return kc <= 8 && narrow_smem_bytes<float>(n, kc) <= (200u << 10); }
+
+// Device-controlled refinement (mixed, kc <= 8): the same sweeps as dense_solve, all
+// enqueued up front -- 1 + max_refine solves and max_refine + 1 residual checks -- each
+// kernel returning at once after refine_check has found every instance converged.  The
+// result is bit-identical to dense_solve's, which stops launching at that point.
+static cudaError_t dense_solve_devctl(const DenseGeom &g, const DenseIO &io, const DenseSystems &sys,
+                                      const void *fwork, void *swork, cudaStream_t st, Profiler &prof,
+                                      const DenseDevOut &out) {
+    if (!g.mixed || g.kc > 8 || narrow_smem_bytes<float>(g.n, g.kc) > (200u << 10)) return cudaErrorInvalidValue;
+    const int64_t nk = (int64_t)g.n * g.kc;
+    const DenseLayout L = dense_layout(g);
+    const cx<float> *F = (const cx<float> *)((const unsigned char *)fwork + L.F);
+    unsigned char *p = (unsigned char *)swork;
+    double *rn2 = (double *)(p + L.rn2);
+    double *xn2 = (double *)(p + L.xn2);
+    double *an2 = (double *)(p + L.an2);
+    int *done = (int *)(p + L.ctl);
+    cx<double> *X = (cx<double> *)(p + L.X);
+    cx<double> *R = (cx<double> *)(p + L.R);
+    cx<float> *D = (cx<float> *)(p + L.D);
+    const int nsz = g.ninst * g.nsys;
+    const unsigned gx = grid1d(nk);
+    EXPM_TRY(cudaMemsetAsync(X, 0, (size_t)nsz * nk * sizeof(cx<double>), st));
+    EXPM_TRY(cudaMemsetAsync(done, 0, sizeof(int), st));
+    EXPM_TRY(cudaMemsetAsync(out.iters, 0, sizeof(int), st));
+    EXPM_TRY(cudaMemsetAsync(an2, 0, sizeof(double) * g.ninst, st));
+    frob2<<<dim3((unsigned)std::min(g.n, 1024), 1, g.ninst), 256, 0, st>>>(g.n, io.A, io.lda, io.astride, g.complex_a,
+                                                                          an2);
+    EXPM_TRY(cudaGetLastError());
+    for (int it = 0; it <= g.max_refine + 1; ++it) {
+        residual_diag<<<dim3(gx, 1, nsz), 256, 0, st>>>(g.n, g.kc, io, g.nsys, X, R, nk, sys, done);
+        EXPM_TRY(cudaGetLastError());
+        if (it > 0) {
+            EXPM_TRY(prof.timed("resid_gemv<f64>", st, [&] {
+                dim3 gg((g.n + 7) / 8, (g.nsys * g.kc + 15) / 16, g.ninst);
+                if (g.complex_a)
+                    resid_gemv_multi<cx<double>><<<gg, 256, 0, st>>>(g.n, g.kc, g.nsys, g.t, (const cx<double> *)io.A,
+                                                                      (int)io.lda, io.astride, X, nk, R, done);
+                else
+                    resid_gemv_multi<double><<<gg, 256, 0, st>>>(g.n, g.kc, g.nsys, g.t, io.A, (int)io.lda,
+                                                                  io.astride, X, nk, R, done);
+                return cudaGetLastError();
+            }));
+        }
+        EXPM_TRY(cudaMemsetAsync(rn2, 0, sizeof(double) * nsz, st));
+        EXPM_TRY(cudaMemsetAsync(xn2, 0, sizeof(double) * nsz, st));
+        demote_and_norms<<<dim3(gx, 1, nsz), 256, 0, st>>>(nk, R, X, D, nk, rn2, xn2, done);
+        EXPM_TRY(cudaGetLastError());
+        if (it > 0) {
+            refine_check<<<1, 1024, 0, st>>>(g.ninst, g.nsys, rn2, xn2, an2, g.t, sys, g.tol, it, done, out.iters,
+                                             out.inst_resid);
+            EXPM_TRY(cudaGetLastError());
+        }
+        if (it <= g.max_refine) {
+            EXPM_TRY(solve_systems<float>(g, F, D, nk, st, prof, done));
+            add_correction<<<dim3(gx, 1, nsz), 256, 0, st>>>(nk, D, X, nk, done);
+            EXPM_TRY(cudaGetLastError());
+        }
+    }
+    return prof.timed("accumulate", st, [&] {
+        accumulate<<<dim3(gx, 1, g.ninst), 256, 0, st>>>(g.n, g.kc, g.nsys, X, nk, sys, io);
+        return cudaGetLastError();
+    });
+}
+
+cudaError_t dense_run_devctl(const DenseGeom &g, const DenseIO &io, const DenseSystems &sys, void *work,
+                             cudaStream_t st, Profiler &prof, const DenseDevOut &out) {
+    const DenseLayout L = dense_layout(g);
+    unsigned char *p = (unsigned char *)work;
+    EXPM_TRY(dense_factor(g, io, sys, p, st, prof));
+    growth_dev<<<1, 1024, 0, st>>>(g.ninst, g.npairs, (const unsigned *)(p + L.amax), (const unsigned *)(p + L.umax),
+                                   out.inst_growth);
+    EXPM_TRY(cudaGetLastError());
+    if (g.mixed) return dense_solve_devctl(g, io, sys, p, p + L.factor_total, st, prof, out);
+    // binary64: no refinement, and its solve reads nothing back
+    EXPM_TRY(cudaMemsetAsync(out.iters, 0, sizeof(int), st));
+    EXPM_TRY(cudaMemsetAsync(out.inst_resid, 0, sizeof(double) * g.ninst, st));
+    DenseResult unused;
+    return dense_solve(g, io, sys, p, p + L.factor_total, st, prof, &unused);
 }
 
 cudaError_t dense_run(const DenseGeom &g, const DenseIO &io, const DenseSystems &sys, void *work, cudaStream_t st,

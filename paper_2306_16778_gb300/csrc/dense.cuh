@@ -35,6 +35,16 @@ struct DenseGeom {
     double t;       // time factor
     double tol;     // refinement tolerance
     int max_refine;
+    int devctl = 0;  // mixed, kc <= 8 only: refinement decided on the device (no host
+                     // synchronisation; every sweep is launched and skips itself once the
+                     // stopping test has passed), so the whole solve can be captured in a graph
+};
+
+// Device-side results of a devctl solve, written where these point (device memory).
+struct DenseDevOut {
+    int *iters;          // refinement sweeps applied (one int)
+    double *inst_resid;  // per instance: the last relative residual formed
+    double *inst_growth; // per instance: growth factor of its pairs' LUs
 };
 
 struct DenseIO {
@@ -71,5 +81,11 @@ cudaError_t dense_solve(const DenseGeom &g, const DenseIO &io, const DenseSystem
 cudaError_t dense_growth(const DenseGeom &g, const void *fwork, cudaStream_t st, DenseResult *res);
 cudaError_t dense_run(const DenseGeom &g, const DenseIO &io, const DenseSystems &sys, void *work, cudaStream_t st,
                       Profiler &prof, DenseResult *res);
+// whether the fused narrow triangular solve (kc <= 8, solution in shared memory) takes
+// an n x kc right-hand side in binary32 -- the requirement of a devctl solve
+bool dense_narrow_fits(int n, int kc);
+// devctl form: factor + growth + solve fully enqueued on st (nothing read back); results to out
+cudaError_t dense_run_devctl(const DenseGeom &g, const DenseIO &io, const DenseSystems &sys, void *work,
+                             cudaStream_t st, Profiler &prof, const DenseDevOut &out);
 
 }  // namespace expm

@@ -318,7 +318,8 @@ __global__ void __launch_bounds__(256) resid_gemv(int m, int n, int K, double t,
 // cross-group partial sums 4 x DN_NB x 8.
 template <class T, bool CONJ>
 __global__ void __launch_bounds__(256) lu_solve_narrow(int n, int kc, const cx<T> *__restrict__ F, int64_t fstride,
-                                                       cx<T> *X, int64_t xstride) {
+                                                       cx<T> *X, int64_t xstride, const int *skip) {
+    if (skip != nullptr && *skip) return;  // device-side refinement already converged
     constexpr int NB = DN_NB;
     cx<T> *xs = reinterpret_cast<cx<T> *>(dyn_smem);                       // [n][kc]
     cx<T>(*D)[NB + 1] = reinterpret_cast<cx<T>(*)[NB + 1]>(xs + (size_t)n * kc);  // diagonal block
@@ -448,7 +449,8 @@ template <class T> constexpr size_t narrow_smem_bytes(int n, int kc) {
 template <class AE>
 __global__ void __launch_bounds__(256) resid_gemv_multi(int n, int kc, int nsys, double t, const AE *__restrict__ A,
                                                         int lda, int64_t sA, const cx<double> *__restrict__ X,
-                                                        int64_t sX, cx<double> *__restrict__ Rm) {
+                                                        int64_t sX, cx<double> *__restrict__ Rm, const int *skip) {
+    if (skip != nullptr && *skip) return;
     constexpr int CB = 16, KCH = 128;
     __shared__ cx<double> xs[CB][KCH];
     const int inst = blockIdx.z;

@@ -914,7 +914,9 @@ cudaError_t tri_mixed_solve(const TriGeom &g, const double *V, double *Y, const 
     if (err != cudaSuccess) return err;
     const size_t smem = g.P > 1 ? (size_t)4 * (g.P - 1) * sizeof(cx<float>) : 0;
     if (g.P > 1) {
-        err = cudaFuncSetAttribute(tri_reduced_cr<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        // a ceiling for the largest reduced system, never lowered under a concurrent launch
+        err = cudaFuncSetAttribute(tri_reduced_cr<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)(4 * (size_t)(TRI_PMAX - 1) * sizeof(cx<float>)));
         if (err != cudaSuccess) return err;
     }
     const int npass = 1 + mo.max_refine;

@@ -63,3 +63,90 @@ def test_batched_equals_single_calls():
         P.expm_apply_dense(plan, A, V, Y1)
         torch.cuda.synchronize()
         assert matrix.rel_err(Y.cpu().numpy(), Y1.cpu().numpy()) <= 1e-13
+
+
+# ------------------------------------------------------------------ captured graph
+
+def _batch(seed, count, lo, hi, complex_=True, kmax=3):
+    g = workloads.rng(seed)
+    sizes = list(workloads.batch_sizes(count, g, lo, hi)) + [1, 33]
+    inst = [workloads.dense_symmetric(int(n), -30.0, 0.0, 1 + i % kmax, g, complex_) for i, n in enumerate(sizes)]
+    As = [torch.from_numpy(A).to(DEV) for A, _, _, _ in inst]
+    Vs = [torch.from_numpy(V).to(DEV) for _, _, _, V in inst]
+    return inst, As, Vs
+
+
+@pytest.mark.parametrize("prec", [P.EXPM_FP64, P.EXPM_MIXED_FP32])
+def test_graph_replay_equals_batched_call(prec):
+    """With the default bucket scheme the captured graph performs the same launches, the
+    refinement decided on the device instead of the host: bit-identical results and the
+    same per-instance reports (sweeps, growth, status; residual norms to rounding)."""
+    inst, As, Vs = _batch(510, 30, 8, 400)
+    plan = P.Plan(degree=12)
+    Ya = [torch.empty_like(v) for v in Vs]
+    ia = P.expm_apply_batched(plan, As, Vs, Ya, prec=prec)
+    Yg = [torch.empty_like(v) for v in Vs]
+    gr = P.BatchGraph(plan, As, Vs, Yg, prec=prec, scheme=0)
+    for y in Yg:
+        y.zero_()
+    ig = gr.replay(want_info=True)
+    torch.cuda.synchronize()
+    for a, b in zip(Ya, Yg):
+        assert torch.equal(a, b)
+    for a, b in zip(ia, ig):
+        # the residual norms are sums taken with atomics: equal up to their last bits
+        assert (a.refine_iters_max, a.growth_max_seen, a.status_worst) == \
+               (b.refine_iters_max, b.growth_max_seen, b.status_worst)
+        assert abs(a.resid_rel_max - b.resid_rel_max) <= 1e-12 * max(a.resid_rel_max, 1e-300)
+    gr.close()
+
+
+def test_graph_replay_reads_new_data():
+    """The graph reads the instance buffers at every launch: new V, new result."""
+    inst, As, Vs = _batch(511, 20, 16, 300)
+    plan = P.Plan(degree=12)
+    Yg = [torch.empty_like(v) for v in Vs]
+    gr = P.BatchGraph(plan, As, Vs, Yg, prec=P.EXPM_MIXED_FP32, scheme=1)
+    g = workloads.rng(512)
+    for v in Vs:
+        v.copy_(torch.from_numpy(workloads.complex_normal(tuple(v.shape), g)))
+    gr.replay()
+    torch.cuda.synchronize()
+    th, a = coeffs.theta(12), coeffs.residues(12)
+    for (A, _, _, _), V, Y in zip(inst, Vs, Yg):
+        Vh = V.cpu().numpy()
+        Yo, _ = matrix.apply_dense(A, Vh, th, a)
+        assert _close(Y.cpu().numpy(), Yo, Vh, 12, 1e-8)
+    gr.close()
+
+
+def test_graph_autotune():
+    """scheme = -1 captures and times all three bucket schemes and keeps the fastest."""
+    inst, As, Vs = _batch(513, 40, 16, 500, kmax=1)
+    plan = P.Plan(degree=12)
+    Yg = [torch.empty_like(v) for v in Vs]
+    gr = P.BatchGraph(plan, As, Vs, Yg, prec=P.EXPM_MIXED_FP32, scheme=-1)
+    info = gr.info()
+    assert info["scheme"] in (0, 1, 2)
+    assert all(ms > 0 for ms in info["ms_per_scheme"])
+    assert info["ms_per_scheme"][info["scheme"]] == min(info["ms_per_scheme"])
+    infos = gr.replay(want_info=True)
+    assert all(i.status_worst == 0 for i in infos)
+    th, a = coeffs.theta(12), coeffs.residues(12)
+    for (A, _, _, V), Y in zip(inst, Yg):
+        Yo, _ = matrix.apply_dense(A, V, th, a)
+        assert _close(Y.cpu().numpy(), Yo, V, 12, 1e-8)
+    gr.close()
+
+
+def test_graph_rejections():
+    plan = P.Plan(degree=12)
+    A = torch.eye(10, dtype=torch.complex128, device=DEV)
+    V = torch.ones(10, 9, dtype=torch.complex128, device=DEV)
+    with pytest.raises(P.ExpmError) as ei:                      # more than 8 columns
+        P.BatchGraph(plan, [A], [V], [torch.empty_like(V)], scheme=0)
+    assert ei.value.status == 1
+    V = torch.ones(10, 1, dtype=torch.complex128, device=DEV)
+    with pytest.raises(P.ExpmError) as ei:                      # unknown scheme
+        P.BatchGraph(plan, [A], [V], [torch.empty_like(V)], scheme=3)
+    assert ei.value.status == 1
