@@ -464,6 +464,24 @@ def run_batched(args):
     worst = max(float((a - b).abs().pow(2).sum().sqrt() / b.abs().pow(2).sum().sqrt())
                 for a, b in zip(Ys["mixed"], Ys["fp64"]))
     out["mixed_vs_fp64_worst_rel"] = worst
+    # the same batch captured into one CUDA graph (bucket scheme autotuned), replayed
+    Yg = [torch.empty_like(v) for v in Vs]
+    t0 = time.perf_counter()
+    gr = P.BatchGraph(plan, As, Vs, Yg, prec=P.EXPM_MIXED_FP32, scheme=-1)
+    cap_s = time.perf_counter() - t0
+    infos = gr.replay(want_info=True)
+    ts = _time_calls(lambda: gr.replay(), max(1, args.steps), 1)
+    med = statistics.median(ts)
+    gi = gr.info()
+    out["mixed_graph"] = {"s_per_batch": round(med, 4), "instances_per_s": round(args.batch_count / med, 2),
+                          "scheme": gi["scheme"], "ms_per_scheme": [round(x, 2) for x in gi["ms_per_scheme"]],
+                          "launch_groups": gi["launch_groups"], "capture_and_tune_s": round(cap_s, 2),
+                          "refine_sweeps_max": max(i.refine_iters_max for i in infos),
+                          "worst_status": max(i.status_worst for i in infos),
+                          "vs_fp64_worst_rel": max(float((a - b).abs().pow(2).sum().sqrt() /
+                                                         b.abs().pow(2).sum().sqrt())
+                                                   for a, b in zip(Yg, Ys["fp64"]))}
+    gr.close()
     print(json.dumps(out), flush=True)
 
 
