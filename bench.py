@@ -46,9 +46,12 @@ DEGREE = 16
 SMS = 152
 FP64_FLOP_PER_CLK_SM = 4
 SM_MAX_MHZ = 2070.0
-# algorithmic flops per (system, column, row) of the dominant kernel (tri_block_solve):
-# forward 9 (t = v - e d' : 3, d' = g t : 6), back 8 (x = d' - c' x+ : 8), sum Re(W x) 4
-FLOPS_K3 = 21
+# algorithmic flops per (system, column, row) of the dominant kernel (tri_block_solve),
+# whose forward substitution runs on z = W d' with the residue weight folded into its
+# coefficients: forward 10 (z = a v - b z_prev: a v 2, b z_prev 6, subtraction 2), back 8
+# (x = z - c' x+: product 6, subtraction 2); Re(W x) is then Re(x) and costs nothing (the
+# reduce-scatter addition over the systems, < 1 per element, is not counted)
+FLOPS_K3 = 18
 
 
 def _hbm_peak() -> float:
@@ -65,11 +68,11 @@ HBM_GBS = _hbm_peak()
 MIXED_OPTS = dict(tol=1e-10, max_refine=1)
 # algorithmic HBM bytes of one evaluation: d, e, V read, Y written (binary64)
 # dram bytes (read + write) per launch of tri_block_solve<f64> at N = 2^20: one ncu
-# capture at N = 2^19 (1.2923 GB: 729.9 MB read + 562.3 MB write) scaled by 2, the
+# capture at N = 2^19 (1.4247 GB: 857.7 MB read + 567.0 MB write) scaled by 2, the
 # traffic being proportional to N; valid while the kernel's source text hashes to
 # TRAFFIC_SRC_SHA (otherwise reported as null)
-TRAFFIC_K3 = 2.5845e9
-TRAFFIC_SRC_SHA = "3d4a93a079644dc8"
+TRAFFIC_K3 = 2.8495e9
+TRAFFIC_SRC_SHA = "b5a5c00d7042b497"
 
 
 def log(*a):

@@ -198,8 +198,8 @@ expm_status expm_apply_tridiag(expm_plan plan, int64_t N, const double *d, const
  *   device memory (host buffers would need staging memory: EXPM_EINVAL).
  *   Size limit: a problem whose scratch exceeds EXPM_NOALLOC_SCRATCH_BYTES is
  *   rejected with EXPM_EINVAL and a message giving the bytes needed (about
- *   N * (272 + 136 r) bytes for degree 16 and r >= 2 real right-hand sides, so N up
- *   to about 24,000 for r = 8).
+ *   N * (400 + 136 r) bytes for degree 16 and r >= 2 real right-hand sides, so N up
+ *   to about 22,000 for r = 8).
  *   Set-up: the first call on each device looks up the array's device address
  *   (cudaGetSymbolAddress) with that device current; make that first call before any
  *   stream capture.

@@ -60,6 +60,15 @@ template <> EXPM_D void store_out<f32x2>(double *Y, int64_t idx, f32x2 v) {
     reinterpret_cast<f32x2 *>(Y)[idx] = v;
 }
 
+// z = a v - b z_prev  (a, b, z_prev complex; v real): one row of the weighted forward
+// substitution, two multiplies and four FMAs in binary64
+template <class R> EXPM_D cx<R> zstep(cx<R> a, cx<R> b, R v, cx<R> zp) {
+    return {a.re * v - b.re * zp.re + b.im * zp.im, a.im * v - b.re * zp.im - b.im * zp.re};
+}
+template <> EXPM_D cx<double> zstep<double>(cx<double> a, cx<double> b, double v, cx<double> zp) {
+    return {fma(b.im, zp.im, fma(-b.re, zp.re, a.re * v)), fma(-b.im, zp.re, fma(-b.re, zp.im, a.im * v))};
+}
+
 template <class R, int LG>
 __global__ void __launch_bounds__(128) tri_block_solve(TriGeom g, const R *__restrict__ eP,
                                                        const R *__restrict__ VP, TriPoles ps,
@@ -87,35 +96,39 @@ __global__ void __launch_bounds__(128) tri_block_solve(TriGeom g, const R *__res
     const cx<R> sr_v = has_right ? SG[(int64_t)b * g.Rc + j] : cxz<R>();
     const R eleft = has_left ? eP[first - 1] : RealOps<R>::zero();
     const R eright = has_right ? eP[first + len - 1] : RealOps<R>::zero();
-    const cx<R> *F = fact + (int64_t)s * g.N * 2;
+    const cx<R> *F = fact + (int64_t)s * g.N * 3;  // per row: c', a = W g, b = g e'_{q-1}
     cx<R> *SC = scr + (((int64_t)first * g.Rc + j) * LG + sl);  // this lane's column
     const int64_t sstride = (int64_t)g.Rc * LG;
 
-    // forward substitution
-    cx<R> dp = cxz<R>();
+    // forward substitution on z = W d' (the factor kernel folded W into a and b):
+    // z_i = a_i (v_i - boundary terms) - b_i z_{i-1}; the back substitution then gives W x
+    cx<R> dz = cxz<R>();
     R vn = VP[first * g.Rc + j];
-    cx<R> gn = F[2 * first + 1];
-    R en = RealOps<R>::zero();
+    cx<R> an = F[3 * first + 1], bn = F[3 * first + 2];
     for (int i = 0; i < len; ++i) {
         const int64_t q = first + i;
-        const R vq = vn, elq = en;  // v[q], e'[q-1]
-        const cx<R> gi = gn;
+        const R vq = vn;
+        const cx<R> aq = an, bq = bn;
         if (i + 1 < len) {
             vn = VP[(q + 1) * g.Rc + j];
-            gn = F[2 * (q + 1) + 1];
-            en = eP[q];
+            an = F[3 * (q + 1) + 1];
+            bn = F[3 * (q + 1) + 2];
         }
-        cx<R> rhs = (i > 0) ? real_minus_scaled(vq, elq, dp) : cx<R>{vq, RealOps<R>::zero()};
-        if (i == 0 && has_left) rhs = rhs - scale(eleft, sl_v);
-        if (i == len - 1 && has_right) rhs = rhs - scale(eright, sr_v);
-        dp = gi * rhs;
-        SC[(int64_t)i * sstride] = dp;
+        if ((i == 0 && has_left) || (i == len - 1 && has_right)) {  // a separator value enters
+            cx<R> rhs = {vq, RealOps<R>::zero()};
+            if (i == 0 && has_left) rhs = rhs - scale(eleft, sl_v);
+            if (i == len - 1 && has_right) rhs = rhs - scale(eright, sr_v);
+            dz = aq * rhs - bq * dz;
+        } else {
+            dz = zstep(aq, bq, vq, dz);  // b = 0 on a block's first row
+        }
+        SC[(int64_t)i * sstride] = dz;
     }
     // back substitution in chunks of LG rows; each chunk's weighted contributions
     // are reduce-scattered so lane l writes row (i0 - l) of column j
     cx<R> xn = cxz<R>();
     cx<R> scn = SC[(int64_t)(len - 1) * sstride];
-    cx<R> cn = (len > 1) ? F[2 * (first + len - 2)] : cxz<R>();  // c' of row last-1
+    cx<R> cn = (len > 1) ? F[3 * (first + len - 2)] : cxz<R>();  // c' of row last-1
     for (int i0 = len - 1; i0 >= 0; i0 -= LG) {
         R v[LG];
 #pragma unroll
@@ -128,10 +141,10 @@ __global__ void __launch_bounds__(128) tri_block_solve(TriGeom g, const R *__res
                 cx<R> x = sc;
                 if (i < len - 1) {
                     x = csub_mul(sc, cn, xn);            // cn is c'[row i]
-                    if (i > 0) cn = F[2 * (first + i - 1)];  // c'[row i-1] for the next row
+                    if (i > 0) cn = F[3 * (first + i - 1)];  // c'[row i-1] for the next row
                 }
                 xn = x;
-                v[r] = re_mul(wgt, x);
+                v[r] = active ? x.re : RealOps<R>::zero();  // x is W x_s: its real part is the term
             }
         }
         reduce_scatter<LG>(gmask, sl, v);
@@ -190,7 +203,7 @@ static TriLayout tri_layout(const TriGeom &g, bool ff) {
     const size_t c = 16;  // sizeof(cx<double>) == sizeof(cx<f32x2>)
     TriLayout L{};
     size_t off = 0;
-    L.fact = off; off += align_up((size_t)g.S * g.N * 2 * c);
+    L.fact = off; off += align_up((size_t)g.S * g.N * 3 * c);
     L.spk = off; off += align_up((size_t)g.S * g.P * 4 * c);
     L.prepd = off; off += align_up((size_t)g.N * 8);
     L.prepe = off; off += align_up((size_t)g.N * 8);

@@ -59,12 +59,16 @@ __global__ void __launch_bounds__(128) tri_block_factor(TriGeom g, const R *__re
     const int64_t first = (int64_t)b * g.B;
     const int len = (b < g.P - 1) ? g.m : (int)(g.N - first);
     const cx<R> theta = cx_from<R>(ps.th_re[s], ps.th_im[s]);
-    cx<R> *F = fact + ((int64_t)s * g.N) * 2;
+    const cx<R> wgt = cx_from<R>(ps.w_re[s], ps.w_im[s]);
+    cx<R> *F = fact + ((int64_t)s * g.N) * 3;  // per row: c', a = W g, b = g e'_{q-1}
     cx<R> *U = us + (int64_t)s * g.N;
     cx<R> *W = wsp + (int64_t)s * g.N;
 
-    // forward: LU of M_b (c'_i, g_i = 1/w_i) and the forward-eliminated eps_first
-    cx<R> cprev = cxz<R>(), hprev = cxz<R>();
+    // forward: LU of M_b (c'_i, g_i = 1/w_i) and the forward-eliminated eps_first.
+    // The solve kernel runs the forward substitution on z = W d' (W the system's residue
+    // weight): z_i = a_i v_i - b_i z_{i-1} with a_i = W g_i, b_i = g_i e'_{i-1}, so that
+    // its back substitution yields W x directly and Re(W x) costs nothing.
+    cx<R> cprev = cxz<R>(), hprev = cxz<R>(), glast = cxz<R>();
     R dn = dP[first], en = eP[first];
     R eprev = RealOps<R>::zero();  // e'[q-1]
     for (int i = 0; i < len; ++i) {
@@ -79,9 +83,11 @@ __global__ void __launch_bounds__(128) tri_block_factor(TriGeom g, const R *__re
         const cx<R> gi = cinv(w);
         const cx<R> cp = (i < len - 1) ? scale(eq, gi) : cxz<R>();
         const cx<R> h = (i == 0) ? gi : -(gi * scale(eprev, hprev));
+        F[3 * q] = cp;
+        F[3 * q + 1] = wgt * gi;
+        F[3 * q + 2] = (i > 0) ? scale(eprev, gi) : cxz<R>();
         eprev = eq;
-        F[2 * q] = cp;
-        F[2 * q + 1] = gi;
+        glast = gi;
         U[q] = h;
         cprev = cp;
         hprev = h;
@@ -89,7 +95,7 @@ __global__ void __launch_bounds__(128) tri_block_factor(TriGeom g, const R *__re
     // backward: u = M_b^{-1} eps_first, w = M_b^{-1} eps_last.  The chain per row is
     // short, so the (h, c') of the next TRI_PF rows are kept in flight.
     const int64_t last = first + len - 1;
-    cx<R> un = U[last], wn = F[2 * last + 1];
+    cx<R> un = U[last], wn = glast;
     const cx<R> uL = un, wL = wn;
     W[last] = wn;
     cx<R> hq[TRI_PF], cq[TRI_PF];
@@ -97,7 +103,7 @@ __global__ void __launch_bounds__(128) tri_block_factor(TriGeom g, const R *__re
     for (int r = 0; r < TRI_PF; ++r) {
         const int i = len - 2 - r;
         hq[r] = (i >= 0) ? U[first + i] : cxz<R>();
-        cq[r] = (i >= 0) ? F[2 * (first + i)] : cxz<R>();
+        cq[r] = (i >= 0) ? F[3 * (first + i)] : cxz<R>();
     }
     for (int i0 = len - 2; i0 >= 0; i0 -= TRI_PF) {
 #pragma unroll
@@ -108,7 +114,7 @@ __global__ void __launch_bounds__(128) tri_block_factor(TriGeom g, const R *__re
                 const int ipf = i - TRI_PF;  // refill this slot for the next round
                 if (ipf >= 0) {
                     hq[r] = U[first + ipf];
-                    cq[r] = F[2 * (first + ipf)];
+                    cq[r] = F[3 * (first + ipf)];
                 }
                 un = csub_mul(h, cp, un);
                 wn = -(cp * wn);
