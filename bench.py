@@ -439,7 +439,21 @@ def run_dense(args):
                      "refine_sweeps": info.refine_iters_max, "resid_rel": info.resid_rel_max,
                      "growth": info.growth_max_seen,
                      "kernels_ms_total": {k: round(v[1], 3) for k, v in prof.items()}}
-    for name in ("mixed", "mixed_tc"):
+    # the same through the reduction of A to real tridiagonal form (binary64 reduction and
+    # reflector products; binary64 or binary32 + refinement tridiagonal solves)
+    for name, prec, kw in (("reduced", P.EXPM_FP64, {}),
+                           ("reduced_mixed", P.EXPM_MIXED_FP32, dict(tol=1e-12, max_refine=2))):
+        Y = torch.empty_like(V)
+        P.expm_apply_dense_reduced(plan, A, V, Y, prec=prec, **kw)
+        P.expm_profile_enable(plan, True)
+        ts = _time_calls(lambda: P.expm_apply_dense_reduced(plan, A, V, Y, prec=prec, want_info=False, **kw),
+                         max(1, args.steps), 0)
+        prof = P.expm_profile_read(plan)
+        P.expm_profile_enable(plan, False)
+        Ys[name] = Y.clone()
+        out[name] = {"s_per_eval": round(statistics.median(ts), 5), "evals_per_s": round(1 / statistics.median(ts), 4),
+                     "kernels_ms_total": {k: round(v[1], 3) for k, v in prof.items()}}
+    for name in ("mixed", "mixed_tc", "reduced", "reduced_mixed"):
         d = (Ys[name] - Ys["fp64"]).abs().pow(2).sum().sqrt() / Ys["fp64"].abs().pow(2).sum().sqrt()
         out[f"{name}_vs_fp64_rel"] = float(d)
     print(json.dumps(out), flush=True)

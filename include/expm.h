@@ -151,7 +151,7 @@ expm_status expm_plan_destroy(expm_plan plan);
  *                 doubles if e_is_complex == 0, else N-1 complex
  *   V             N x r right-hand sides, row-major, ld = r; real doubles if
  *                 v_is_complex == 0, else complex
- *   r             number of right-hand sides, 1 <= r <= 64
+ *   r             number of right-hand sides, 1 <= r <= 1024
  *   Y             N x r output, row-major; complex when V or e is complex, else real.
  *                 Must not overlap V, d or e.
  *   opts          precision EXPM_FP64, EXPM_MIXED_F32X2 or EXPM_MIXED_FP32; t, shift_c,
@@ -260,6 +260,30 @@ expm_status expm_apply_dense(expm_plan plan, int n, const void *A, int lda, int 
  */
 expm_status expm_apply_dense_full(expm_plan plan, int n, const void *A, int lda, int a_is_complex, void *Y, int ldy,
                                   const expm_opts *opts, expm_info *info);
+
+/*
+ * expm_apply_dense_reduced -- Y = e^c R_n(tA - cI) V for a dense Hermitian A through a
+ * unitary reduction to real symmetric tridiagonal form: A = Q T Q^H by Householder
+ * reflectors (each mapping the column below the diagonal to a real multiple of e_1, so
+ * T is real), then Y = Q [e^c R_n(tT - cI) (Q^H V)] (Remark 3.1: R_n commutes with the
+ * similarity) with the pole-batched tridiagonal path.  The reduction costs about
+ * (8/3) n^3 complex multiply-adds once, whatever the degree, against n/2 LUs for
+ * expm_apply_dense.  No counterpart in the paper's experiments (it is named there as a
+ * way to use tridiagonal solvers for dense Hermitian A).
+ *   n, A, lda, a_is_complex, V, ldv, k, v_is_complex, Y, ldy   as expm_apply_dense, with
+ *                 n <= 12000, 1 <= k <= 1024; A, V and Y must be device memory (A is not modified:
+ *                 the reduction works on a copy)
+ *   opts          t, shift_c, stream; prec selects the tridiagonal solves (EXPM_FP64,
+ *                 EXPM_MIXED_F32X2 or EXPM_MIXED_FP32 with tol / max_refine / flags as in
+ *                 expm_apply_tridiag); the reduction and the reflector products are
+ *                 binary64 in every case
+ *   info          as expm_apply_tridiag for the tridiagonal solves
+ * Asynchronous on opts->stream (except the refinement report of EXPM_MIXED_FP32 with
+ * info, as in expm_apply_tridiag).
+ */
+expm_status expm_apply_dense_reduced(expm_plan plan, int n, const void *A, int lda, int a_is_complex, const void *V,
+                                     int ldv, int k, int v_is_complex, void *Y, int ldy, const expm_opts *opts,
+                                     expm_info *info);
 
 /*
  * expm_apply_batched -- Y_i = e^c R_n(tA_i - cI) V_i for `count` independent dense

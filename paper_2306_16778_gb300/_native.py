@@ -66,6 +66,9 @@ def _load() -> ctypes.CDLL:
     L.expm_plan_create.restype = i
     L.expm_plan_destroy.argtypes = [vp]
     L.expm_plan_destroy.restype = i
+    L.expm_apply_dense_reduced.argtypes = [vp, i, vp, i, i, vp, i, i, i, vp, i, ctypes.POINTER(expm_opts),
+                                           ctypes.POINTER(expm_info)]
+    L.expm_apply_dense_reduced.restype = i
     L.expm_apply_dense_full.argtypes = [vp, i, vp, i, i, vp, i, ctypes.POINTER(expm_opts), ctypes.POINTER(expm_info)]
     L.expm_apply_dense_full.restype = i
     L.expm_apply_tridiag.argtypes = [vp, i64, vp, vp, i, vp, i, i, vp, ctypes.POINTER(expm_opts),
@@ -274,6 +277,25 @@ def expm_apply_dense_full(plan: Plan, A, Y, prec=EXPM_FP64, t=1.0, shift_c=0.0, 
                                    ctypes.byref(info))
     if st != 0 and not (not check and st in (3, 4)):
         _check(st, "expm_apply_dense_full")
+    return info
+
+
+def expm_apply_dense_reduced(plan: Plan, A, V, Y, prec=EXPM_FP64, t=1.0, shift_c=0.0, stream=None, tol=None,
+                             max_refine=None, flags=0, want_info=True, check=True):
+    """Y = e^c R_n(tA - cI) V through the reduction of A to real tridiagonal form (device
+    tensors; see include/expm.h).  ``prec`` selects the tridiagonal solves."""
+    n = int(A.shape[0])
+    k = int(V.shape[1]) if len(V.shape) == 2 else 1
+    if stream is None:
+        stream = _default_stream(A, V, Y)
+    o = make_opts(prec, t, shift_c, stream, tol, max_refine)
+    o.flags = int(flags)
+    info = expm_info() if want_info else None
+    st = lib.expm_apply_dense_reduced(plan.handle, n, _ptr(A), n, int(_is_complex(A)), _ptr(V), k, k,
+                                      int(_is_complex(V)), _ptr(Y), k, ctypes.byref(o),
+                                      ctypes.byref(info) if info is not None else None)
+    if st != 0 and not (not check and st == 4):
+        _check(st, "expm_apply_dense_reduced")
     return info
 
 

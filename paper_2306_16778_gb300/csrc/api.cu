@@ -214,7 +214,7 @@ expm_status expm_apply_tridiag(expm_plan p, int64_t N, const double *d, const vo
     expm_opts opts;
     if (opts_in) opts = *opts_in; else expm_opts_default(&opts);
     if (N < 1) return set_error(EXPM_EINVAL, "apply_tridiag: N must be >= 1");
-    if (r < 1 || r > 64) return set_error(EXPM_EINVAL, "apply_tridiag: r must be in 1..64");
+    if (r < 1 || r > 1024) return set_error(EXPM_EINVAL, "apply_tridiag: r must be in 1..1024");
     if (!d || !V || !Y || (N > 1 && !e)) return set_error(EXPM_EINVAL, "apply_tridiag: NULL data pointer");
     if (opts.prec != EXPM_FP64 && opts.prec != EXPM_MIXED_F32X2 && opts.prec != EXPM_MIXED_FP32)
         return set_error(EXPM_EINVAL, "apply_tridiag: precision must be EXPM_FP64, EXPM_MIXED_F32X2 or EXPM_MIXED_FP32");
