@@ -18,6 +18,8 @@ Closed forms used to pin the above (none goes through partial fractions):
   (Remark 3.1: R_n(P A P^-1) = P R_n(A) P^-1 and R_n(D) = diag(R_n(D_ii))).
 * ``laplacian_apply``: the same with the DST-I eigenbasis of the constant
   tridiagonal matrix tridiag(e0, d0, e0) (eigenvalues d0 + 2 e0 cos(j pi/(N+1))).
+* ``laplacian2d_apply``: the same for the separable 2D operator I (x) T_x + T_y (x) I
+  (the DST-I along both axes).
 * ``product_apply``: R_n(A) v = n! prod_k (A + theta_k I)^{-1} v, which
   follows from R_n(z) = 1/exp_n(-z) = n!/prod_k (z + theta_k) for even n.
 
@@ -153,6 +155,28 @@ def laplacian_apply(d0: float, e0: float, V, f) -> np.ndarray:
     fm = f(mu)
     W = (fm[:, None] if V.ndim == 2 else fm) * W
     return scipy.fft.dst(W, type=1, norm="ortho", axis=0)
+
+
+def laplacian2d_matrix(dx: int, dy: int, ax: float, bx: float, ay: float, by: float) -> np.ndarray:
+    """The separable operator A = I_y (x) T_x + T_y (x) I_x of the 2D finite-difference
+    Laplacian (Sec. 5), T_x = tridiag(ax, bx, ax) of size dx, T_y = tridiag(ay, by, ay) of
+    size dy, assembled densely (row index iy * dx + ix); small sizes only."""
+    Tx = np.diag(np.full(dx, bx)) + np.diag(np.full(dx - 1, ax), 1) + np.diag(np.full(dx - 1, ax), -1)
+    Ty = np.diag(np.full(dy, by)) + np.diag(np.full(dy - 1, ay), 1) + np.diag(np.full(dy - 1, ay), -1)
+    return np.kron(np.eye(dy), Tx) + np.kron(Ty, np.eye(dx))
+
+
+def laplacian2d_apply(dx: int, dy: int, ax: float, bx: float, ay: float, by: float, V, f) -> np.ndarray:
+    """f(A) V for the separable A of laplacian2d_matrix by its eigenbasis, the orthonormal
+    DST-I along both axes: eigenvalue (bx + 2 ax cos(i pi/(dx+1))) + (by + 2 ay cos(j pi/(dy+1)))."""
+    V = np.asarray(V)
+    r = V.shape[1] if V.ndim == 2 else 1
+    W = V.reshape(dy, dx, r)
+    W = scipy.fft.dst(scipy.fft.dst(W, type=1, norm="ortho", axis=0), type=1, norm="ortho", axis=1)
+    lam = laplacian_eigs(by, ay, dy)[:, None] + laplacian_eigs(bx, ax, dx)[None, :]
+    W = f(lam)[:, :, None] * W
+    W = scipy.fft.dst(scipy.fft.dst(W, type=1, norm="ortho", axis=0), type=1, norm="ortho", axis=1)
+    return W.reshape(V.shape)
 
 
 def product_apply(A, v, theta, n: int) -> np.ndarray:

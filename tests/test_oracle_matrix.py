@@ -195,6 +195,29 @@ def test_tridiag_general_matches_dense(complex_e):
     assert matrix.rel_err(Yt, ref) < 1e-12
 
 
+@pytest.mark.parametrize("dx,dy", [(1, 1), (5, 7), (12, 9)])
+def test_laplacian2d_closed_form(dx, dy):
+    """2D separable operator (Sec. 5): the DST-I closed form reproduces A V itself (f = id:
+    pins the eigenvalue order and both transforms) and equals the per-pole dense solves
+    on the assembled matrix for f = R_n."""
+    g = workloads.rng(113 + dx)
+    ax, bx, ay, by = 30.0, -70.0, 25.0, -55.0
+    A = matrix.laplacian2d_matrix(dx, dy, ax, bx, ay, by)
+    V = g.standard_normal((dx * dy, 3))
+    AV = matrix.laplacian2d_apply(dx, dy, ax, bx, ay, by, V, lambda m: m)
+    assert np.allclose(AV, A @ V, rtol=1e-12, atol=1e-12 * np.abs(A @ V).max())
+    n = 12
+    th, a = _coeffs(n)
+    Yd, im = matrix.apply_dense(A, V, th, a)
+    ref = matrix.laplacian2d_apply(dx, dy, ax, bx, ay, by, V, lambda m: scalar.R_n(m, n))
+    assert np.linalg.norm(Yd - ref) <= 1e-12 * np.linalg.norm(ref) + scalar.M2(n, 16, a) * np.linalg.norm(V)
+    # a transposed grid (dx <-> dy, with the coefficients) is the same operator up to the
+    # permutation of the unknowns
+    P = np.arange(dx * dy).reshape(dy, dx).T.reshape(-1)
+    ref_t = matrix.laplacian2d_apply(dy, dx, ay, by, ax, bx, V[P], lambda m: scalar.R_n(m, n))
+    assert np.allclose(ref_t, ref[P], rtol=1e-12, atol=1e-14)
+
+
 def test_threaded_solves_are_identical():
     """The thread pool changes nothing: the sum is always taken in pole order."""
     w = workloads.laplacian_1d(N=3000, nrhs=2, offset=112)
