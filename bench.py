@@ -93,7 +93,8 @@ def parse():
                     help="time only the binary64 path (profiling runs)")
     ap.add_argument("--mixed-only", action="store_true",
                     help="time only the binary32 + refinement path (profiling runs)")
-    ap.add_argument("--workload", default="laplacian", choices=["laplacian", "dense", "batched", "served"],
+    ap.add_argument("--workload", default="laplacian",
+                    choices=["laplacian", "dense", "batched", "served", "laplacian2d"],
                     help="laplacian: the headline line; the others print their own lines "
                          "(dense 4096 Hermitian x 256 RHS; 4096-instance uneven batch; served stream)")
     ap.add_argument("--dense-n", type=int, default=4096)
@@ -459,6 +460,33 @@ def run_dense(args):
     print(json.dumps(out), flush=True)
 
 
+def run_laplacian2d(args):
+    """2D Laplacian 100 (1,-2,1) along both axes on a 1024 x 1024 grid (N = 2^20), 8 RHS, degree 16."""
+    import torch
+    import paper_2306_16778_gb300 as P
+    dev = torch.device("cuda", 0)
+    d = 1024
+    g = np.random.default_rng(20230629 + 6)
+    V = torch.from_numpy(g.standard_normal((d * d, NRHS))).to(dev)
+    plan = P.Plan(degree=DEGREE)
+    out = {"workload": f"2D Laplacian 100 (1,-2,1) along x and y, {d} x {d} grid, {NRHS} RHS, degree {DEGREE}"}
+    Ys = {}
+    for name, prec, kw in (("fp64", P.EXPM_FP64, {}), ("mixed", P.EXPM_MIXED_FP32, MIXED_OPTS)):
+        Y = torch.empty_like(V)
+        P.expm_apply_laplacian2d(plan, d, d, 100.0, -200.0, 100.0, -200.0, V, Y, prec=prec, **kw)
+        P.expm_profile_enable(plan, True)
+        ts = _time_calls(lambda: P.expm_apply_laplacian2d(plan, d, d, 100.0, -200.0, 100.0, -200.0, V, Y, prec=prec,
+                                                          want_info=False, **kw), max(3, args.steps), 2)
+        prof = P.expm_profile_read(plan)
+        P.expm_profile_enable(plan, False)
+        Ys[name] = Y.clone()
+        med = statistics.median(ts)
+        out[name] = {"ms_per_eval": round(med * 1e3, 4), "evals_per_s": round(1 / med, 2),
+                     "kernels_ms": {k: round(v[1] / v[0], 4) for k, v in prof.items()}}
+    out["mixed_vs_fp64_rel"] = float((Ys["mixed"] - Ys["fp64"]).norm() / Ys["fp64"].norm())
+    print(json.dumps(out), flush=True)
+
+
 def run_batched(args):
     """Uneven batch: sizes log-uniform in [32, 768], one complex RHS, degree 12."""
     import torch
@@ -589,6 +617,8 @@ def main():
     if args.peaks:
         run_peaks()
         return
+    if args.workload == "laplacian2d":
+        return run_laplacian2d(args)
     if args.workload == "dense":
         run_dense(args)
         return

@@ -286,6 +286,25 @@ expm_status expm_apply_dense_reduced(expm_plan plan, int n, const void *A, int l
                                      expm_info *info);
 
 /*
+ * expm_apply_laplacian2d -- Y = e^c R_n(tA - cI) V for the separable operator of the 2D
+ * finite-difference Laplacian (the paper's second workload, Sec. 5):
+ *     A = I_y (x) T_x + T_y (x) I_x,  T_x = tridiag(ax, bx, ax) (dx points),
+ *                                     T_y = tridiag(ay, by, ay) (dy points),
+ * unknown (ix, iy) at row iy * dx + ix.  T_y is diagonalised by the orthonormal DST-I S,
+ * so A = (S (x) I)[(+)_j (T_x + mu_j I)](S (x) I) with mu_j = by + 2 ay cos((j+1) pi/(dy+1)),
+ * and (Remark 3.1) Y = (S (x) I) e^c R_n(tB - cI) (S (x) I) V with B block-diagonal
+ * tridiagonal: the pole-batched tridiagonal path on dx * dy rows between two binary64
+ * products with S along y.
+ *   V, Y          device memory, (dx dy) x r row-major, real or complex (v_is_complex);
+ *                 1 <= r <= 512, dx * dy <= 2^28
+ *   opts, info    as expm_apply_tridiag (its precisions select the tridiagonal solves)
+ * Asynchronous on opts->stream (except an EXPM_MIXED_FP32 report, as there).
+ */
+expm_status expm_apply_laplacian2d(expm_plan plan, int dx, int dy, double ax, double bx, double ay, double by,
+                                   const void *V, int r, int v_is_complex, void *Y, const expm_opts *opts,
+                                   expm_info *info);
+
+/*
  * expm_apply_batched -- Y_i = e^c R_n(tA_i - cI) V_i for `count` independent dense
  * Hermitian problems of uneven sizes (eq. expAx per instance, Sec. 3).
  *   count            number of instances (0 is a no-op)

@@ -25,6 +25,7 @@ from ._native import (  # noqa: F401
     expm_apply_dense,
     expm_apply_dense_full,
     expm_apply_dense_reduced,
+    expm_apply_laplacian2d,
     expm_apply_tridiag,
     expm_apply_tridiag_noalloc,
     expm_profile_enable,

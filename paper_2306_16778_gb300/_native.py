@@ -66,6 +66,10 @@ def _load() -> ctypes.CDLL:
     L.expm_plan_create.restype = i
     L.expm_plan_destroy.argtypes = [vp]
     L.expm_plan_destroy.restype = i
+    L.expm_apply_laplacian2d.argtypes = [vp, i, i, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                         ctypes.c_double, vp, i, i, vp, ctypes.POINTER(expm_opts),
+                                         ctypes.POINTER(expm_info)]
+    L.expm_apply_laplacian2d.restype = i
     L.expm_apply_dense_reduced.argtypes = [vp, i, vp, i, i, vp, i, i, i, vp, i, ctypes.POINTER(expm_opts),
                                            ctypes.POINTER(expm_info)]
     L.expm_apply_dense_reduced.restype = i
@@ -296,6 +300,25 @@ def expm_apply_dense_reduced(plan: Plan, A, V, Y, prec=EXPM_FP64, t=1.0, shift_c
                                       ctypes.byref(info) if info is not None else None)
     if st != 0 and not (not check and st == 4):
         _check(st, "expm_apply_dense_reduced")
+    return info
+
+
+def expm_apply_laplacian2d(plan: Plan, dx: int, dy: int, ax: float, bx: float, ay: float, by: float, V, Y,
+                           prec=EXPM_FP64, t=1.0, shift_c=0.0, stream=None, tol=None, max_refine=None, flags=0,
+                           want_info=True, check=True):
+    """Y = e^c R_n(tA - cI) V for A = I (x) tridiag(ax, bx, ax) + tridiag(ay, by, ay) (x) I on a
+    dx x dy grid (row iy * dx + ix); V, Y device tensors of dx*dy rows (see include/expm.h)."""
+    r = int(V.shape[1]) if len(V.shape) == 2 else 1
+    if stream is None:
+        stream = _default_stream(V, Y)
+    o = make_opts(prec, t, shift_c, stream, tol, max_refine)
+    o.flags = int(flags)
+    info = expm_info() if want_info else None
+    st = lib.expm_apply_laplacian2d(plan.handle, int(dx), int(dy), float(ax), float(bx), float(ay), float(by), _ptr(V),
+                                    r, int(_is_complex(V)), _ptr(Y), ctypes.byref(o),
+                                    ctypes.byref(info) if info is not None else None)
+    if st != 0 and not (not check and st == 4):
+        _check(st, "expm_apply_laplacian2d")
     return info
 
 
