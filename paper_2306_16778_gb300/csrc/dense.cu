@@ -559,14 +559,21 @@ cudaError_t dense_solve(const DenseGeom &g, const DenseIO &io, const DenseSystem
                     }));
                 } else EXPM_TRY(prof.timed("resid_gemm<f32x2>", st, [&] {
                     dim3 gg((g.kc + 63) / 64, (g.n + 63) / 64, nsz);
-                    if (g.complex_a)
-                        resid_gemm_f32x2<cx<double>><<<gg, 256, 0, st>>>(g.n, g.kc, g.n, g.t,
-                                                                          (const cx<double> *)io.A, (int)io.lda,
-                                                                          io.astride, X, g.kc, nk, R, g.kc, nk, g.nsys);
-                    else
-                        resid_gemm_f32x2<double><<<gg, 256, 0, st>>>(g.n, g.kc, g.n, g.t, io.A, (int)io.lda,
-                                                                      io.astride, X, g.kc, nk, R, g.kc, nk, g.nsys);
-                    return cudaGetLastError();
+                    cudaError_t e;
+                    if (g.complex_a) {
+                        e = set_smem(resid_gemm_f32x2<cx<double>>, RESID_GEMM_SMEM);
+                        if (e == cudaSuccess)
+                            resid_gemm_f32x2<cx<double>><<<gg, 256, RESID_GEMM_SMEM, st>>>(
+                                g.n, g.kc, g.n, g.t, (const cx<double> *)io.A, (int)io.lda, io.astride, X, g.kc, nk, R,
+                                g.kc, nk, g.nsys);
+                    } else {
+                        e = set_smem(resid_gemm_f32x2<double>, RESID_GEMM_SMEM);
+                        if (e == cudaSuccess)
+                            resid_gemm_f32x2<double><<<gg, 256, RESID_GEMM_SMEM, st>>>(g.n, g.kc, g.n, g.t, io.A,
+                                                                                       (int)io.lda, io.astride, X, g.kc,
+                                                                                       nk, R, g.kc, nk, g.nsys);
+                    }
+                    return e != cudaSuccess ? e : cudaGetLastError();
                 }));
             }
             EXPM_TRY(cudaMemsetAsync(rn2, 0, sizeof(double) * nsz, st));

@@ -500,7 +500,7 @@ __global__ void __launch_bounds__(256) resid_gemv_multi(int n, int kc, int nsys,
 // ------------------------------------------------------------------ resid_gemm_f32x2
 // R[z] = R[z] - t * A[z / adiv] * X[z]  (A: m x K, X: K x n, all binary64 in memory)
 // with binary64-level accuracy on the FP32 pipe.  Inside each K-block of 16 the
-// products are accumulated in float-float (dd_fma); the block sums are added in
+// products are accumulated as float pairs (pair_mac); the block sums are added in
 // binary64.  The rounding error of a block is ~16 * 2^-47 of its sum of |products|,
 // and the blocks' errors are independent, so the total stays within a few 1e-15 of
 // sum |a_il x_lj| -- far below what the refinement needs.
@@ -508,26 +508,40 @@ template <class AE> EXPM_D cx<f32x2> split_cx(AE v);
 template <> EXPM_D cx<f32x2> split_cx<double>(double v) { return {split_bits(v), {0.f, 0.f}}; }
 template <> EXPM_D cx<f32x2> split_cx<cx<double>>(cx<double> v) { return {split_bits(v.re), split_bits(v.im)}; }
 
+// a * b accumulated into the unnormalised pair (hi, lo): the product of the high parts
+// split exactly by an FMA, the cross terms added to its error, the sum's rounding error
+// from one TwoSum; lo collects all errors and is folded in once per K-block.
+EXPM_D void pair_mac(float &hi, float &lo, f32x2 a, f32x2 b) {
+    const float p = __fmul_rn(a.hi, b.hi);
+    float e = __fmaf_rn(a.hi, b.hi, -p);
+    e = __fmaf_rn(a.hi, b.lo, e);
+    e = __fmaf_rn(a.lo, b.hi, e);
+    const f32x2 s = two_sum(hi, p);
+    hi = s.hi;
+    lo = __fadd_rn(lo, __fadd_rn(s.lo, e));
+}
+
+constexpr size_t RESID_GEMM_SMEM = 16 * 256 * sizeof(cx<double>);  // dynamic: the binary64 block sums
+
 template <class AE>
-__global__ void __launch_bounds__(256) resid_gemm_f32x2(int m, int n, int K, double t, const AE *__restrict__ A,
-                                                        int lda, int64_t sA, const cx<double> *__restrict__ X, int ldx,
-                                                        int64_t sX, cx<double> *__restrict__ Rm, int ldr, int64_t sR,
-                                                        int adiv) {
+__global__ void __launch_bounds__(256, 2) resid_gemm_f32x2(int m, int n, int K, double t, const AE *__restrict__ A,
+                                                           int lda, int64_t sA, const cx<double> *__restrict__ X,
+                                                           int ldx, int64_t sX, cx<double> *__restrict__ Rm, int ldr,
+                                                           int64_t sR, int adiv) {
     constexpr int BM = 64, BN = 64, BK = 16;
     __shared__ cx<f32x2> As[BK][BM + 1];
     __shared__ cx<f32x2> Bs[BK][BN + 1];
+    // the binary64 block sums live in shared memory ([output][thread]: conflict-free), so
+    // the registers hold only the float-pair accumulators of the current K-block
+    extern __shared__ cx<double> accS[];  // 16 x 256
     const AE *a = A + (int64_t)(blockIdx.z / adiv) * sA;
     const cx<double> *x = X + (int64_t)blockIdx.z * sX;
     cx<double> *r = Rm + (int64_t)blockIdx.z * sR;
     const int i0 = blockIdx.y * BM, j0 = blockIdx.x * BN;
     const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
     const f32x2 z2 = {0.f, 0.f};
-    cx<double> acc[4][4];
-    cx<f32x2> blk[4][4];
 #pragma unroll
-    for (int rr = 0; rr < 4; ++rr)
-#pragma unroll
-        for (int q = 0; q < 4; ++q) acc[rr][q] = {0.0, 0.0};
+    for (int o = 0; o < 16; ++o) accS[o * 256 + threadIdx.x] = {0.0, 0.0};
     for (int l0 = 0; l0 < K; l0 += BK) {
         for (int idx = threadIdx.x; idx < BM * BK; idx += 256) {
             const int ii = idx / BK, ll = idx % BK;
@@ -540,11 +554,12 @@ __global__ void __launch_bounds__(256) resid_gemm_f32x2(int m, int n, int K, dou
             Bs[ll][jj] = (gl < K && gj < n) ? split_cx<cx<double>>(x[(int64_t)gl * ldx + gj]) : cx<f32x2>{z2, z2};
         }
         __syncthreads();
+        float hr[4][4], lr[4][4], hi_[4][4], li[4][4];  // (hi, lo) of the real and imaginary parts
 #pragma unroll
         for (int rr = 0; rr < 4; ++rr)
 #pragma unroll
-            for (int q = 0; q < 4; ++q) blk[rr][q] = {z2, z2};
-#pragma unroll 2
+            for (int q = 0; q < 4; ++q) hr[rr][q] = lr[rr][q] = hi_[rr][q] = li[rr][q] = 0.f;
+#pragma unroll 1
         for (int l = 0; l < BK; ++l) {
             cx<f32x2> av[4], bv[4];
 #pragma unroll
@@ -555,19 +570,19 @@ __global__ void __launch_bounds__(256) resid_gemm_f32x2(int m, int n, int K, dou
             for (int rr = 0; rr < 4; ++rr)
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
-                    cx<f32x2> &c = blk[rr][q];
-                    c.re = dd_fma(av[rr].re, bv[q].re, c.re);
-                    c.re = dd_fma(-av[rr].im, bv[q].im, c.re);
-                    c.im = dd_fma(av[rr].re, bv[q].im, c.im);
-                    c.im = dd_fma(av[rr].im, bv[q].re, c.im);
+                    pair_mac(hr[rr][q], lr[rr][q], av[rr].re, bv[q].re);
+                    pair_mac(hr[rr][q], lr[rr][q], -av[rr].im, bv[q].im);
+                    pair_mac(hi_[rr][q], li[rr][q], av[rr].re, bv[q].im);
+                    pair_mac(hi_[rr][q], li[rr][q], av[rr].im, bv[q].re);
                 }
         }
 #pragma unroll
         for (int rr = 0; rr < 4; ++rr)
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
-                acc[rr][q].re += widen_bits(blk[rr][q].re.hi) + widen_bits(blk[rr][q].re.lo);
-                acc[rr][q].im += widen_bits(blk[rr][q].im.hi) + widen_bits(blk[rr][q].im.lo);
+                cx<double> &acc = accS[(rr * 4 + q) * 256 + threadIdx.x];
+                acc.re += widen_bits(hr[rr][q]) + widen_bits(lr[rr][q]);
+                acc.im += widen_bits(hi_[rr][q]) + widen_bits(li[rr][q]);
             }
         __syncthreads();
     }
@@ -577,9 +592,10 @@ __global__ void __launch_bounds__(256) resid_gemm_f32x2(int m, int n, int K, dou
         for (int q = 0; q < 4; ++q) {
             const int gi = i0 + ty + 16 * rr, gj = j0 + tx + 16 * q;
             if (gi < m && gj < n) {
+                const cx<double> acc = accS[(rr * 4 + q) * 256 + threadIdx.x];
                 cx<double> *rp = r + (int64_t)gi * ldr + gj;
-                rp->re -= t * acc[rr][q].re;
-                rp->im -= t * acc[rr][q].im;
+                rp->re -= t * acc.re;
+                rp->im -= t * acc.im;
             }
         }
 }
