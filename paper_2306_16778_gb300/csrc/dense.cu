@@ -24,6 +24,7 @@
 
 #include "arith.cuh"
 #include "dense.cuh"
+#include "oz_gemm.cuh"
 #include "dense_kernels.cuh"
 #include "plan.cuh"
 #include "tc_gemm.cuh"
@@ -386,9 +387,16 @@ static cudaError_t lu_solve(int n, int kc, int batch, const cx<T> *F, int64_t fs
 // the poles and can be kept for later right-hand sides.
 struct DenseLayout {
     size_t amax, umax, F, tcA, tcB, tcflag, factor_total;  // factor part
-    size_t rn2, xn2, an2, ctl, X, R, D, solve_total;  // solve part (offsets from its own base)
+    size_t rn2, xn2, an2, ctl, X, R, D, oz, solve_total;  // solve part (offsets from its own base)
 };
 static inline size_t align_up(size_t x) { return (x + 255) & ~size_t(255); }
+
+// The refinement residual of a single problem with more than 8 right-hand-side columns
+// runs on the tensor cores (binary64-accurate slice products, oz_gemm.cu); batches of
+// instances keep the float-pair GEMM.
+static bool dense_uses_oz(const DenseGeom &g) {
+    return g.mixed && g.kc > 8 && g.ninst == 1 && oz_resid_supported(g.n, g.kc, g.nsys);
+}
 
 static DenseLayout dense_layout(const DenseGeom &g) {
     DenseLayout L{};
@@ -418,6 +426,8 @@ static DenseLayout dense_layout(const DenseGeom &g) {
         L.D = off;
         off += align_up(nsz * nk * sizeof(cx<float>));
     }
+    L.oz = off;
+    if (dense_uses_oz(g)) off += align_up(oz_resid_bytes(g.n, g.kc, g.nsys, g.complex_a));
     L.solve_total = off;
     return L;
 }
@@ -490,7 +500,7 @@ cudaError_t dense_growth(const DenseGeom &g, const void *fwork, cudaStream_t st,
     EXPM_TRY(cudaMemcpyAsync(hm.data() + npz, p + L.umax, sizeof(unsigned) * npz, cudaMemcpyDeviceToHost, st));
     if (g.mixed && g.tc) EXPM_TRY(cudaMemcpyAsync(&tcflag, p + L.tcflag, sizeof(int), cudaMemcpyDeviceToHost, st));
     EXPM_TRY(cudaStreamSynchronize(st));
-    res->tc_timeout = tcflag;
+    res->tc_timeout = res->tc_timeout || tcflag;  // keeps a time-out of the solve's residual kernel
     res->growth_max = 0.0;
     res->inst_growth.assign(g.ninst, 0.0);
     for (int z = 0; z < npz; ++z) {
@@ -529,6 +539,9 @@ cudaError_t dense_solve(const DenseGeom &g, const DenseIO &io, const DenseSystem
     } else {
         cx<double> *R = (cx<double> *)(p + L.R);
         cx<float> *D = (cx<float> *)(p + L.D);
+        const bool use_oz = dense_uses_oz(g);
+        void *oz_ws = p + L.oz;
+        bool oz_a_ready = false;  // A's slices are formed at the first residual product
         EXPM_TRY(cudaMemsetAsync(X, 0, (size_t)nsz * nk * sizeof(cx<double>), st));
         std::vector<double> h(2 * (size_t)nsz), an(g.ninst);
         // ||tA||_F of every instance for the relative residual of the stopping test
@@ -545,7 +558,22 @@ cudaError_t dense_solve(const DenseGeom &g, const DenseIO &io, const DenseSystem
             residual_diag<<<dim3(gx, 1, nsz), 256, 0, st>>>(g.n, g.kc, io, g.nsys, X, R, nk, sys, nullptr);
             EXPM_TRY(cudaGetLastError());
             if (it > 0) {
-                if (g.kc <= 8) {
+                if (use_oz) {
+                    if (!oz_a_ready) {
+                        EXPM_TRY(prof.timed("oz_split_a", st, [&] {
+                            return oz_split_a(g.n, io.A, io.lda, g.complex_a, oz_ws, st);
+                        }));
+                        oz_a_ready = true;
+                    }
+                    int to = 0;
+                    EXPM_TRY(prof.timed("resid_oz", st, [&] {
+                        return oz_resid(g.n, g.kc, g.nsys, g.complex_a, g.t, X, nk, R, oz_ws, st, &to);
+                    }));
+                    if (to) {
+                        res->tc_timeout = 1;
+                        return cudaSuccess;
+                    }
+                } else if (g.kc <= 8) {
                     EXPM_TRY(prof.timed("resid_gemv<f64>", st, [&] {
                         dim3 gg((g.n + 7) / 8, (g.nsys * g.kc + 15) / 16, g.ninst);
                         if (g.complex_a)

@@ -132,6 +132,8 @@ extern "C" expm_status expm_apply_dense_full(expm_plan p, int n, const void *A, 
         iob.Y = dY + (size_t)c0 * ea;
         err = dense_solve(gb, iob, sys, fwork, swork, st, p->prof, &res);
         if (err != cudaSuccess) return cuda_error(err, "apply_dense_full: solve");
+        if (res.tc_timeout)
+            return set_error(EXPM_ETIMEOUT, "apply_dense_full: a bounded wait in the tensor-core kernel gave up");
         iters = std::max(iters, res.iters);
         resid = std::max(resid, res.resid_rel_max);
     }

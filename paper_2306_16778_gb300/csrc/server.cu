@@ -249,7 +249,8 @@ void run_request(expm_server_s *sv, Worker &w, Request &r, FactorEntry &fe, bool
             r.info.refine_iters_max = res.iters;
             r.info.resid_rel_max = res.resid_rel_max;
             r.info.growth_max_seen = fe.growth.growth_max;
-            if (fe.growth.growth_max > r.opts.growth_max) st = EXPM_EGROWTH;
+            if (fe.growth.tc_timeout || res.tc_timeout) st = EXPM_ETIMEOUT;
+            else if (fe.growth.growth_max > r.opts.growth_max) st = EXPM_EGROWTH;
             else if (g.mixed && !(res.resid_rel_max <= r.opts.tol)) st = EXPM_ENOCONV;
         }
     }

@@ -25,6 +25,7 @@
 
 #include "plan.cuh"
 #include "tc_gemm.cuh"
+#include "tcgen05_util.cuh"
 
 namespace expm {
 
@@ -35,57 +36,13 @@ constexpr int TC_STAGES = 4;
 constexpr int TC_TILE_BYTES = TC_BM * TC_BK * 4;      // 16 KB for A, same for B (BN == BM)
 constexpr int TC_CTILE_BYTES = TC_BM * TC_BN * 4;     // the C tile, prefetched by TMA
 constexpr int TC_SMEM = TC_STAGES * 2 * TC_TILE_BYTES + TC_CTILE_BYTES + 1024 + 256;
-constexpr long long TC_SPIN_LIMIT = 1ll << 26;        // bounded mbarrier waits
+using tcu::mbar_expect_tx;
+using tcu::mbar_init;
+using tcu::mbar_wait;
+using tcu::smem_u32;
+using tcu::tma_load_2d;
 
-__device__ __forceinline__ uint32_t smem_u32(const void *p) {
-    return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
-                 : "memory");
-}
-
-// true once the phase with the given parity has completed; false after the spin limit
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
-    const uint32_t addr = smem_u32(bar);
-    for (long long it = 0; it < TC_SPIN_LIMIT; ++it) {
-        uint32_t done;
-        asm volatile(
-            "{\n\t.reg .pred p;\n\t"
-            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-            "selp.u32 %0, 1, 0, p;\n\t}"
-            : "=r"(done)
-            : "r"(addr), "r"(parity)
-            : "memory");
-        if (done) return true;
-    }
-    return false;
-}
-
-__device__ __forceinline__ void tma_load_2d(const CUtensorMap *map, uint64_t *bar, void *dst, int x, int y) {
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::"r"(
-            smem_u32(dst)),
-        "l"((uint64_t)map), "r"(smem_u32(bar)), "r"(x), "r"(y)
-        : "memory");
-}
-
-// Shared-memory matrix descriptor: K-major tile, 128-byte rows, 128-byte swizzle,
-// 8-row groups 1024 bytes apart.
-__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t saddr) {
-    uint64_t d = 0;
-    d |= (uint64_t)((saddr >> 4) & 0x3FFF);         // start address
-    d |= (uint64_t)(1) << 16;                        // leading byte offset (unused for swizzled K-major)
-    d |= (uint64_t)((1024 >> 4) & 0x3FFF) << 32;     // stride byte offset: 8 rows x 128 B
-    d |= (uint64_t)1 << 46;                          // descriptor version
-    d |= (uint64_t)2 << 61;                          // swizzle: 128 B
-    return d;
-}
+__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t saddr) { return tcu::smem_desc(saddr, 128); }
 
 // Instruction descriptor of kind::tf32: D fp32, A and B TF32, both K-major, M x N.
 __host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
@@ -254,23 +211,8 @@ __global__ void __launch_bounds__(128, 1)
     }
 }
 
-// cuTensorMapEncodeTiled through the runtime's driver entry point (no link to libcuda)
-using EncodeFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
-                              const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
-                              CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-
-EncodeFn encode_fn() {
-    static std::once_flag once;
-    static EncodeFn fn = nullptr;
-    std::call_once(once, [] {
-        void *p = nullptr;
-        cudaDriverEntryPointQueryResult q;
-        if (cudaGetDriverEntryPoint("cuTensorMapEncodeTiled", &p, cudaEnableDefault, &q) == cudaSuccess &&
-            q == cudaDriverEntryPointSuccess)
-            fn = (EncodeFn)p;
-    });
-    return fn;
-}
+using tcu::EncodeFn;
+using tcu::encode_fn;
 
 // K-major operand tiles (TC_BK x TC_BM, 128-byte swizzle) or the plain C tile
 // (TC_BN x TC_BM, no swizzle); out-of-range elements read as zero.

@@ -162,3 +162,79 @@ def test_tensor_core_gemm_against_torch():
         ref = C0.double() - tf(A) @ tf(B).T
         err = (C.double() - ref).abs().max().item() / ref.abs().max().item()
         assert err < 1e-5, (M, N, K, err)
+
+
+def _oz_hook():
+    import ctypes
+    f = P.lib.expm_internal_oz_resid
+    f.restype = ctypes.c_int
+    f.argtypes = [ctypes.c_int] * 4 + [ctypes.c_double, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
+                                       ctypes.c_void_p]
+    return f
+
+
+def _oz_run(A, X, R0, t, complex_a):
+    """R_s - t A X_s on the GPU through the slice-product tensor-core kernel."""
+    n, kc, nsys = A.shape[0], X.shape[2], X.shape[0]
+    dA = torch.from_numpy(np.ascontiguousarray(A)).to(DEV)
+    dX = torch.from_numpy(np.ascontiguousarray(X)).to(DEV)
+    dR = torch.from_numpy(np.ascontiguousarray(R0)).to(DEV)
+    assert _oz_hook()(n, kc, nsys, int(complex_a), t, dA.data_ptr(), n, dX.data_ptr(), dR.data_ptr()) == 0
+    torch.cuda.synchronize()
+    return dR.cpu().numpy()
+
+
+def _cgauss(g, shape):
+    return g.standard_normal(shape) + 1j * g.standard_normal(shape)
+
+
+@pytest.mark.parametrize("n,kc,nsys,complex_a", [(1, 1, 1, True), (100, 9, 2, True), (130, 70, 1, True),
+                                                 (257, 33, 3, True), (300, 16, 3, False), (1030, 16, 8, True),
+                                                 (200, 12, 5, False)])
+def test_tensor_core_residual_product(n, kc, nsys, complex_a):
+    """The binary64-accurate residual product R_s -= t A X_s on the bf16 tensor cores
+    (six-slice splitting, 21 slice products): ragged tiles in M, N and K, real and
+    complex A, against the float64 product on the host (whose own error, ~K 2^-53, is
+    far below the bound)."""
+    g = np.random.default_rng(4000 + n + kc)
+    A = _cgauss(g, (n, n)) if complex_a else g.standard_normal((n, n))
+    X = _cgauss(g, (nsys, n, kc))
+    R0 = _cgauss(g, (nsys, n, kc))
+    t = -0.75
+    R = _oz_run(A, X, R0, t, complex_a)
+    ref = R0 - t * np.einsum("il,slc->sic", A, X)
+    prod = np.linalg.norm(t * np.einsum("il,slc->sic", A, X))
+    assert np.linalg.norm(R - ref) <= 1e-13 * prod, np.linalg.norm(R - ref) / prod
+
+
+def test_tensor_core_residual_scaling_and_special_values():
+    """Per-row and per-column power-of-two scales: rows of A and columns of X spread
+    over 2^-60 .. 2^60 keep the same relative accuracy; a zero row and a zero column
+    leave R unchanged; a NaN in A poisons its row only, a NaN in X its column only."""
+    g = np.random.default_rng(4100)
+    n, kc, nsys = 260, 20, 2
+    A = _cgauss(g, (n, n)) * np.exp2(g.integers(-60, 61, size=(n, 1)))
+    X = _cgauss(g, (nsys, n, kc)) * np.exp2(g.integers(-60, 61, size=(nsys, 1, kc)))
+    A[7, :] = 0.0
+    X[1, :, 3] = 0.0
+    R0 = _cgauss(g, (nsys, n, kc))
+    R = _oz_run(A, X, R0, 1.0, True)
+    ref = R0 - np.einsum("il,slc->sic", A, X)
+    # error of each entry against max|A_i.| max|X_.j| sqrt(K) (scale-free), plus the final
+    # rounding of R0 - t A X (one ulp of R, which decides where |A X| << |R0|)
+    scale = np.abs(A).max(axis=1)[None, :, None] * np.abs(X).max(axis=1)[:, None, :] * np.sqrt(2 * n)
+    err = np.abs(R - ref)
+    assert (err <= 1e-13 * scale + 2.0 ** -52 * np.abs(ref)).all(), (err / np.where(scale > 0, scale, 1)).max()
+    np.testing.assert_array_equal(R[:, 7, :], R0[:, 7, :])
+    np.testing.assert_array_equal(R[1, :, 3], R0[1, :, 3])
+    A2 = _cgauss(g, (n, n))
+    A2[11, 5] = np.nan
+    X2 = _cgauss(g, (nsys, n, kc))
+    X2[0, 9, 4] = complex(np.nan, 0.0)
+    R2 = _oz_run(A2, X2, R0, 1.0, True)
+    bad = np.zeros(R2.shape, dtype=bool)
+    bad[:, 11, :] = True
+    bad[0, :, 4] = True
+    assert np.isnan(R2[bad]).all()
+    ref2 = R0 - np.einsum("il,slc->sic", np.nan_to_num(A2), np.nan_to_num(X2))
+    assert np.abs(R2[~bad] - ref2[~bad]).max() <= 1e-12 * np.abs(ref2[~bad]).max()
