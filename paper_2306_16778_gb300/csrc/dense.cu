@@ -566,9 +566,13 @@ cudaError_t dense_solve(const DenseGeom &g, const DenseIO &io, const DenseSystem
                         oz_a_ready = true;
                     }
                     int to = 0;
-                    EXPM_TRY(prof.timed("resid_oz", st, [&] {
-                        return oz_resid(g.n, g.kc, g.nsys, g.complex_a, g.t, X, nk, R, oz_ws, st, &to);
+                    EXPM_TRY(prof.timed("oz_split_x", st, [&] {
+                        return oz_split_x(g.n, g.kc, g.nsys, g.complex_a, X, nk, oz_ws, st);
                     }));
+                    EXPM_TRY(prof.timed("oz_gemm", st, [&] {
+                        return oz_product(g.n, g.kc, g.nsys, g.complex_a, g.t, nk, R, oz_ws, st, nullptr);
+                    }));
+                    EXPM_TRY(oz_read_timeout(g.n, g.kc, g.nsys, g.complex_a, oz_ws, st, &to));
                     if (to) {
                         res->tc_timeout = 1;
                         return cudaSuccess;

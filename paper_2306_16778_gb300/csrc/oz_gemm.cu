@@ -489,19 +489,27 @@ cudaError_t oz_split_a(int n, const double *A, int64_t lda, int complex_a, void 
     return cudaGetLastError();
 }
 
-cudaError_t oz_resid(int n, int kc, int nsys, int complex_a, double t, const cx<double> *X, int64_t nk, cx<double> *R,
-                     void *ws, cudaStream_t st, int *timeout) {
+cudaError_t oz_split_x(int n, int kc, int nsys, int complex_a, const cx<double> *X, int64_t nk, void *ws,
+                       cudaStream_t st) {
     // the A part of the layout (slices, row scales) does not depend on kc or nsys
     const OzLayout L = oz_layout(n, kc, nsys, complex_a);
     unsigned char *b = (unsigned char *)ws;
-    int *F = (int *)(b + L.F), *flag = (int *)(b + L.flag);
+    int *F = (int *)(b + L.F);
     cudaError_t e = cudaMemsetAsync(F, 0, sizeof(int) * (size_t)nsys * kc, st);
     if (e != cudaSuccess) return e;
     oz_col_exp<<<dim3((kc + 127) / 128, (n + 63) / 64, nsys), 128, 0, st>>>(n, kc, X, nk, F);
     const int64_t work = (int64_t)nsys * kc * n;
     const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>((work + 255) / 256, 152 * 16));
     oz_split_cols<<<grid, 256, 0, st>>>(n, kc, nsys, complex_a, L.K2p, L.N2, X, nk, F, (uint16_t *)(b + L.Bs));
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    return cudaGetLastError();
+}
+
+cudaError_t oz_product(int n, int kc, int nsys, int complex_a, double t, int64_t nk, cx<double> *R, void *ws,
+                       cudaStream_t st, int *timeout) {
+    const OzLayout L = oz_layout(n, kc, nsys, complex_a);
+    unsigned char *b = (unsigned char *)ws;
+    int *F = (int *)(b + L.F), *flag = (int *)(b + L.flag);
+    cudaError_t e;
     CUtensorMap ma, mb;
     if (!make_slice_map(&ma, (const uint16_t *)(b + L.As), n, L.K2, L.K2p, OZ_BM) ||
         !make_slice_map(&mb, (const uint16_t *)(b + L.Bs), L.N2, L.K2, L.K2p, OZ_BN))
@@ -520,6 +528,12 @@ cudaError_t oz_resid(int n, int kc, int nsys, int complex_a, double t, const cx<
     return e;
 }
 
+cudaError_t oz_read_timeout(int n, int kc, int nsys, int complex_a, void *ws, cudaStream_t st, int *timeout) {
+    const OzLayout L = oz_layout(n, kc, nsys, complex_a);
+    cudaError_t e = cudaMemcpyAsync(timeout, (unsigned char *)ws + L.flag, sizeof(int), cudaMemcpyDeviceToHost, st);
+    return e == cudaSuccess ? cudaStreamSynchronize(st) : e;
+}
+
 }  // namespace expm
 
 // Test hook (not part of the documented interface): R_s -= t A X_s for s < nsys on
@@ -534,8 +548,8 @@ extern "C" int expm_internal_oz_resid(int n, int kc, int nsys, int complex_a, do
     if (cudaMalloc(&ws, oz_resid_bytes(n, kc, nsys, complex_a)) != cudaSuccess) return 1;
     int to = 0;
     cudaError_t e = oz_split_a(n, A, lda, complex_a, ws, 0);
-    if (e == cudaSuccess)
-        e = oz_resid(n, kc, nsys, complex_a, t, (const cx<double> *)X, (int64_t)n * kc, (cx<double> *)R, ws, 0, &to);
+    if (e == cudaSuccess) e = oz_split_x(n, kc, nsys, complex_a, (const cx<double> *)X, (int64_t)n * kc, ws, 0);
+    if (e == cudaSuccess) e = oz_product(n, kc, nsys, complex_a, t, (int64_t)n * kc, (cx<double> *)R, ws, 0, &to);
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     cudaFree(ws);
     if (e != cudaSuccess) return 1;

@@ -13,10 +13,16 @@ size_t oz_resid_bytes(int n, int kc, int nsys, int complex_a);
 bool oz_resid_supported(int n, int kc, int nsys);
 // slices of A (n x n, row stride lda in elements, real or interleaved complex) into ws
 cudaError_t oz_split_a(int n, const double *A, int64_t lda, int complex_a, void *ws, cudaStream_t st);
-// R_s -= t A X_s, s < nsys (X_s, R_s: n x kc complex, system stride nk), with A's slices
-// already in ws.  When `timeout` is non-null the stream is synchronised and *timeout set
-// to 1 if a bounded wait in the kernel gave up.
-cudaError_t oz_resid(int n, int kc, int nsys, int complex_a, double t, const cx<double> *X, int64_t nk, cx<double> *R,
-                     void *ws, cudaStream_t st, int *timeout);
+// slices of X_s, s < nsys (n x kc complex, system stride nk) into ws
+cudaError_t oz_split_x(int n, int kc, int nsys, int complex_a, const cx<double> *X, int64_t nk, void *ws,
+                       cudaStream_t st);
+// R_s -= t A X_s (R_s: n x kc complex, system stride nk) from the slices in ws.  When
+// `timeout` is non-null the stream is synchronised and *timeout set to 1 if a bounded
+// wait in the kernel gave up.
+cudaError_t oz_product(int n, int kc, int nsys, int complex_a, double t, int64_t nk, cx<double> *R, void *ws,
+                       cudaStream_t st, int *timeout);
+
+// the product's time-out flag (1 if a bounded wait gave up); synchronises st
+cudaError_t oz_read_timeout(int n, int kc, int nsys, int complex_a, void *ws, cudaStream_t st, int *timeout);
 
 }  // namespace expm
