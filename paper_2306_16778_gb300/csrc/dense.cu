@@ -340,44 +340,57 @@ static cudaError_t lu_solve(int n, int kc, int batch, const cx<T> *F, int64_t fs
     EXPM_TRY(set_smem(trsm_left<T, false, false, false>, sm2));
     EXPM_TRY(set_smem(trsm_left<T, true, false, true>, sm2));
     EXPM_TRY(set_smem(trsm_left<T, false, true, true>, sm2));
-    return prof.timed(sizeof(T) == 8 ? "lu_solve<f64>" : "lu_solve<f32>", st, [&]() -> cudaError_t {
-        // forward sweep
-        for (int p = 0; p < n; p += DN_NB) {
-            const int nb = std::min(DN_NB, n - p), rest = n - p - nb;
-            const cx<T> *dg = F + (int64_t)p * n + p;
-            cx<T> *xp = X + (int64_t)p * kc;
-            if (!conj) trsm_left<T, true, true, false><<<dim3(cb, 1, batch), 64, sm2, st>>>(nb, kc, dg, n, fstride, xp, kc, xstride);
-            else trsm_left<T, true, false, true><<<dim3(cb, 1, batch), 64, sm2, st>>>(nb, kc, dg, n, fstride, xp, kc, xstride);
-            if (rest > 0) {
-                if (!conj)  // X[p+nb:] -= L[p+nb:, p:p+nb] X[p:p+nb]
-                    cgemm_launch<T, cx<T>, false, false>(rest, kc, nb, cx<T>{T(-1), T(0)}, T(1), dg + (int64_t)nb * n,
-                                                         n, fstride, xp, kc, xstride, xp + (int64_t)nb * kc, kc,
-                                                         xstride, 1, batch, st);
-                else  // X[p+nb:] -= (U[p:p+nb, p+nb:])^H X[p:p+nb]
-                    cgemm_launch<T, cx<T>, true, false>(rest, kc, nb, cx<T>{T(-1), T(0)}, T(1), dg + nb, n, fstride,
-                                                        xp, kc, xstride, xp + (int64_t)nb * kc, kc, xstride, 1, batch,
-                                                        st);
-            }
+    auto ones = cx<T>{T(-1), T(0)};
+    // Two-level blocking: 64-row diagonal blocks (triangular solve, then the update of the
+    // rest of their 256-row panel), and one update with K = 256 of everything past the
+    // panel -- a quarter of the passes over X that rank-64 updates would make.
+    constexpr int PNB = 4 * DN_NB;
+    auto trsm = [&](int p, int nb, bool lower) {
+        const cx<T> *dg = F + (int64_t)p * n + p;
+        cx<T> *xp = X + (int64_t)p * kc;
+        const dim3 grid(cb, 1, batch);
+        if (lower) {
+            if (!conj) trsm_left<T, true, true, false><<<grid, 64, sm2, st>>>(nb, kc, dg, n, fstride, xp, kc, xstride);
+            else trsm_left<T, true, false, true><<<grid, 64, sm2, st>>>(nb, kc, dg, n, fstride, xp, kc, xstride);
+        } else {
+            if (!conj) trsm_left<T, false, false, false><<<grid, 64, sm2, st>>>(nb, kc, dg, n, fstride, xp, kc, xstride);
+            else trsm_left<T, false, true, true><<<grid, 64, sm2, st>>>(nb, kc, dg, n, fstride, xp, kc, xstride);
         }
-        // backward sweep
-        const int nblk = (n + DN_NB - 1) / DN_NB;
+    };
+    // X[r0 : r0+m] -= op(factor block rows r0.., columns k0 .. k0+K) X[k0 : k0+K], where the
+    // block is L or U of the non-conjugate solve, or the conjugate transpose of U (forward)
+    // or L (backward) of the conjugate one -- all read from the one stored factor
+    auto update = [&](int r0, int m, int k0, int K) {
+        cx<T> *xk = X + (int64_t)k0 * kc, *xr = X + (int64_t)r0 * kc;
+        if (!conj)
+            cgemm_launch<T, cx<T>, false, false>(m, kc, K, ones, T(1), F + (int64_t)r0 * n + k0, n, fstride, xk, kc,
+                                                 xstride, xr, kc, xstride, 1, batch, st);
+        else
+            cgemm_launch<T, cx<T>, true, false>(m, kc, K, ones, T(1), F + (int64_t)k0 * n + r0, n, fstride, xk, kc,
+                                                xstride, xr, kc, xstride, 1, batch, st);
+    };
+    // forward sweep (unit L, or U^H)
+    for (int p0 = 0; p0 < n; p0 += PNB) {
+        const int pe = std::min(n, p0 + PNB);
+        for (int p = p0; p < pe; p += DN_NB) {
+            const int nb = std::min(DN_NB, pe - p);
+            trsm(p, nb, true);
+            if (pe - p - nb > 0) update(p + nb, pe - p - nb, p, nb);
+        }
+        if (n - pe > 0) update(pe, n - pe, p0, pe - p0);
+    }
+    // backward sweep (U, or unit L^H), panels from the bottom
+    for (int pe = n; pe > 0; pe -= PNB) {
+        const int p0 = std::max(0, pe - PNB);
+        const int nblk = (pe - p0 + DN_NB - 1) / DN_NB;
         for (int bi = nblk - 1; bi >= 0; --bi) {
-            const int p = bi * DN_NB, nb = std::min(DN_NB, n - p);
-            const cx<T> *dg = F + (int64_t)p * n + p;
-            cx<T> *xp = X + (int64_t)p * kc;
-            if (!conj) trsm_left<T, false, false, false><<<dim3(cb, 1, batch), 64, sm2, st>>>(nb, kc, dg, n, fstride, xp, kc, xstride);
-            else trsm_left<T, false, true, true><<<dim3(cb, 1, batch), 64, sm2, st>>>(nb, kc, dg, n, fstride, xp, kc, xstride);
-            if (p > 0) {
-                if (!conj)  // X[:p] -= U[:p, p:p+nb] X[p:p+nb]
-                    cgemm_launch<T, cx<T>, false, false>(p, kc, nb, cx<T>{T(-1), T(0)}, T(1), F + p, n, fstride, xp,
-                                                         kc, xstride, X, kc, xstride, 1, batch, st);
-                else  // X[:p] -= (L[p:p+nb, :p])^H X[p:p+nb]
-                    cgemm_launch<T, cx<T>, true, false>(p, kc, nb, cx<T>{T(-1), T(0)}, T(1), F + (int64_t)p * n, n,
-                                                        fstride, xp, kc, xstride, X, kc, xstride, 1, batch, st);
-            }
+            const int p = p0 + bi * DN_NB, nb = std::min(DN_NB, pe - p);
+            trsm(p, nb, false);
+            if (p > p0) update(p0, p - p0, p, nb);
         }
-        return cudaGetLastError();
-    });
+        if (p0 > 0) update(0, p0, p0, pe - p0);
+    }
+    return cudaGetLastError();
 }
 
 // ------------------------------------------------------------------ driver
@@ -463,16 +476,61 @@ static cudaError_t factor_pairs(const DenseGeom &g, const DenseIO &io, const Den
     return cudaGetLastError();
 }
 
+// A second stream per host thread and device for the conjugate half of a complex solve
+// (created on first use, destroyed when the thread exits).
+static cudaStream_t aux_stream() {
+    struct Holder {
+        cudaStream_t s[16] = {};
+        ~Holder() {
+            for (cudaStream_t x : s)
+                if (x) cudaStreamDestroy(x);
+        }
+    };
+    static thread_local Holder h;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 16) return nullptr;
+    if (!h.s[dev] && cudaStreamCreateWithFlags(&h.s[dev], cudaStreamNonBlocking) != cudaSuccess) h.s[dev] = nullptr;
+    return h.s[dev];
+}
+
 template <class T>
 static cudaError_t solve_systems(const DenseGeom &g, const cx<T> *F, cx<T> *X, int64_t xstride, cudaStream_t st,
                                  Profiler &prof, const int *skip = nullptr) {
     const int64_t fs = (int64_t)g.n * g.n;
     const int batch = g.ninst * g.npairs;
-    if (!g.complex_a) return lu_solve<T>(g.n, g.kc, batch, F, fs, false, X, xstride, st, prof, skip);
-    // systems 2s (theta) and 2s+1 (conj theta) of every instance share factor s: the
-    // even and the odd systems each form a batch with stride 2*xstride
-    EXPM_TRY(lu_solve<T>(g.n, g.kc, batch, F, fs, false, X, 2 * xstride, st, prof, skip));
-    return lu_solve<T>(g.n, g.kc, batch, F, fs, true, X + xstride, 2 * xstride, st, prof, skip);
+    const bool wide = !(g.kc <= 8 && narrow_smem_bytes<T>(g.n, g.kc) <= (200u << 10));
+    const char *name = sizeof(T) == 8 ? "lu_solve<f64>" : "lu_solve<f32>";
+    if (!wide) {  // the narrow kernel times itself
+        if (!g.complex_a) return lu_solve<T>(g.n, g.kc, batch, F, fs, false, X, xstride, st, prof, skip);
+        // systems 2s (theta) and 2s+1 (conj theta) of every instance share factor s: the
+        // even and the odd systems each form a batch with stride 2*xstride
+        EXPM_TRY(lu_solve<T>(g.n, g.kc, batch, F, fs, false, X, 2 * xstride, st, prof, skip));
+        return lu_solve<T>(g.n, g.kc, batch, F, fs, true, X + xstride, 2 * xstride, st, prof, skip);
+    }
+    if (!g.complex_a)
+        return prof.timed(name, st, [&] { return lu_solve<T>(g.n, g.kc, batch, F, fs, false, X, xstride, st, prof, skip); });
+    cudaStream_t aux = aux_stream();
+    if (!aux)
+        return prof.timed(name, st, [&]() -> cudaError_t {
+            EXPM_TRY(lu_solve<T>(g.n, g.kc, batch, F, fs, false, X, 2 * xstride, st, prof, skip));
+            return lu_solve<T>(g.n, g.kc, batch, F, fs, true, X + xstride, 2 * xstride, st, prof, skip);
+        });
+    // many columns: the two halves are independent and run concurrently (fork / join
+    // through events, so the work stays ordered on st for the caller)
+    return prof.timed(name, st, [&]() -> cudaError_t {
+        cudaEvent_t fork, join;
+        EXPM_TRY(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
+        cudaError_t e = cudaEventCreateWithFlags(&join, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventRecord(fork, st);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(aux, fork, 0);
+        if (e == cudaSuccess) e = lu_solve<T>(g.n, g.kc, batch, F, fs, false, X, 2 * xstride, st, prof, skip);
+        if (e == cudaSuccess) e = lu_solve<T>(g.n, g.kc, batch, F, fs, true, X + xstride, 2 * xstride, aux, prof, skip);
+        if (e == cudaSuccess) e = cudaEventRecord(join, aux);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(st, join, 0);
+        cudaEventDestroy(fork);
+        cudaEventDestroy(join);
+        return e;
+    });
 }
 
 cudaError_t dense_factor(const DenseGeom &g, const DenseIO &io, const DenseSystems &sys, void *fwork, cudaStream_t st,
