@@ -15,6 +15,7 @@
 // Hermitian part |Im theta| I for Hermitian A, so unpivoted LU exists; its growth
 // is monitored (max|U| / max|M|) and reported.
 #pragma once
+#include <type_traits>
 #include "arith.cuh"
 #include "dense.cuh"
 
@@ -251,11 +252,112 @@ __global__ void __launch_bounds__(256) cgemm(int m, int n, int K, cx<T> alpha, T
         }
 }
 
+// Binary32 complex GEMM for wide operands: C = beta C + alpha op(A) B, op(A) = A or A^H.
+// 128 x 64 complex tile, BK = 8, 256 threads with 8 x 4 complex outputs each (rows
+// ty + 16 r, columns tx + 16 q), two shared-memory stages: the next K tile is fetched
+// into registers while the current one is consumed, then stored into the other stage,
+// one barrier per K tile.  Two CTAs per SM.
+template <bool CONJ_A>
+__global__ void __launch_bounds__(256, 2) cgemm_f32w(int m, int n, int K, cx<float> alpha, float beta,
+                                                     const cx<float> *__restrict__ A, int lda, int64_t sA,
+                                                     const cx<float> *__restrict__ B, int ldb, int64_t sB,
+                                                     cx<float> *__restrict__ C, int ldc, int64_t sC, int adiv) {
+    constexpr int BM = 128, BN = 64, BK = 8;
+    __shared__ cx<float> As[2][BK][BM + 4];
+    __shared__ cx<float> Bs[2][BK][BN + 4];
+    const cx<float> *a = A + (int64_t)(blockIdx.z / adiv) * sA;
+    const cx<float> *b = B + (int64_t)blockIdx.z * sB;
+    cx<float> *c = C + (int64_t)blockIdx.z * sC;
+    const int i0 = blockIdx.y * BM, j0 = blockIdx.x * BN;
+    const int t = threadIdx.x, tx = t % 16, ty = t / 16;
+    // this thread's share of a K tile: 4 elements of A, 2 of B
+    cx<float> pa[4], pb[2];
+    auto fetch = [&](int l0) {
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const int idx = t + 256 * e;
+            int ii, ll;
+            if (CONJ_A) { ii = idx % BM; ll = idx / BM; } else { ii = idx / BK; ll = idx % BK; }
+            const int gi = i0 + ii, gl = l0 + ll;
+            cx<float> v = {0.f, 0.f};
+            if (gi < m && gl < K) v = CONJ_A ? conj(a[(int64_t)gl * lda + gi]) : a[(int64_t)gi * lda + gl];
+            pa[e] = v;
+        }
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+            const int idx = t + 256 * e;
+            const int ll = idx / BN, jj = idx % BN;
+            const int gl = l0 + ll, gj = j0 + jj;
+            pb[e] = (gl < K && gj < n) ? b[(int64_t)gl * ldb + gj] : cx<float>{0.f, 0.f};
+        }
+    };
+    auto stash = [&](int st) {
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const int idx = t + 256 * e;
+            int ii, ll;
+            if (CONJ_A) { ii = idx % BM; ll = idx / BM; } else { ii = idx / BK; ll = idx % BK; }
+            As[st][ll][ii] = pa[e];
+        }
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+            const int idx = t + 256 * e;
+            Bs[st][idx / BN][idx % BN] = pb[e];
+        }
+    };
+    cx<float> acc[8][4];
+#pragma unroll
+    for (int r = 0; r < 8; ++r)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[r][q] = {0.f, 0.f};
+    const int nt = (K + BK - 1) / BK;
+    fetch(0);
+    stash(0);
+    __syncthreads();
+    for (int kt = 0; kt < nt; ++kt) {
+        const int cur = kt & 1;
+        if (kt + 1 < nt) fetch((kt + 1) * BK);
+#pragma unroll
+        for (int l = 0; l < BK; ++l) {
+            cx<float> av[8], bv[4];
+#pragma unroll
+            for (int r = 0; r < 8; ++r) av[r] = As[cur][l][ty + 16 * r];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) bv[q] = Bs[cur][l][tx + 16 * q];
+#pragma unroll
+            for (int r = 0; r < 8; ++r)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) acc[r][q] = cfma(acc[r][q], av[r], bv[q]);
+        }
+        if (kt + 1 < nt) stash(cur ^ 1);  // the other stage was last read before the previous barrier
+        __syncthreads();
+    }
+#pragma unroll
+    for (int r = 0; r < 8; ++r)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int gi = i0 + ty + 16 * r, gj = j0 + tx + 16 * q;
+            if (gi < m && gj < n) {
+                cx<float> *cp = c + (int64_t)gi * ldc + gj;
+                cx<float> out = alpha * acc[r][q];
+                if (beta != 0.f) out = out + scale(beta, *cp);
+                *cp = out;
+            }
+        }
+}
+
 // Launch helper: wide or narrow tile by the number of columns n.
 template <class T, class AE, bool CONJ_A, bool CONJ_B>
 inline void cgemm_launch(int m, int n, int K, cx<T> alpha, T beta, const AE *A, int lda, int64_t sA,
                          const cx<T> *B, int ldb, int64_t sB, cx<T> *C, int ldc, int64_t sC, int adiv, int batch,
                          cudaStream_t st) {
+    if constexpr (std::is_same<T, float>::value && std::is_same<AE, cx<float>>::value && !CONJ_B) {
+        if (n > 32) {
+            dim3 g((n + 63) / 64, (m + 127) / 128, batch);
+            cgemm_f32w<CONJ_A><<<g, 256, 0, st>>>(m, n, K, alpha, beta, A, lda, sA, B, ldb, sB, C, ldc, sC, adiv);
+            return;
+        }
+    }
     if (n <= 8) {
         dim3 g(1, (m + 127) / 128, batch);
         cgemm<T, AE, CONJ_A, CONJ_B, 128, 8, 4, 1><<<g, 256, 0, st>>>(m, n, K, alpha, beta, A, lda, sA, B, ldb, sB,
