@@ -506,6 +506,12 @@ def run_batched(args):
         Ys[name] = Y
         med = statistics.median(ts)
         out[name] = {"s_per_batch": round(med, 4), "instances_per_s": round(args.batch_count / med, 2)}
+        # one more call with per-kernel CUDA events (outside the timed calls)
+        P.expm_profile_enable(plan, True)
+        P.expm_apply_batched(plan, As, Vs, Y, prec=prec)
+        prof = P.expm_profile_read(plan)
+        P.expm_profile_enable(plan, False)
+        out[name]["kernels_ms"] = {k: round(v[1], 3) for k, v in prof.items()}
     worst = max(float((a - b).abs().pow(2).sum().sqrt() / b.abs().pow(2).sum().sqrt())
                 for a, b in zip(Ys["mixed"], Ys["fp64"]))
     out["mixed_vs_fp64_worst_rel"] = worst

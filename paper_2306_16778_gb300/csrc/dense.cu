@@ -613,8 +613,10 @@ cudaError_t dense_solve(const DenseGeom &g, const DenseIO &io, const DenseSystem
         // of the current X is checked before every sweep and once after the last one
         for (int it = 0;; ++it) {
             // R = V - (tA - cI + theta I) X, binary64
-            residual_diag<<<dim3(gx, 1, nsz), 256, 0, st>>>(g.n, g.kc, io, g.nsys, X, R, nk, sys, nullptr);
-            EXPM_TRY(cudaGetLastError());
+            EXPM_TRY(prof.timed("residual_diag", st, [&] {
+                residual_diag<<<dim3(gx, 1, nsz), 256, 0, st>>>(g.n, g.kc, io, g.nsys, X, R, nk, sys, nullptr);
+                return cudaGetLastError();
+            }));
             if (it > 0) {
                 if (use_oz) {
                     if (!oz_a_ready) {
@@ -636,15 +638,14 @@ cudaError_t dense_solve(const DenseGeom &g, const DenseIO &io, const DenseSystem
                         return cudaSuccess;
                     }
                 } else if (g.kc <= 8) {
-                    EXPM_TRY(prof.timed("resid_gemv<f64>", st, [&] {
-                        dim3 gg((g.n + 7) / 8, (g.nsys * g.kc + 15) / 16, g.ninst);
+                    EXPM_TRY(prof.timed("resid_gemv<f32x2>", st, [&] {
                         if (g.complex_a)
-                            resid_gemv_multi<cx<double>><<<gg, 256, 0, st>>>(g.n, g.kc, g.nsys, g.t,
-                                                                              (const cx<double> *)io.A, (int)io.lda,
-                                                                              io.astride, X, nk, R, nullptr);
+                            resid_gemv_f32x2_launch<cx<double>>(g.n, g.kc, g.nsys, g.ninst, g.t,
+                                                                (const cx<double> *)io.A, (int)io.lda, io.astride, X,
+                                                                nk, R, nullptr, st);
                         else
-                            resid_gemv_multi<double><<<gg, 256, 0, st>>>(g.n, g.kc, g.nsys, g.t, io.A, (int)io.lda,
-                                                                          io.astride, X, nk, R, nullptr);
+                            resid_gemv_f32x2_launch<double>(g.n, g.kc, g.nsys, g.ninst, g.t, io.A, (int)io.lda,
+                                                            io.astride, X, nk, R, nullptr, st);
                         return cudaGetLastError();
                     }));
                 } else EXPM_TRY(prof.timed("resid_gemm<f32x2>", st, [&] {
@@ -668,8 +669,10 @@ cudaError_t dense_solve(const DenseGeom &g, const DenseIO &io, const DenseSystem
             }
             EXPM_TRY(cudaMemsetAsync(rn2, 0, sizeof(double) * nsz, st));
             EXPM_TRY(cudaMemsetAsync(xn2, 0, sizeof(double) * nsz, st));
-            demote_and_norms<<<dim3(gx, 1, nsz), 256, 0, st>>>(nk, R, X, D, nk, rn2, xn2, nullptr);
-            EXPM_TRY(cudaGetLastError());
+            EXPM_TRY(prof.timed("demote_and_norms", st, [&] {
+                demote_and_norms<<<dim3(gx, 1, nsz), 256, 0, st>>>(nk, R, X, D, nk, rn2, xn2, nullptr);
+                return cudaGetLastError();
+            }));
             if (it > 0) {
                 EXPM_TRY(cudaMemcpyAsync(h.data(), rn2, sizeof(double) * nsz, cudaMemcpyDeviceToHost, st));
                 EXPM_TRY(cudaMemcpyAsync(h.data() + nsz, xn2, sizeof(double) * nsz, cudaMemcpyDeviceToHost, st));
@@ -692,8 +695,10 @@ cudaError_t dense_solve(const DenseGeom &g, const DenseIO &io, const DenseSystem
                 if (done || it > g.max_refine) break;
             }
             EXPM_TRY(solve_systems<float>(g, (const cx<float> *)F, D, nk, st, prof));
-            add_correction<<<dim3(gx, 1, nsz), 256, 0, st>>>(nk, D, X, nk, nullptr);
-            EXPM_TRY(cudaGetLastError());
+            EXPM_TRY(prof.timed("add_correction", st, [&] {
+                add_correction<<<dim3(gx, 1, nsz), 256, 0, st>>>(nk, D, X, nk, nullptr);
+                return cudaGetLastError();
+            }));
         }
     }
     EXPM_TRY(prof.timed("accumulate", st, [&] {
@@ -737,14 +742,13 @@ static cudaError_t dense_solve_devctl(const DenseGeom &g, const DenseIO &io, con
         residual_diag<<<dim3(gx, 1, nsz), 256, 0, st>>>(g.n, g.kc, io, g.nsys, X, R, nk, sys, done);
         EXPM_TRY(cudaGetLastError());
         if (it > 0) {
-            EXPM_TRY(prof.timed("resid_gemv<f64>", st, [&] {
-                dim3 gg((g.n + 7) / 8, (g.nsys * g.kc + 15) / 16, g.ninst);
+            EXPM_TRY(prof.timed("resid_gemv<f32x2>", st, [&] {
                 if (g.complex_a)
-                    resid_gemv_multi<cx<double>><<<gg, 256, 0, st>>>(g.n, g.kc, g.nsys, g.t, (const cx<double> *)io.A,
-                                                                      (int)io.lda, io.astride, X, nk, R, done);
+                    resid_gemv_f32x2_launch<cx<double>>(g.n, g.kc, g.nsys, g.ninst, g.t, (const cx<double> *)io.A,
+                                                        (int)io.lda, io.astride, X, nk, R, done, st);
                 else
-                    resid_gemv_multi<double><<<gg, 256, 0, st>>>(g.n, g.kc, g.nsys, g.t, io.A, (int)io.lda,
-                                                                  io.astride, X, nk, R, done);
+                    resid_gemv_f32x2_launch<double>(g.n, g.kc, g.nsys, g.ninst, g.t, io.A, (int)io.lda, io.astride, X,
+                                                    nk, R, done, st);
                 return cudaGetLastError();
             }));
         }

@@ -9,6 +9,9 @@
 //   trsm_left        op(T)^{-1} B for a triangular nb x nb block T (4 variants)
 //   trsm_right_upper B U^{-1} (the L21 panel of the blocked LU)
 //   cgemm            C = beta C + alpha op(A) op(B)  (op = N or conjugate transpose)
+//   cgemm_f32w       the same for wide binary32 operands (double-buffered 128 x 64 tile)
+//   resid_gemv_f32x2 / resid_gemm_f32x2  binary64-accurate refinement residuals on the
+//                    FP32 pipe (float pairs), at most 8 / more right-hand-side columns
 //   max_abs          max |x| over a (triangle of a) matrix, for the growth check
 //
 // No pivoting anywhere: (-i sign(Im theta)) (A + theta I) has the positive-definite
@@ -369,45 +372,6 @@ inline void cgemm_launch(int m, int n, int K, cx<T> alpha, T beta, const AE *A, 
     }
 }
 
-// ------------------------------------------------------------------ resid_gemv
-// R[z] -= t * A[z / adiv] * X[z] for at most 8 columns, binary64: one warp per row,
-// lanes stride over K, shuffle reduction.  Narrow residuals are memory-bound, so the
-// binary64 pipe suffices here.
-template <class AE>
-__global__ void __launch_bounds__(256) resid_gemv(int m, int n, int K, double t, const AE *__restrict__ A, int lda,
-                                                  int64_t sA, const cx<double> *__restrict__ X, int ldx, int64_t sX,
-                                                  cx<double> *__restrict__ Rm, int ldr, int64_t sR, int adiv) {
-    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-    const int row = blockIdx.x * 8 + warp;
-    if (row >= m) return;
-    const AE *a = A + (int64_t)(blockIdx.z / adiv) * sA + (int64_t)row * lda;
-    const cx<double> *x = X + (int64_t)blockIdx.z * sX;
-    cx<double> acc[8];
-#pragma unroll
-    for (int j = 0; j < 8; ++j) acc[j] = {0.0, 0.0};
-    for (int l = lane; l < K; l += 32) {
-        const cx<double> av = as_cx<double>(a[l]);
-#pragma unroll
-        for (int j = 0; j < 8; ++j)
-            if (j < n) acc[j] = cfma(acc[j], av, x[(int64_t)l * ldx + j]);
-    }
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
-        if (j < n) {
-            double re = acc[j].re, im = acc[j].im;
-            for (int o = 16; o > 0; o >>= 1) {
-                re += __shfl_xor_sync(0xffffffffu, re, o);
-                im += __shfl_xor_sync(0xffffffffu, im, o);
-            }
-            if (lane == 0) {
-                cx<double> *rp = Rm + (int64_t)blockIdx.z * sR + (int64_t)row * ldr + j;
-                rp->re -= t * re;
-                rp->im -= t * im;
-            }
-        }
-    }
-}
-
 // ------------------------------------------------------------------ lu_solve_narrow
 // X <- (L U)^{-1} X (CONJ = false) or (L U)^{-H} X = U^{-H} L^{-H} X (CONJ = true) for an
 // LU stored in place (unit L below the diagonal, U on and above), at most 8 columns.
@@ -541,64 +505,6 @@ template <class T> constexpr size_t narrow_smem_bytes(int n, int kc) {
     return sizeof(cx<T>) * ((size_t)n * kc + (size_t)DN_NB * (DN_NB + 1) + 4 * (size_t)DN_NB * 8);
 }
 
-// ------------------------------------------------------------------ resid_gemv_multi
-// R[inst, sys] -= t * A[inst] * X[inst, sys] for every system of an instance and at most
-// 8 columns, binary64.  The nsys * kc (system, column) pairs are taken 16 at a time
-// (grid.y), so A is read once per 16 pairs instead of once per system; a block holds 8
-// rows of A (one warp per row, lanes over K) and stages the X rows of the pairs in
-// shared memory in chunks of 128, transposed so that lanes read consecutive rows.
-// X and R of (inst, sys) start at (inst * nsys + sys) * sX, row-major n x kc.
-template <class AE>
-__global__ void __launch_bounds__(256) resid_gemv_multi(int n, int kc, int nsys, double t, const AE *__restrict__ A,
-                                                        int lda, int64_t sA, const cx<double> *__restrict__ X,
-                                                        int64_t sX, cx<double> *__restrict__ Rm, const int *skip) {
-    if (skip != nullptr && *skip) return;
-    constexpr int CB = 16, KCH = 128;
-    __shared__ cx<double> xs[CB][KCH];
-    const int inst = blockIdx.z;
-    const int cb0 = blockIdx.y * CB, ncomb = nsys * kc;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int row = blockIdx.x * 8 + warp;
-    const AE *arow = A + (int64_t)inst * sA + (int64_t)row * lda;
-    const cx<double> *Xi = X + (int64_t)inst * nsys * sX;
-    cx<double> acc[CB];
-#pragma unroll
-    for (int c = 0; c < CB; ++c) acc[c] = {0.0, 0.0};
-    for (int k0 = 0; k0 < n; k0 += KCH) {
-        __syncthreads();
-        for (int e = threadIdx.x; e < CB * KCH; e += blockDim.x) {
-            const int c = e / KCH, l = e % KCH, comb = cb0 + c, k = k0 + l;
-            cx<double> v = {0.0, 0.0};
-            if (comb < ncomb && k < n) v = Xi[(int64_t)(comb / kc) * sX + (int64_t)k * kc + comb % kc];
-            xs[c][l] = v;
-        }
-        __syncthreads();
-        if (row < n) {
-            const int lim = min(KCH, n - k0);
-            for (int l = lane; l < lim; l += 32) {
-                const cx<double> av = as_cx<double>(arow[k0 + l]);
-#pragma unroll
-                for (int c = 0; c < CB; ++c) acc[c] = cfma(acc[c], av, xs[c][l]);
-            }
-        }
-    }
-    if (row >= n) return;
-#pragma unroll
-    for (int c = 0; c < CB; ++c) {
-        double re = acc[c].re, im = acc[c].im;
-        for (int o = 16; o > 0; o >>= 1) {
-            re += __shfl_xor_sync(0xffffffffu, re, o);
-            im += __shfl_xor_sync(0xffffffffu, im, o);
-        }
-        const int comb = cb0 + c;
-        if (lane == 0 && comb < ncomb) {
-            cx<double> *rp = Rm + (int64_t)(inst * nsys + comb / kc) * sX + (int64_t)row * kc + comb % kc;
-            rp->re -= t * re;
-            rp->im -= t * im;
-        }
-    }
-}
-
 // ------------------------------------------------------------------ resid_gemm_f32x2
 // R[z] = R[z] - t * A[z / adiv] * X[z]  (A: m x K, X: K x n, all binary64 in memory)
 // with binary64-level accuracy on the FP32 pipe.  Inside each K-block of 16 the
@@ -624,6 +530,110 @@ EXPM_D void pair_mac(float &hi, float &lo, f32x2 a, f32x2 b) {
 }
 
 constexpr size_t RESID_GEMM_SMEM = 16 * 256 * sizeof(cx<double>);  // dynamic: the binary64 block sums
+
+// ------------------------------------------------------------------ resid_gemv_f32x2
+// R[inst, sys] -= t * A[inst] * X[inst, sys] for every system of an instance and at most
+// 8 columns ((system, column) pairs taken CB at a time, so A is read once per CB pairs;
+// a block holds 8 rows of A, one warp per row, lanes over K; X and R of (inst, sys)
+// start at (inst * nsys + sys) * sX, row-major n x kc), with binary64-level accuracy on
+// the FP32 pipe: A and X are split into float pairs (X once, when staged in
+// shared memory), each product is error-free up to the dropped lo*lo term (pair_mac),
+// a lane accumulates its terms of a 256-wide K chunk as an unnormalised pair and folds
+// it into a normalised double-word sum once per chunk, and the warp's lanes are
+// combined by double-word additions.  Relative error a few 2^-48 of sum |a_il x_l|.
+template <class AE, int CB, int LPR>
+__global__ void __launch_bounds__(256) resid_gemv_f32x2(int n, int kc, int nsys, double t, const AE *__restrict__ A,
+                                                        int lda, int64_t sA, const cx<double> *__restrict__ X,
+                                                        int64_t sX, cx<double> *__restrict__ Rm, const int *skip) {
+    if (skip != nullptr && *skip) return;
+    constexpr int KCH = 256;
+    __shared__ cx<f32x2> xs[CB][KCH];
+    const int inst = blockIdx.z;
+    const int cb0 = blockIdx.y * CB, ncomb = nsys * kc;
+    // LPR lanes per row (32, or 8 for short rows: fewer butterfly levels), 256 / LPR rows
+    // per block
+    const int lane = threadIdx.x % LPR;
+    const int row = blockIdx.x * (256 / LPR) + threadIdx.x / LPR;
+    const AE *arow = A + (int64_t)inst * sA + (int64_t)row * lda;
+    const cx<double> *Xi = X + (int64_t)inst * nsys * sX;
+    const f32x2 z2 = {0.f, 0.f};
+    cx<f32x2> acc[CB];
+#pragma unroll
+    for (int c = 0; c < CB; ++c) acc[c] = {z2, z2};
+    for (int k0 = 0; k0 < n; k0 += KCH) {
+        const int lim = min(KCH, n - k0);
+        __syncthreads();
+        for (int e = threadIdx.x; e < CB * lim; e += blockDim.x) {  // only the live columns
+            const int c = e / lim, l = e % lim, comb = cb0 + c;
+            cx<f32x2> v = {z2, z2};
+            if (comb < ncomb) v = split_cx<cx<double>>(Xi[(int64_t)(comb / kc) * sX + (int64_t)(k0 + l) * kc + comb % kc]);
+            xs[c][l] = v;
+        }
+        __syncthreads();
+        if (row < n) {
+            float hr[CB], lr[CB], hi[CB], li[CB];
+#pragma unroll
+            for (int c = 0; c < CB; ++c) hr[c] = lr[c] = hi[c] = li[c] = 0.f;
+            for (int l = lane; l < lim; l += LPR) {
+                const cx<f32x2> av = split_cx<AE>(arow[k0 + l]);
+                const f32x2 nai = {-av.im.hi, -av.im.lo};
+#pragma unroll
+                for (int c = 0; c < CB; ++c) {
+                    const cx<f32x2> xv = xs[c][l];
+                    pair_mac(hr[c], lr[c], av.re, xv.re);
+                    pair_mac(hr[c], lr[c], nai, xv.im);
+                    pair_mac(hi[c], li[c], av.re, xv.im);
+                    pair_mac(hi[c], li[c], av.im, xv.re);
+                }
+            }
+#pragma unroll
+            for (int c = 0; c < CB; ++c) {
+                acc[c].re = acc[c].re + two_sum(hr[c], lr[c]);
+                acc[c].im = acc[c].im + two_sum(hi[c], li[c]);
+            }
+        }
+    }
+    // the lanes' double-word sums combined by a butterfly of double-word additions (the
+    // FP32 pipe; all lanes take part, rows past n with zero sums); binary64 only for the
+    // final value
+#pragma unroll
+    for (int c = 0; c < CB; ++c) {
+        f32x2 re = acc[c].re, im = acc[c].im;
+#pragma unroll
+        for (int o = LPR / 2; o > 0; o >>= 1) {
+            const f32x2 ro = {__shfl_xor_sync(0xffffffffu, re.hi, o), __shfl_xor_sync(0xffffffffu, re.lo, o)};
+            const f32x2 io = {__shfl_xor_sync(0xffffffffu, im.hi, o), __shfl_xor_sync(0xffffffffu, im.lo, o)};
+            re = re + ro;
+            im = im + io;
+        }
+        const int comb = cb0 + c;
+        if (lane == 0 && comb < ncomb && row < n) {
+            cx<double> *rp = Rm + (int64_t)(inst * nsys + comb / kc) * sX + (int64_t)row * kc + comb % kc;
+            rp->re -= t * (widen_bits(re.hi) + widen_bits(re.lo));
+            rp->im -= t * (widen_bits(im.hi) + widen_bits(im.lo));
+        }
+    }
+}
+
+// pairs per block of resid_gemv_f32x2: 6 when that divides the pair count and 8 does not
+inline int gemv_f32x2_cb(int ncomb) { return (ncomb % 8 != 0 && ncomb % 6 == 0) ? 6 : 8; }
+
+template <class AE>
+inline void resid_gemv_f32x2_launch(int n, int kc, int nsys, int ninst, double t, const AE *A, int lda, int64_t sA,
+                                    const cx<double> *X, int64_t sX, cx<double> *R, const int *skip,
+                                    cudaStream_t st) {
+    const int ncomb = nsys * kc, cbw = gemv_f32x2_cb(ncomb);
+    const bool shortrow = n <= 256;
+    const int rpb = shortrow ? 32 : 8;  // rows per block
+    const dim3 gg((n + rpb - 1) / rpb, (ncomb + cbw - 1) / cbw, ninst);
+    if (shortrow) {
+        if (cbw == 6) resid_gemv_f32x2<AE, 6, 8><<<gg, 256, 0, st>>>(n, kc, nsys, t, A, lda, sA, X, sX, R, skip);
+        else resid_gemv_f32x2<AE, 8, 8><<<gg, 256, 0, st>>>(n, kc, nsys, t, A, lda, sA, X, sX, R, skip);
+    } else {
+        if (cbw == 6) resid_gemv_f32x2<AE, 6, 32><<<gg, 256, 0, st>>>(n, kc, nsys, t, A, lda, sA, X, sX, R, skip);
+        else resid_gemv_f32x2<AE, 8, 32><<<gg, 256, 0, st>>>(n, kc, nsys, t, A, lda, sA, X, sX, R, skip);
+    }
+}
 
 template <class AE>
 __global__ void __launch_bounds__(256, 2) resid_gemm_f32x2(int m, int n, int K, double t, const AE *__restrict__ A,
