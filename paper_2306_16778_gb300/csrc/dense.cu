@@ -498,33 +498,28 @@ static cudaError_t solve_systems(const DenseGeom &g, const cx<T> *F, cx<T> *X, i
                                  Profiler &prof, const int *skip = nullptr) {
     const int64_t fs = (int64_t)g.n * g.n;
     const int batch = g.ninst * g.npairs;
-    const bool wide = !(g.kc <= 8 && narrow_smem_bytes<T>(g.n, g.kc) <= (200u << 10));
     const char *name = sizeof(T) == 8 ? "lu_solve<f64>" : "lu_solve<f32>";
-    if (!wide) {  // the narrow kernel times itself
-        if (!g.complex_a) return lu_solve<T>(g.n, g.kc, batch, F, fs, false, X, xstride, st, prof, skip);
-        // systems 2s (theta) and 2s+1 (conj theta) of every instance share factor s: the
-        // even and the odd systems each form a batch with stride 2*xstride
-        EXPM_TRY(lu_solve<T>(g.n, g.kc, batch, F, fs, false, X, 2 * xstride, st, prof, skip));
-        return lu_solve<T>(g.n, g.kc, batch, F, fs, true, X + xstride, 2 * xstride, st, prof, skip);
-    }
+    Profiler quiet;  // the inner launches are timed as a whole here
     if (!g.complex_a)
-        return prof.timed(name, st, [&] { return lu_solve<T>(g.n, g.kc, batch, F, fs, false, X, xstride, st, prof, skip); });
+        return prof.timed(name, st, [&] { return lu_solve<T>(g.n, g.kc, batch, F, fs, false, X, xstride, st, quiet, skip); });
+    // systems 2s (theta) and 2s+1 (conj theta) of every instance share factor s: the
+    // even and the odd systems each form a batch with stride 2*xstride
     cudaStream_t aux = aux_stream();
     if (!aux)
         return prof.timed(name, st, [&]() -> cudaError_t {
-            EXPM_TRY(lu_solve<T>(g.n, g.kc, batch, F, fs, false, X, 2 * xstride, st, prof, skip));
-            return lu_solve<T>(g.n, g.kc, batch, F, fs, true, X + xstride, 2 * xstride, st, prof, skip);
+            EXPM_TRY(lu_solve<T>(g.n, g.kc, batch, F, fs, false, X, 2 * xstride, st, quiet, skip));
+            return lu_solve<T>(g.n, g.kc, batch, F, fs, true, X + xstride, 2 * xstride, st, quiet, skip);
         });
-    // many columns: the two halves are independent and run concurrently (fork / join
-    // through events, so the work stays ordered on st for the caller)
+    // the two halves are independent and run concurrently (fork / join through events,
+    // so the work stays ordered on st for the caller; also inside a stream capture)
     return prof.timed(name, st, [&]() -> cudaError_t {
         cudaEvent_t fork, join;
         EXPM_TRY(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
         cudaError_t e = cudaEventCreateWithFlags(&join, cudaEventDisableTiming);
         if (e == cudaSuccess) e = cudaEventRecord(fork, st);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(aux, fork, 0);
-        if (e == cudaSuccess) e = lu_solve<T>(g.n, g.kc, batch, F, fs, false, X, 2 * xstride, st, prof, skip);
-        if (e == cudaSuccess) e = lu_solve<T>(g.n, g.kc, batch, F, fs, true, X + xstride, 2 * xstride, aux, prof, skip);
+        if (e == cudaSuccess) e = lu_solve<T>(g.n, g.kc, batch, F, fs, false, X, 2 * xstride, st, quiet, skip);
+        if (e == cudaSuccess) e = lu_solve<T>(g.n, g.kc, batch, F, fs, true, X + xstride, 2 * xstride, aux, quiet, skip);
         if (e == cudaSuccess) e = cudaEventRecord(join, aux);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(st, join, 0);
         cudaEventDestroy(fork);
