@@ -59,6 +59,16 @@ expm_status plan_reserve(expm_plan p, void **buf, size_t *have, size_t need) {
     return EXPM_OK;
 }
 
+// the plan's second stream and its two events, created on first use (false if unavailable)
+bool plan_copy_stream(expm_plan p) {
+    if (p->copy && p->ev_fork && p->ev_copied) return true;
+    if (!p->copy && cudaStreamCreateWithFlags(&p->copy, cudaStreamNonBlocking) != cudaSuccess) p->copy = nullptr;
+    if (!p->ev_fork && cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming) != cudaSuccess) p->ev_fork = nullptr;
+    if (!p->ev_copied && cudaEventCreateWithFlags(&p->ev_copied, cudaEventDisableTiming) != cudaSuccess)
+        p->ev_copied = nullptr;
+    return p->copy && p->ev_fork && p->ev_copied;
+}
+
 int Profiler::kernel_index(const char *name) {
     for (size_t i = 0; i < names.size(); ++i)
         if (names[i] == name || std::strcmp(names[i], name) == 0) return (int)i;
@@ -203,6 +213,9 @@ expm_status expm_plan_destroy(expm_plan p) {
     p->prof.release();
     if (p->work) cudaFree(p->work);
     if (p->stage) cudaFree(p->stage);
+    if (p->copy) cudaStreamDestroy(p->copy);
+    if (p->ev_fork) cudaEventDestroy(p->ev_fork);
+    if (p->ev_copied) cudaEventDestroy(p->ev_copied);
     delete p;
     return EXPM_OK;
 }
@@ -257,6 +270,7 @@ expm_status expm_apply_tridiag(expm_plan p, int64_t N, const double *d, const vo
     double *dY = (double *)Y;
     const size_t nV = (size_t)N * Rc;
     const bool staged = !(dd && de && dv && dy);
+    cudaEvent_t v_ready = nullptr;  // set when V is copied on the second stream
     if (staged) {
         const size_t bytes = sizeof(double) * ((size_t)N + (size_t)N + 2 * nV) + 1024;
         s = plan_reserve(p, &p->stage, &p->stage_bytes, bytes);
@@ -269,7 +283,21 @@ expm_status expm_apply_tridiag(expm_plan p, int64_t N, const double *d, const vo
             err = cudaMemcpyAsync(sE, e, sizeof(double) * (N - 1), cudaMemcpyHostToDevice, st);
             dE = sE;
         }
-        if (err == cudaSuccess && !dv) { err = cudaMemcpyAsync(sV, V, sizeof(double) * nV, cudaMemcpyHostToDevice, st); dV = sV; }
+        if (err == cudaSuccess && !dv) {
+            // V is first read after the factorization (which needs d and e only): its copy
+            // runs on the plan's second stream, overlapping the factor kernels, and st
+            // waits for it just before the solve
+            if (plan_copy_stream(p)) {
+                err = cudaEventRecord(p->ev_fork, st);
+                if (err == cudaSuccess) err = cudaStreamWaitEvent(p->copy, p->ev_fork, 0);
+                if (err == cudaSuccess) err = cudaMemcpyAsync(sV, V, sizeof(double) * nV, cudaMemcpyHostToDevice, p->copy);
+                if (err == cudaSuccess) err = cudaEventRecord(p->ev_copied, p->copy);
+                v_ready = p->ev_copied;
+            } else {
+                err = cudaMemcpyAsync(sV, V, sizeof(double) * nV, cudaMemcpyHostToDevice, st);
+            }
+            dV = sV;
+        }
         if (!dy) dY = sY;
         if (err != cudaSuccess) return cuda_error(err, "apply_tridiag: staging copy");
     }
@@ -277,6 +305,7 @@ expm_status expm_apply_tridiag(expm_plan p, int64_t N, const double *d, const vo
     if (mixed) {
         void *swork = (unsigned char *)p->work + mix_factor;
         err = tri_mixed_factor(g, dD, dE, ps, p->work, st, p->prof);
+        if (err == cudaSuccess && v_ready) err = cudaStreamWaitEvent(st, v_ready, 0);
         if (err == cudaSuccess) err = tri_mixed_solve(g, dV, dY, ps, p->work, swork, mo, st, p->prof);
         if (err != cudaSuccess) return cuda_error(err, "apply_tridiag: kernel launch");
         if (info) {
@@ -288,7 +317,7 @@ expm_status expm_apply_tridiag(expm_plan p, int64_t N, const double *d, const vo
             if (mo.verify && !mr.converged) info->status_worst = EXPM_ENOCONV;
         }
     } else {
-        err = tri_run(g, ff, dD, dE, dV, dY, ps, p->work, st, p->prof);
+        err = tri_run(g, ff, dD, dE, dV, dY, ps, p->work, st, p->prof, v_ready);
         if (err != cudaSuccess) return cuda_error(err, "apply_tridiag: kernel launch");
     }
     if (staged) {

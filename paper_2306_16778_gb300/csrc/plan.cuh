@@ -48,6 +48,8 @@ struct expm_plan_s {
     size_t work_bytes = 0;
     void *stage = nullptr;    // device staging area for host buffers
     size_t stage_bytes = 0;
+    cudaStream_t copy = nullptr;            // second stream: host-to-device copies that overlap kernels
+    cudaEvent_t ev_fork = nullptr, ev_copied = nullptr;
     expm::Profiler prof;
 };
 
@@ -57,6 +59,7 @@ expm_status set_error(expm_status s, const std::string &msg);
 expm_status cuda_error(cudaError_t e, const char *where);
 bool is_device_ptr(const void *p);
 expm_status plan_reserve(expm_plan p, void **buf, size_t *have, size_t need);
+bool plan_copy_stream(expm_plan p);
 
 // Makes a device current for the lifetime of the object and restores the previous one.
 class DeviceGuard {

@@ -339,12 +339,13 @@ cudaError_t tri_solve(const TriGeom &g, bool ff, const double *V, double *Y, con
 }
 
 cudaError_t tri_run(const TriGeom &g, bool ff, const double *d, const double *e, const double *V, double *Y,
-                    const TriPoles &ps, void *work, cudaStream_t st, Profiler &prof) {
+                    const TriPoles &ps, void *work, cudaStream_t st, Profiler &prof, cudaEvent_t v_ready) {
     const TriLayout L = tri_layout(g, ff);
     unsigned char *p = (unsigned char *)work;
     void *scr = p + L.us;
     unsigned char *solve_base = p + L.factor_total + tri_overflow(g);
     cudaError_t err = ff ? tri_factor_t<f32x2>(g, d, e, ps, p, st, prof) : tri_factor_t<double>(g, d, e, ps, p, st, prof);
+    if (err == cudaSuccess && v_ready) err = cudaStreamWaitEvent(st, v_ready, 0);  // V arrives on another stream
     if (err != cudaSuccess) return err;
     return ff ? tri_solve_t<f32x2>(g, V, Y, ps, p, solve_base, scr, st, prof)
               : tri_solve_t<double>(g, V, Y, ps, p, solve_base, scr, st, prof);

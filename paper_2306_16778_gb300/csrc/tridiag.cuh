@@ -43,8 +43,10 @@ cudaError_t tri_factor(const TriGeom &g, bool ff, const double *d, const double 
 // solve part for a block of right-hand sides, with a factor part made by tri_factor
 cudaError_t tri_solve(const TriGeom &g, bool ff, const double *V, double *Y, const TriPoles &ps, const void *fwork,
                       void *swork, cudaStream_t st, Profiler &prof);
+// v_ready (optional): an event that st waits for between the factorization and the
+// first kernel that reads V (V copied on another stream meanwhile)
 cudaError_t tri_run(const TriGeom &g, bool ff, const double *d, const double *e, const double *V, double *Y,
-                    const TriPoles &ps, void *work, cudaStream_t st, Profiler &prof);
+                    const TriPoles &ps, void *work, cudaStream_t st, Profiler &prof, cudaEvent_t v_ready = nullptr);
 
 // binary32 factors + refinement (EXPM_MIXED_FP32), tridiag_mixed.cu.  The factor part
 // (prep + binary32 block LUs and spikes) depends on T, t, c and the poles only.
