@@ -428,7 +428,8 @@ def run_dense(args):
     A, V = (torch.from_numpy(x).to(dev) for x in (w["A"], w["V"]))
     out = {"workload": f"dense Hermitian n={args.dense_n}, 256 complex RHS, degree 16, spectrum U[-50,0]"}
     Ys = {}
-    for name, prec in (("fp64", P.EXPM_FP64), ("mixed", P.EXPM_MIXED_FP32), ("mixed_tc", P.EXPM_MIXED_TF32X3)):
+    for name, prec in (("fp64", P.EXPM_FP64), ("mixed", P.EXPM_MIXED_FP32), ("mixed_tc", P.EXPM_MIXED_TF32X3),
+                       ("mixed_bf16x3", P.EXPM_MIXED_BF16X3)):
         Y = torch.empty_like(V)
         info = P.expm_apply_dense(plan, A, V, Y, prec=prec)
         P.expm_profile_enable(plan, True)
@@ -454,7 +455,7 @@ def run_dense(args):
         Ys[name] = Y.clone()
         out[name] = {"s_per_eval": round(statistics.median(ts), 5), "evals_per_s": round(1 / statistics.median(ts), 4),
                      "kernels_ms_total": {k: round(v[1], 3) for k, v in prof.items()}}
-    for name in ("mixed", "mixed_tc", "reduced", "reduced_mixed"):
+    for name in ("mixed", "mixed_tc", "mixed_bf16x3", "reduced", "reduced_mixed"):
         d = (Ys[name] - Ys["fp64"]).abs().pow(2).sum().sqrt() / Ys["fp64"].abs().pow(2).sum().sqrt()
         out[f"{name}_vs_fp64_rel"] = float(d)
     print(json.dumps(out), flush=True)

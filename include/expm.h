@@ -70,8 +70,11 @@ typedef enum expm_precision {
     EXPM_MIXED_FP32 = 2,  /* dense: binary32 LU + binary64-residual refinement;
                              tridiagonal: binary32 factors and solves + refinement
                              with float-float residuals (FP32 pipe only)            */
-    EXPM_MIXED_TF32X3 = 3 /* dense: LU trailing updates on the tensor cores with a
-                             3-term TF32 split, + binary64-residual refinement      */
+    EXPM_MIXED_TF32X3 = 3, /* dense: LU trailing updates on the tensor cores with a
+                              3-term TF32 split, + binary64-residual refinement     */
+    EXPM_MIXED_BF16X3 = 4  /* dense: LU trailing updates on the tensor cores with a
+                              3-part bf16 split (six products), + binary64-residual
+                              refinement                                            */
 } expm_precision;
 
 typedef struct expm_opts {
@@ -231,8 +234,10 @@ expm_status expm_apply_tridiag_noalloc(expm_plan plan, int64_t N, const double *
  *                 complex, else real.  Must not overlap A or V.
  *   opts          prec: EXPM_FP64 (binary64 throughout), EXPM_MIXED_FP32 /
  *                 EXPM_MIXED_F32X2 (binary32 factorization on the CUDA cores) or
- *                 EXPM_MIXED_TF32X3 (binary32 factorization whose trailing updates run
- *                 on the tensor cores, tcgen05 kind::tf32 with the 3xTF32 split), each
+ *                 EXPM_MIXED_TF32X3 / EXPM_MIXED_BF16X3 (binary32 factorization whose
+ *                 trailing updates run on the tensor cores: tcgen05 kind::tf32 with the
+ *                 3xTF32 split, or kind::f16 with each value split into three bf16
+ *                 parts and the six products of order <= 2), each
  *                 followed by iterative refinement with binary64-accurate residuals until
  *                 ||R_k||_F <= tol (||tA||_F + |theta_k - c|) ||X_k||_F, at most
  *                 max_refine sweeps); growth_max bounds max|U| / max|tA - cI + theta I|.

@@ -16,6 +16,7 @@ from ._native import (  # noqa: F401
     EXPM_MIXED_F32X2,
     EXPM_MIXED_FP32,
     EXPM_MIXED_TF32X3,
+    EXPM_MIXED_BF16X3,
     EXPM_FLAG_SKIP_FINAL_RESIDUAL,
     BatchGraph,
     ExpmError,

@@ -14,6 +14,7 @@ EXPM_FP64 = 0
 EXPM_MIXED_F32X2 = 1
 EXPM_MIXED_FP32 = 2
 EXPM_MIXED_TF32X3 = 3
+EXPM_MIXED_BF16X3 = 4
 EXPM_FLAG_SKIP_FINAL_RESIDUAL = 1
 
 STATUS = {0: "EXPM_OK", 1: "EXPM_EINVAL", 2: "EXPM_ENOMEM", 3: "EXPM_EGROWTH", 4: "EXPM_ENOCONV",

@@ -338,7 +338,7 @@ expm_status expm_apply_dense(expm_plan p, int n, const void *A, int lda, int a_i
     if (n < 1 || k < 1 || k > 4096) return set_error(EXPM_EINVAL, "apply_dense: need n >= 1 and 1 <= k <= 4096");
     if (lda < n || ldv < k || ldy < k) return set_error(EXPM_EINVAL, "apply_dense: leading dimension too small");
     if (!A || !V || !Y) return set_error(EXPM_EINVAL, "apply_dense: NULL data pointer");
-    if (opts.prec < EXPM_FP64 || opts.prec > EXPM_MIXED_TF32X3)
+    if (opts.prec < EXPM_FP64 || opts.prec > EXPM_MIXED_BF16X3)
         return set_error(EXPM_EINVAL, "apply_dense: unknown precision");
     if (opts.flags != 0) return set_error(EXPM_EINVAL, "apply_dense: opts.flags must be 0");
     if (!std::isfinite(opts.t) || !std::isfinite(opts.shift_c) || !(opts.tol > 0) || opts.max_refine < 0)
@@ -358,7 +358,7 @@ expm_status expm_apply_dense(expm_plan p, int n, const void *A, int lda, int a_i
     const bool split_v = !complex_a && v_is_complex;
     g.kc = split_v ? 2 * k : k;
     g.mixed = opts.prec != EXPM_FP64;
-    g.tc = opts.prec == EXPM_MIXED_TF32X3;
+    g.tc = opts.prec == EXPM_MIXED_TF32X3 ? 1 : opts.prec == EXPM_MIXED_BF16X3 ? 2 : 0;
     g.t = opts.t;
     g.tol = opts.tol;
     g.max_refine = opts.max_refine;

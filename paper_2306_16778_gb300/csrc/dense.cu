@@ -194,8 +194,11 @@ __global__ void frob2(int n, const double *__restrict__ A, int64_t lda, int64_t 
 //   U12 (nb x rest complex) becomes the real 2rest x 2nb matrix BT with rows
 //       BT[2j] = (.. ur_kj, -ui_kj ..),  BT[2j+1] = (.. ui_kj, ur_kj ..),
 //   so that (A BT^T)[i][2j] = Re(L21 U12)_ij and [i][2j+1] = Im(L21 U12)_ij;
-//   A' = [A_hi | A_hi | A_lo] and B' = [BT_hi | BT_lo | BT_hi] (K = 6 nb), with x_hi
-//   x rounded to TF32 and x_lo = x - x_hi (exact in binary32).
+//   A' = [A_lo | A_hi | A_hi] and B' = [BT_hi | BT_lo | BT_hi] (K = 6 nb), with x_hi
+//   x rounded to TF32 and x_lo = x - x_hi (exact in binary32).  The small products come
+//   first along K: the tensor cores' fp32 accumulation truncates, so each addition loses
+//   up to an ulp of the running sum, and the running sum is kept small while the small
+//   terms go in.
 // Batch z of A' occupies rows z*rest_a .. of a stacked matrix, likewise B' (2 rest rows).
 EXPM_D float tf32_hi(float x) { return __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u); }
 
@@ -211,9 +214,9 @@ __global__ void split_tc_operands(int rest, int nb, const cx<float> *__restrict_
         const cx<float> a = L21[(int64_t)i * n + k];
         float *row = Ap + ((int64_t)z * rest + i) * K6;
         const float hr = tf32_hi(a.re), hi = tf32_hi(a.im);
-        row[2 * k] = hr;               row[2 * k + 1] = hi;
+        row[2 * k] = a.re - hr;        row[2 * k + 1] = a.im - hi;
         row[2 * nb + 2 * k] = hr;      row[2 * nb + 2 * k + 1] = hi;
-        row[4 * nb + 2 * k] = a.re - hr; row[4 * nb + 2 * k + 1] = a.im - hi;
+        row[4 * nb + 2 * k] = hr;      row[4 * nb + 2 * k + 1] = hi;
         // the U12 entry (k, i) of the same index range (rest x nb pairs, transposed)
         const cx<float> u = U12[(int64_t)k * n + i];
         float *r0 = Bp + ((int64_t)z * 2 * rest + 2 * i) * K6;
@@ -227,6 +230,63 @@ __global__ void split_tc_operands(int rest, int nb, const cx<float> *__restrict_
         r1[2 * k] = wh;                r1[2 * k + 1] = uh;
         r1[2 * nb + 2 * k] = wr - wh;  r1[2 * nb + 2 * k + 1] = ur - uh;
         r1[4 * nb + 2 * k] = wh;       r1[4 * nb + 2 * k + 1] = uh;
+    }
+}
+
+// The same update with the bf16x3 split: x = h + m + l, each part bf16 (h = bf16(x),
+// m = bf16(x - h), l = bf16(x - h - m); the differences are exact in binary32), 24 bits
+// in all.  A' = [A_l | A_m | A_h | A_m | A_h | A_h] and B' = [BT_h | BT_m | BT_l | BT_h |
+// BT_m | BT_h] (K = 12 nb), so A' B'^T sums the six products with p + q <= 2, the
+// smallest first (see the TF32 split above).
+EXPM_D uint16_t bf16_rn_bits(float x) {  // round to nearest even (finite x)
+    const unsigned u = __float_as_uint(x);
+    return (uint16_t)((u + 0x7FFFu + ((u >> 16) & 1u)) >> 16);
+}
+EXPM_D float bf16_val(uint16_t b) { return __uint_as_float((unsigned)b << 16); }
+EXPM_D void bf16x3(float x, uint16_t &h, uint16_t &m, uint16_t &l) {
+    h = bf16_rn_bits(x);
+    const float r1 = __fsub_rn(x, bf16_val(h));
+    m = bf16_rn_bits(r1);
+    l = bf16_rn_bits(__fsub_rn(r1, bf16_val(m)));
+}
+
+__global__ void split_tc_operands_bf16(int rest, int nb, const cx<float> *__restrict__ F, int n, int64_t fstride,
+                                       uint16_t *__restrict__ Ap, uint16_t *__restrict__ Bp) {
+    const int z = blockIdx.z;
+    const cx<float> *L21 = F + (int64_t)z * fstride + (int64_t)nb * n;
+    const cx<float> *U12 = F + (int64_t)z * fstride + nb;
+    const int K12 = 12 * nb, w = 2 * nb;  // one segment: nb complex = 2 nb values
+    const int64_t na = (int64_t)rest * nb;
+    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < na; idx += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(idx / nb), k = (int)(idx % nb);
+        const cx<float> a = L21[(int64_t)i * n + k];
+        uint16_t rh, rm, rl, ih, im, il;
+        bf16x3(a.re, rh, rm, rl);
+        bf16x3(a.im, ih, im, il);
+        uint16_t *row = Ap + ((int64_t)z * rest + i) * K12 + 2 * k;
+        const uint16_t segr[6] = {rl, rm, rh, rm, rh, rh}, segi[6] = {il, im, ih, im, ih, ih};
+#pragma unroll
+        for (int q = 0; q < 6; ++q) {
+            row[q * w] = segr[q];
+            row[q * w + 1] = segi[q];
+        }
+        // U12 entry (k, i): rows 2i (Re output: (ur, -ui)) and 2i+1 (Im output: (ui, ur))
+        const cx<float> u = U12[(int64_t)k * n + i];
+        uint16_t uh, um, ul, vh, vm, vl, wh, wm, wl;
+        bf16x3(u.re, uh, um, ul);
+        bf16x3(-u.im, vh, vm, vl);
+        bf16x3(u.im, wh, wm, wl);
+        uint16_t *r0 = Bp + ((int64_t)z * 2 * rest + 2 * i) * K12 + 2 * k;
+        uint16_t *r1 = r0 + K12;
+        const uint16_t s0r[6] = {uh, um, ul, uh, um, uh}, s0i[6] = {vh, vm, vl, vh, vm, vh};
+        const uint16_t s1r[6] = {wh, wm, wl, wh, wm, wh}, s1i[6] = {uh, um, ul, uh, um, uh};
+#pragma unroll
+        for (int q = 0; q < 6; ++q) {
+            r0[q * w] = s0r[q];
+            r0[q * w + 1] = s0i[q];
+            r1[q * w] = s1r[q];
+            r1[q * w + 1] = s1i[q];
+        }
     }
 }
 
@@ -249,8 +309,9 @@ template <class K> static cudaError_t set_smem(K kernel, size_t bytes) {
 
 // Tensor-core scratch of the trailing update (binary32 LU with the TF32 split).
 struct TcScratch {
-    float *Ap = nullptr, *Bp = nullptr;
+    float *Ap = nullptr, *Bp = nullptr;  // bf16 operands in the same bytes when bf16
     int *err = nullptr;
+    bool bf16 = false;
 };
 
 // Unpivoted blocked LU of `batch` n x n matrices F (ld n, batch stride n*n).  With
@@ -282,7 +343,29 @@ static cudaError_t lu_blocked(int n, int batch, cx<T> *F, cudaStream_t st, Profi
                                                                                  diag + (int64_t)nb * n, n, bs);
             return cudaGetLastError();
         }));
-        if (tc != nullptr && sizeof(T) == 4 && rest >= 128 &&
+        if (tc != nullptr && tc->bf16 && sizeof(T) == 4 && rest >= 128 &&
+            tc_gemm_supported(rest, 2 * rest, 12 * nb, tc->Ap, 12 * nb, tc->Bp, 12 * nb,
+                              F + (int64_t)(p + nb) * n + p + nb, 2 * n, true)) {
+            // A22 -= L21 U12 as one real product per matrix, bf16x3 split
+            uint16_t *Ab = reinterpret_cast<uint16_t *>(tc->Ap), *Bb = reinterpret_cast<uint16_t *>(tc->Bp);
+            EXPM_TRY(prof.timed("split_tc_operands", st, [&] {
+                split_tc_operands_bf16<<<dim3(grid1d((int64_t)rest * nb), 1, batch), 256, 0, st>>>(
+                    rest, nb, reinterpret_cast<const cx<float> *>(diag), n, bs, Ab, Bb);
+                return cudaGetLastError();
+            }));
+            EXPM_TRY(prof.timed("tc_gemm_bf16x3", st, [&]() -> cudaError_t {
+                for (int z = 0; z < batch; ++z) {
+                    float *Cz = reinterpret_cast<float *>(F + (int64_t)z * bs + (int64_t)(p + nb) * n + p + nb);
+                    cudaError_t e = tc_gemm_bf16_sub(rest, 2 * rest, 12 * nb, Ab + (int64_t)z * rest * 12 * nb,
+                                                     12 * nb, Bb + (int64_t)z * 2 * rest * 12 * nb, 12 * nb, Cz,
+                                                     2 * n, tc->err, st);
+                    if (e != cudaSuccess) return e;
+                }
+                return cudaSuccess;
+            }));
+            continue;
+        }
+        if (tc != nullptr && !tc->bf16 && sizeof(T) == 4 && rest >= 128 &&
             tc_gemm_supported(rest, 2 * rest, 6 * nb, tc->Ap, 6 * nb, tc->Bp, 6 * nb,
                               F + (int64_t)(p + nb) * n + p + nb, 2 * n)) {
             // A22 -= L21 U12 as one real product per matrix on the tensor cores
@@ -535,7 +618,7 @@ cudaError_t dense_factor(const DenseGeom &g, const DenseIO &io, const DenseSyste
     unsigned *amax = (unsigned *)(p + L.amax);
     unsigned *umax = (unsigned *)(p + L.umax);
     if (g.mixed && g.tc) {
-        TcScratch tc{(float *)(p + L.tcA), (float *)(p + L.tcB), (int *)(p + L.tcflag)};
+        TcScratch tc{(float *)(p + L.tcA), (float *)(p + L.tcB), (int *)(p + L.tcflag), g.tc == 2};
         EXPM_TRY(cudaMemsetAsync(tc.err, 0, sizeof(int), st));
         return factor_pairs<float>(g, io, sys, (cx<float> *)(p + L.F), amax, umax, st, prof, &tc);
     }

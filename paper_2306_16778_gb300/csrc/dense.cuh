@@ -31,7 +31,7 @@ struct DenseGeom {
     int nsys;       // solved systems per instance
     int complex_a;  // A complex Hermitian (else real symmetric)
     int mixed;      // binary32 factorization + binary64 refinement
-    int tc;         // mixed only: LU trailing updates on the tensor cores (3xTF32)
+    int tc;         // mixed only: LU trailing updates on the tensor cores (1: 3xTF32, 2: bf16x3)
     double t;       // time factor
     double tol;     // refinement tolerance
     int max_refine;

@@ -46,7 +46,7 @@ extern "C" expm_status expm_apply_dense_full(expm_plan p, int n, const void *A, 
     if (n < 1) return set_error(EXPM_EINVAL, "apply_dense_full: need n >= 1");
     if (lda < n || ldy < n) return set_error(EXPM_EINVAL, "apply_dense_full: leading dimension too small");
     if (!A || !Y) return set_error(EXPM_EINVAL, "apply_dense_full: NULL data pointer");
-    if (opts.prec < EXPM_FP64 || opts.prec > EXPM_MIXED_TF32X3)
+    if (opts.prec < EXPM_FP64 || opts.prec > EXPM_MIXED_BF16X3)
         return set_error(EXPM_EINVAL, "apply_dense_full: unknown precision");
     if (opts.flags != 0) return set_error(EXPM_EINVAL, "apply_dense_full: opts.flags must be 0");
     if (!std::isfinite(opts.t) || !std::isfinite(opts.shift_c) || !(opts.tol > 0) || opts.max_refine < 0)
@@ -65,7 +65,7 @@ extern "C" expm_status expm_apply_dense_full(expm_plan p, int n, const void *A, 
     g.nsys = complex_a ? 2 * S : S;
     g.kc = kcw;
     g.mixed = opts.prec != EXPM_FP64;
-    g.tc = opts.prec == EXPM_MIXED_TF32X3;
+    g.tc = opts.prec == EXPM_MIXED_TF32X3 ? 1 : opts.prec == EXPM_MIXED_BF16X3 ? 2 : 0;
     g.t = opts.t;
     g.tol = opts.tol;
     g.max_refine = opts.max_refine;

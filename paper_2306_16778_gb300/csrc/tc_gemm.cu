@@ -1,15 +1,18 @@
-// tc_gemm.cu -- C -= A * B^T on the 5th-generation tensor cores (tcgen05, kind::tf32).
+// tc_gemm.cu -- C -= A * B^T on the 5th-generation tensor cores (tcgen05: kind::tf32, or
+// kind::f16 with bf16 operands).
 //
-// A is M x K and B is N x K, both K-major (row-major with the K index fastest), fp32 in
-// memory and read by the tensor cores as TF32; C is M x N fp32 row-major, updated in
-// place.  This is the trailing update of the mixed-precision LU: with the operands
-// split into TF32 high and low parts and concatenated along K, one call computes
-// C -= A_hi B_hi^T + A_hi B_lo^T + A_lo B_hi^T (the 3xTF32 scheme), i.e. an update with
-// binary32-level accuracy at three TF32 products per term.
+// A is M x K and B is N x K, both K-major (row-major with the K index fastest): fp32 in
+// memory read by the tensor cores as TF32, or bf16; C is M x N fp32 row-major, updated
+// in place.  This is the trailing update of the mixed-precision LU: with the operands
+// split into high and low parts and concatenated along K, one call computes
+// C -= A_hi B_hi^T + A_hi B_lo^T + A_lo B_hi^T (the 3xTF32 scheme), or with bf16 parts
+// (h, m, l) the six products h h + h m + m h + h l + m m + l h (the bf16x3 scheme) --
+// an update with binary32-level accuracy either way.
 //
-// One CTA computes one 128 x 128 tile of C: warp 0 issues TMA loads of 128 x 32 fp32
-// tiles of A and B (128-byte rows, 128-byte swizzle) into a 4-stage shared-memory ring;
-// one thread of warp 1 issues tcgen05.mma (M = 128, N = 128, K = 8 per instruction)
+// One CTA computes one 128 x 128 tile of C: warp 0 issues TMA loads of 128-row tiles of
+// A and B, one 128-byte row of K each (32 fp32 or 64 bf16; 128-byte swizzle), into a
+// 4-stage shared-memory ring; one thread of warp 1 issues tcgen05.mma (M = 128, N = 128,
+// 32 bytes of K per instruction)
 // into a 128 x 128 fp32 accumulator in tensor memory and releases each stage with
 // tcgen05.commit; the C tile is fetched by TMA into shared memory while the K loop runs.
 // Then all four warps read the accumulator back with tcgen05.ld (warp w owns TMEM lanes
@@ -31,9 +34,11 @@ namespace expm {
 
 namespace {
 
-constexpr int TC_BM = 128, TC_BN = 128, TC_BK = 32;  // BK fp32 = 128 bytes per tile row
+constexpr int TC_BM = 128, TC_BN = 128;
+constexpr int TC_ROW_BYTES = 128;                     // one 128-byte swizzled row per tile row and stage:
+                                                      // 32 fp32 (TF32) or 64 bf16 elements of K
 constexpr int TC_STAGES = 4;
-constexpr int TC_TILE_BYTES = TC_BM * TC_BK * 4;      // 16 KB for A, same for B (BN == BM)
+constexpr int TC_TILE_BYTES = TC_BM * TC_ROW_BYTES;   // 16 KB for A, same for B (BN == BM)
 constexpr int TC_CTILE_BYTES = TC_BM * TC_BN * 4;     // the C tile, prefetched by TMA
 constexpr int TC_SMEM = TC_STAGES * 2 * TC_TILE_BYTES + TC_CTILE_BYTES + 1024 + 256;
 using tcu::mbar_expect_tx;
@@ -44,19 +49,24 @@ using tcu::tma_load_2d;
 
 __device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t saddr) { return tcu::smem_desc(saddr, 128); }
 
-// Instruction descriptor of kind::tf32: D fp32, A and B TF32, both K-major, M x N.
-__host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
-    return (1u << 4)                       // D format: F32
-           | (2u << 7)                     // A format: TF32
-           | (2u << 10)                    // B format: TF32
-           | ((uint32_t)(N >> 3) << 17)    // N / 8
-           | ((uint32_t)(M >> 4) << 24);   // M / 16
+// Instruction descriptor: D fp32, A and B both TF32 (kind::tf32) or both bf16
+// (kind::f16), K-major, M x N.
+__host__ __device__ constexpr uint32_t idesc_tc(bool bf16, int M, int N) {
+    return (1u << 4)                              // D format: F32
+           | ((bf16 ? 1u : 2u) << 7)              // A format: BF16 / TF32
+           | ((bf16 ? 1u : 2u) << 10)             // B format: BF16 / TF32
+           | ((uint32_t)(N >> 3) << 17)           // N / 8
+           | ((uint32_t)(M >> 4) << 24);          // M / 16
 }
 
+// BF16 = false: fp32 operands read as TF32, 32 of K per stage; true: bf16 operands, 64.
+// Either way four MMAs of 32 bytes of K per stage.
+template <bool BF16>
 __global__ void __launch_bounds__(128, 1)
-    tc_gemm_tf32_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
-                        const __grid_constant__ CUtensorMap mapC, int M, int N, int K, float *__restrict__ C, int ldc,
-                        int *__restrict__ err_flag) {
+    tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
+                   const __grid_constant__ CUtensorMap mapC, int M, int N, int K, float *__restrict__ C, int ldc,
+                   int *__restrict__ err_flag) {
+    constexpr int TC_BK = BF16 ? 64 : 32;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     // 1024-byte aligned stage buffers (required by the 128-byte swizzle)
     unsigned char *base = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -117,7 +127,7 @@ __global__ void __launch_bounds__(128, 1)
         }
     } else if (warp == 1 && lane == 0) {
         // MMA issuer
-        constexpr uint32_t idesc = idesc_tf32(TC_BM, TC_BN);
+        constexpr uint32_t idesc = idesc_tc(BF16, TC_BM, TC_BN);
         int issued = 0;
         for (int kb = 0; kb < nk; ++kb) {
             const int s = kb % TC_STAGES;
@@ -129,15 +139,23 @@ __global__ void __launch_bounds__(128, 1)
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const uint32_t a0 = smem_u32(sA + s * TC_TILE_BYTES), b0 = smem_u32(sB + s * TC_TILE_BYTES);
 #pragma unroll
-            for (int kk = 0; kk < TC_BK / 8; ++kk) {  // K = 8 TF32 = 32 bytes per instruction
+            for (int kk = 0; kk < 4; ++kk) {  // 32 bytes of K per instruction (8 TF32 or 16 bf16)
                 const uint64_t ad = smem_desc_sw128(a0 + kk * 32), bd = smem_desc_sw128(b0 + kk * 32);
                 const uint32_t acc = (kb > 0 || kk > 0) ? 1u : 0u;
-                asm volatile(
-                    "{\n\t.reg .pred p;\n\t"
-                    "setp.ne.u32 p, %4, 0;\n\t"
-                    "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
-                    "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
-                    : "memory");
+                if (BF16)
+                    asm volatile(
+                        "{\n\t.reg .pred p;\n\t"
+                        "setp.ne.u32 p, %4, 0;\n\t"
+                        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+                        "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+                        : "memory");
+                else
+                    asm volatile(
+                        "{\n\t.reg .pred p;\n\t"
+                        "setp.ne.u32 p, %4, 0;\n\t"
+                        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+                        "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+                        : "memory");
             }
             // release the stage once these MMAs have read it
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
@@ -214,62 +232,86 @@ __global__ void __launch_bounds__(128, 1)
 using tcu::EncodeFn;
 using tcu::encode_fn;
 
-// K-major operand tiles (TC_BK x TC_BM, 128-byte swizzle) or the plain C tile
-// (TC_BN x TC_BM, no swizzle); out-of-range elements read as zero.
-bool make_map(CUtensorMap *map, const float *ptr, int rows, int cols, int ld, bool ctile) {
+// K-major operand tiles (one 128-byte swizzled row of K per tile row: 32 fp32 or 64
+// bf16) or the plain fp32 C tile (TC_BN x TC_BM, no swizzle); out-of-range elements read
+// as zero.
+bool make_map(CUtensorMap *map, const void *ptr, int rows, int cols, int ld, bool ctile, bool bf16) {
     EncodeFn enc = encode_fn();
     if (!enc) return false;
+    const size_t es = bf16 ? 2 : 4;
     const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
-    const cuuint64_t strides[1] = {(cuuint64_t)ld * sizeof(float)};
-    const cuuint32_t box[2] = {ctile ? (cuuint32_t)TC_BN : (cuuint32_t)TC_BK, (cuuint32_t)TC_BM};
+    const cuuint64_t strides[1] = {(cuuint64_t)ld * es};
+    const cuuint32_t box[2] = {ctile ? (cuuint32_t)TC_BN : (cuuint32_t)(TC_ROW_BYTES / es), (cuuint32_t)TC_BM};
     const cuuint32_t estr[2] = {1, 1};
-    return enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void *)ptr, dims, strides, box, estr,
-               CU_TENSOR_MAP_INTERLEAVE_NONE, ctile ? CU_TENSOR_MAP_SWIZZLE_NONE : CU_TENSOR_MAP_SWIZZLE_128B,
-               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+    return enc(map, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void *)ptr, dims,
+               strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+               ctile ? CU_TENSOR_MAP_SWIZZLE_NONE : CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+template <bool BF16>
+cudaError_t tc_gemm_sub(int M, int N, int K, const void *A, int lda, const void *B, int ldb, float *C, int ldc,
+                        int *err_flag, cudaStream_t st) {
+    CUtensorMap ma, mb, mc;
+    if (!make_map(&ma, A, M, K, lda, false, BF16) || !make_map(&mb, B, N, K, ldb, false, BF16) ||
+        !make_map(&mc, C, M, N, ldc, true, false))
+        return cudaErrorInvalidValue;
+    static std::once_flag once;
+    static cudaError_t attr = cudaSuccess;
+    std::call_once(once, [] {
+        attr = cudaFuncSetAttribute(tc_gemm_kernel<BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
+    });
+    if (attr != cudaSuccess) return attr;
+    dim3 grid((N + TC_BN - 1) / TC_BN, (M + TC_BM - 1) / TC_BM, 1);
+    tc_gemm_kernel<BF16><<<grid, 128, TC_SMEM, st>>>(ma, mb, mc, M, N, K, C, ldc, err_flag);
+    return cudaGetLastError();
+}
+
+int run_hook(bool bf16, int M, int N, int K, const void *A, int lda, const void *B, int ldb, float *C, int ldc) {
+    if (!tc_gemm_supported(M, N, K, A, lda, B, ldb, C, ldc, bf16)) return 1;
+    int *flag = nullptr;
+    if (cudaMalloc(&flag, sizeof(int)) != cudaSuccess) return 1;
+    cudaMemset(flag, 0, sizeof(int));
+    cudaError_t e = bf16 ? tc_gemm_sub<true>(M, N, K, A, lda, B, ldb, C, ldc, flag, 0)
+                         : tc_gemm_sub<false>(M, N, K, A, lda, B, ldb, C, ldc, flag, 0);
+    int h = 0;
+    if (e == cudaSuccess) e = cudaMemcpy(&h, flag, sizeof(int), cudaMemcpyDeviceToHost);
+    cudaFree(flag);
+    if (e != cudaSuccess) return 1;
+    return h ? 2 : 0;
 }
 
 }  // namespace
 
-bool tc_gemm_supported(int M, int N, int K, const void *A, int lda, const void *B, int ldb, const void *C, int ldc) {
+bool tc_gemm_supported(int M, int N, int K, const void *A, int lda, const void *B, int ldb, const void *C, int ldc,
+                       bool bf16) {
     if (M < 1 || N < 1 || K < 1) return false;
-    if ((lda % 4) || (ldb % 4) || (ldc % 4) || ((uintptr_t)A % 16) || ((uintptr_t)B % 16) || ((uintptr_t)C % 16))
+    const int q = bf16 ? 8 : 4;  // operand rows a multiple of 16 bytes
+    if ((lda % q) || (ldb % q) || (ldc % 4) || ((uintptr_t)A % 16) || ((uintptr_t)B % 16) || ((uintptr_t)C % 16))
         return false;
     return encode_fn() != nullptr;
 }
 
 cudaError_t tc_gemm_tf32_sub(int M, int N, int K, const float *A, int lda, const float *B, int ldb, float *C, int ldc,
                              int *err_flag, cudaStream_t st) {
-    CUtensorMap ma, mb, mc;
-    if (!make_map(&ma, A, M, K, lda, false) || !make_map(&mb, B, N, K, ldb, false) ||
-        !make_map(&mc, C, M, N, ldc, true))
-        return cudaErrorInvalidValue;
-    static std::once_flag once;
-    static cudaError_t attr = cudaSuccess;
-    std::call_once(once, [] {
-        attr = cudaFuncSetAttribute(tc_gemm_tf32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
-    });
-    if (attr != cudaSuccess) return attr;
-    dim3 grid((N + TC_BN - 1) / TC_BN, (M + TC_BM - 1) / TC_BM, 1);
-    tc_gemm_tf32_kernel<<<grid, 128, TC_SMEM, st>>>(ma, mb, mc, M, N, K, C, ldc, err_flag);
-    return cudaGetLastError();
+    return tc_gemm_sub<false>(M, N, K, A, lda, B, ldb, C, ldc, err_flag, st);
+}
+
+cudaError_t tc_gemm_bf16_sub(int M, int N, int K, const uint16_t *A, int lda, const uint16_t *B, int ldb, float *C,
+                             int ldc, int *err_flag, cudaStream_t st) {
+    return tc_gemm_sub<true>(M, N, K, A, lda, B, ldb, C, ldc, err_flag, st);
 }
 
 }  // namespace expm
 
-// Test hook (not part of the documented interface): C -= A B^T with the tensor-core
-// kernel on device buffers; returns 0, or 1 for unsupported arguments / CUDA errors,
-// or 2 when a bounded wait gave up.
+// Test hooks (not part of the documented interface): C -= A B^T with the tensor-core
+// kernel on device buffers (fp32 operands read as TF32, or bf16 operands); return 0, or
+// 1 for unsupported arguments / CUDA errors, or 2 when a bounded wait gave up.
 extern "C" int expm_internal_tc_gemm_tf32(int M, int N, int K, const float *A, int lda, const float *B, int ldb,
                                           float *C, int ldc) {
-    using namespace expm;
-    if (!tc_gemm_supported(M, N, K, A, lda, B, ldb, C, ldc)) return 1;
-    int *flag = nullptr;
-    if (cudaMalloc(&flag, sizeof(int)) != cudaSuccess) return 1;
-    cudaMemset(flag, 0, sizeof(int));
-    cudaError_t e = tc_gemm_tf32_sub(M, N, K, A, lda, B, ldb, C, ldc, flag, 0);
-    int h = 0;
-    if (e == cudaSuccess) e = cudaMemcpy(&h, flag, sizeof(int), cudaMemcpyDeviceToHost);
-    cudaFree(flag);
-    if (e != cudaSuccess) return 1;
-    return h ? 2 : 0;
+    return expm::run_hook(false, M, N, K, A, lda, B, ldb, C, ldc);
+}
+extern "C" int expm_internal_tc_gemm_bf16(int M, int N, int K, const uint16_t *A, int lda, const uint16_t *B, int ldb,
+                                          float *C, int ldc) {
+    return expm::run_hook(true, M, N, K, A, lda, B, ldb, C, ldc);
 }

@@ -1,14 +1,20 @@
-// tc_gemm.cuh -- tensor-core (tcgen05, kind::tf32) update C -= A B^T.
+// tc_gemm.cuh -- tensor-core (tcgen05) update C -= A B^T, operands TF32 (kind::tf32) or
+// bf16 (kind::f16), fp32 accumulation.
 #pragma once
 #include <cuda_runtime.h>
+#include <stdint.h>
 
 namespace expm {
 
-// A: M x K, B: N x K (both K-major, fp32 read as TF32), C: M x N fp32 row-major.
-// Leading dimensions must be multiples of 4 floats and A, B, C 16-byte aligned (TMA rules).
-bool tc_gemm_supported(int M, int N, int K, const void *A, int lda, const void *B, int ldb, const void *C, int ldc);
+// A: M x K, B: N x K (both K-major: fp32 read as TF32, or bf16), C: M x N fp32 row-major.
+// Operand leading dimensions must be multiples of 16 bytes (4 floats / 8 bf16), C's of 4
+// floats, and A, B, C 16-byte aligned (TMA rules).
+bool tc_gemm_supported(int M, int N, int K, const void *A, int lda, const void *B, int ldb, const void *C, int ldc,
+                       bool bf16 = false);
 // err_flag (device int) is set to 1 if a bounded wait inside the kernel gave up.
 cudaError_t tc_gemm_tf32_sub(int M, int N, int K, const float *A, int lda, const float *B, int ldb, float *C, int ldc,
                              int *err_flag, cudaStream_t st);
+cudaError_t tc_gemm_bf16_sub(int M, int N, int K, const uint16_t *A, int lda, const uint16_t *B, int ldb, float *C,
+                             int ldc, int *err_flag, cudaStream_t st);
 
 }  // namespace expm

@@ -62,7 +62,7 @@ def test_dense_small_workload(plans):
     assert 0 < info.growth_max_seen < 1e3
 
 
-@pytest.mark.parametrize("prec", [P.EXPM_FP64, P.EXPM_MIXED_FP32, P.EXPM_MIXED_TF32X3])
+@pytest.mark.parametrize("prec", [P.EXPM_FP64, P.EXPM_MIXED_FP32, P.EXPM_MIXED_TF32X3, P.EXPM_MIXED_BF16X3])
 @pytest.mark.parametrize("n,k,deg", [(1, 1, 12), (5, 2, 16), (63, 3, 12), (64, 1, 16), (65, 5, 12),
                                      (130, 70, 16), (257, 4, 12), (333, 9, 16)])
 def test_complex_hermitian(plans, prec, n, k, deg):
@@ -99,7 +99,7 @@ def test_time_and_shift(plans):
     assert matrix.rel_err(Y, _oracle(A, V, 16, t=0.5, c=10.0)) <= 1e-12
 
 
-@pytest.mark.parametrize("prec", [P.EXPM_MIXED_FP32, P.EXPM_MIXED_TF32X3])
+@pytest.mark.parametrize("prec", [P.EXPM_MIXED_FP32, P.EXPM_MIXED_TF32X3, P.EXPM_MIXED_BF16X3])
 def test_mixed_matches_fp64_path(plans, prec):
     """Mid-size complex Hermitian: the refined mixed paths agree with the binary64 path."""
     g = workloads.rng(312)
@@ -160,6 +160,28 @@ def test_tensor_core_gemm_against_torch():
         torch.cuda.synchronize()
         tf = lambda x: (x.view(torch.int32) & ~0x1FFF).view(torch.float32).double()
         ref = C0.double() - tf(A) @ tf(B).T
+        err = (C.double() - ref).abs().max().item() / ref.abs().max().item()
+        assert err < 1e-5, (M, N, K, err)
+
+
+def test_tensor_core_gemm_bf16_against_torch():
+    """The tcgen05 kind::f16 kernel with bf16 operands: C -= A B^T equals the product of
+    the bf16 operands (exact in binary32 per term; float64 reference) to fp32
+    accumulation accuracy, on ragged tile edges."""
+    import ctypes
+    f = P.lib.expm_internal_tc_gemm_bf16
+    f.restype = ctypes.c_int
+    f.argtypes = [ctypes.c_int] * 3 + [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_int,
+                                       ctypes.c_void_p, ctypes.c_int]
+    gen = torch.Generator(device="cpu").manual_seed(8)
+    for M, N, K in [(128, 128, 64), (200, 72, 96), (1000, 520, 768), (129, 260, 40)]:
+        A = torch.randn(M, K, generator=gen).to(torch.bfloat16).to(DEV)
+        B = torch.randn(N, K, generator=gen).to(torch.bfloat16).to(DEV)
+        C = torch.randn(M, N, generator=gen).to(DEV)
+        C0 = C.clone()
+        assert f(M, N, K, A.data_ptr(), K, B.data_ptr(), K, C.data_ptr(), N) == 0
+        torch.cuda.synchronize()
+        ref = C0.double() - A.double() @ B.double().T
         err = (C.double() - ref).abs().max().item() / ref.abs().max().item()
         assert err < 1e-5, (M, N, K, err)
 

@@ -90,7 +90,7 @@ def test_shift_method_positive_spectrum(plans):
     assert np.linalg.norm(Y - E, 2) <= np.exp(20.0) * 2.0 ** -16 * 1.0001
 
 
-@pytest.mark.parametrize("prec", [P.EXPM_MIXED_FP32, P.EXPM_MIXED_TF32X3])
+@pytest.mark.parametrize("prec", [P.EXPM_MIXED_FP32, P.EXPM_MIXED_TF32X3, P.EXPM_MIXED_BF16X3])
 def test_full_matrix_mixed(plans, prec):
     A, Q, mu, _ = workloads.dense_symmetric(600, -40.0, 0.0, 1, workloads.rng(814), True)
     Y, info = _full(plans[16], A, prec=prec)

@@ -30,14 +30,17 @@ def test_dense_hermitian_4096():
     ref = matrix.eig_apply(w["Q"], w["mu"], w["V"], lambda m: scalar.R_n(m, 16))
     plan = P.Plan(degree=16)
     A, V = (torch.from_numpy(x).to(DEV) for x in (w["A"], w["V"]))
-    Y64, Ymx, Ytc = torch.empty_like(V), torch.empty_like(V), torch.empty_like(V)
+    Y64, Ymx, Ytc, Ybf = (torch.empty_like(V) for _ in range(4))
     P.expm_apply_dense(plan, A, V, Y64, prec=P.EXPM_FP64)
     info = P.expm_apply_dense(plan, A, V, Ymx, prec=P.EXPM_MIXED_FP32)
     itc = P.expm_apply_dense(plan, A, V, Ytc, prec=P.EXPM_MIXED_TF32X3)
+    ibf = P.expm_apply_dense(plan, A, V, Ybf, prec=P.EXPM_MIXED_BF16X3)
     torch.cuda.synchronize()
-    y64, ymx, ytc = Y64.cpu().numpy(), Ymx.cpu().numpy(), Ytc.cpu().numpy()
+    y64, ymx, ytc, ybf = Y64.cpu().numpy(), Ymx.cpu().numpy(), Ytc.cpu().numpy(), Ybf.cpu().numpy()
     e64, emx, etc = matrix.rel_err(y64, ref), matrix.rel_err(ymx, ref), matrix.rel_err(ytc, ref)
     d, dtc = matrix.rel_err(ymx, y64), matrix.rel_err(ytc, y64)
+    assert matrix.rel_err(ybf, ref) <= 1e-10 and matrix.rel_err(ybf, y64) <= 1e-10
+    assert ibf.status_worst == 0 and ibf.refine_iters_max >= 1
     print(f"dense 4096: fp64 {e64:.3e}, mixed {emx:.3e} ({info.refine_iters_max} sweeps), "
           f"tf32x3 {etc:.3e} ({itc.refine_iters_max} sweeps), vs fp64 {d:.3e} / {dtc:.3e}")
     assert e64 <= 1e-12 and emx <= 1e-10 and d <= 1e-10 and etc <= 1e-10 and dtc <= 1e-10
