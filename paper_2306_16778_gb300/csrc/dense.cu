@@ -314,11 +314,121 @@ struct TcScratch {
     bool bf16 = false;
 };
 
+constexpr int DN_PNB = 4 * DN_NB;  // outer panel of the tensor-core LU
+
+// Binary32 LU with the trailing updates on the tensor cores (bf16x3), in 256-column outer panels:
+// inside a panel, 64-column steps (diagonal LU, L21 for every row below, U12 and the
+// update restricted to the panel's columns, on the CUDA cores); then the panel's row
+// block to the right, U12 = L11^{-1} A12, by the same 64-row steps, and one trailing
+// update A22 -= L21 U12 with K = 256 complex on the tensor cores -- a 128 x 128 C tile
+// is read and written once per 256 columns instead of once per 64, which bounds these
+// updates (the tile traffic, not the tensor pipe).
+static cudaError_t lu_panels_tc(int n, int batch, cx<float> *F, cudaStream_t st, Profiler &prof,
+                                const TcScratch *tc) {
+    const int64_t bs = (int64_t)n * n;
+    const size_t sm1 = tri_smem_bytes<float>(), sm2 = 2 * tri_smem_bytes<float>();
+    EXPM_TRY(set_smem(lu_diag<float>, sm1));
+    EXPM_TRY(set_smem(trsm_left<float, true, true, false>, sm2));
+    EXPM_TRY(set_smem(trsm_right_upper<float>, sm2));
+    const cx<float> mone = {-1.f, 0.f};
+    for (int p0 = 0; p0 < n; p0 += DN_PNB) {
+        const int pe = std::min(n, p0 + DN_PNB), pw = pe - p0;
+        for (int p = p0; p < pe; p += DN_NB) {
+            const int nb = std::min(DN_NB, pe - p);
+            const int below = n - p - nb, inpanel = pe - p - nb;
+            cx<float> *diag = F + (int64_t)p * n + p;
+            EXPM_TRY(prof.timed("lu_diag<f32>", st, [&] {
+                lu_diag<float><<<dim3(1, 1, batch), 256, sm1, st>>>(nb, diag, n, bs);
+                return cudaGetLastError();
+            }));
+            if (below <= 0) break;
+            EXPM_TRY(prof.timed("trsm_panels<f32>", st, [&] {
+                trsm_right_upper<float><<<dim3((below + 63) / 64, 1, batch), 64, sm2, st>>>(
+                    nb, below, diag, n, bs, diag + (int64_t)nb * n, n, bs);
+                if (inpanel > 0)
+                    trsm_left<float, true, true, false><<<dim3((inpanel + 63) / 64, 1, batch), 64, sm2, st>>>(
+                        nb, inpanel, diag, n, bs, diag + nb, n, bs);
+                return cudaGetLastError();
+            }));
+            if (inpanel > 0)
+                EXPM_TRY(prof.timed("cgemm_update<f32>", st, [&] {
+                    cgemm_launch<float, cx<float>, false, false>(below, inpanel, nb, mone, 1.f, diag + (int64_t)nb * n,
+                                                                 n, bs, diag + nb, n, bs, diag + (int64_t)nb * n + nb,
+                                                                 n, bs, 1, batch, st);
+                    return cudaGetLastError();
+                }));
+        }
+        const int right = n - pe;
+        if (right <= 0) continue;
+        for (int p = p0; p < pe; p += DN_NB) {  // U12 = L11^{-1} A12 for the panel's rows
+            const int nb = std::min(DN_NB, pe - p);
+            cx<float> *diag = F + (int64_t)p * n + p;
+            cx<float> *a12 = F + (int64_t)p * n + pe;
+            EXPM_TRY(prof.timed("trsm_panels<f32>", st, [&] {
+                trsm_left<float, true, true, false><<<dim3((right + 63) / 64, 1, batch), 64, sm2, st>>>(
+                    nb, right, diag, n, bs, a12, n, bs);
+                return cudaGetLastError();
+            }));
+            if (pe - p - nb > 0)
+                EXPM_TRY(prof.timed("cgemm_update<f32>", st, [&] {
+                    cgemm_launch<float, cx<float>, false, false>(pe - p - nb, right, nb, mone, 1.f,
+                                                                 diag + (int64_t)nb * n, n, bs, a12, n, bs,
+                                                                 a12 + (int64_t)nb * n, n, bs, 1, batch, st);
+                    return cudaGetLastError();
+                }));
+        }
+        // A22 -= L21 U12 (K = pw complex) on the tensor cores, one real product per matrix
+        cx<float> *pdiag = F + (int64_t)p0 * n + p0;
+        float *C0 = reinterpret_cast<float *>(F + (int64_t)pe * n + pe);
+        const int kr = (tc->bf16 ? 12 : 6) * pw;  // real K of the split product
+        if (!tc_gemm_supported(right, 2 * right, kr, tc->Ap, kr, tc->Bp, kr, C0, 2 * n, tc->bf16)) {
+            EXPM_TRY(prof.timed("cgemm_update<f32>", st, [&] {
+                cgemm_launch<float, cx<float>, false, false>(right, right, pw, mone, 1.f, pdiag + (int64_t)pw * n, n,
+                                                             bs, pdiag + pw, n, bs, pdiag + (int64_t)pw * n + pw, n,
+                                                             bs, 1, batch, st);
+                return cudaGetLastError();
+            }));
+            continue;
+        }
+        EXPM_TRY(prof.timed("split_tc_operands", st, [&] {
+            if (tc->bf16)
+                split_tc_operands_bf16<<<dim3(grid1d((int64_t)right * pw), 1, batch), 256, 0, st>>>(
+                    right, pw, pdiag, n, bs, reinterpret_cast<uint16_t *>(tc->Ap), reinterpret_cast<uint16_t *>(tc->Bp));
+            else
+                split_tc_operands<<<dim3(grid1d((int64_t)right * pw), 1, batch), 256, 0, st>>>(right, pw, pdiag, n, bs,
+                                                                                             tc->Ap, tc->Bp);
+            return cudaGetLastError();
+        }));
+        EXPM_TRY(prof.timed(tc->bf16 ? "tc_gemm_bf16x3" : "tc_gemm_tf32x3", st, [&]() -> cudaError_t {
+            for (int z = 0; z < batch; ++z) {
+                float *Cz = reinterpret_cast<float *>(F + (int64_t)z * bs + (int64_t)pe * n + pe);
+                cudaError_t e;
+                if (tc->bf16) {
+                    const uint16_t *Ab = reinterpret_cast<const uint16_t *>(tc->Ap) + (int64_t)z * right * kr;
+                    const uint16_t *Bb = reinterpret_cast<const uint16_t *>(tc->Bp) + (int64_t)z * 2 * right * kr;
+                    e = tc_gemm_bf16_sub(right, 2 * right, kr, Ab, kr, Bb, kr, Cz, 2 * n, tc->err, st);
+                } else {
+                    e = tc_gemm_tf32_sub(right, 2 * right, kr, tc->Ap + (int64_t)z * right * kr, kr,
+                                         tc->Bp + (int64_t)z * 2 * right * kr, kr, Cz, 2 * n, tc->err, st);
+                }
+                if (e != cudaSuccess) return e;
+            }
+            return cudaSuccess;
+        }));
+    }
+    return cudaSuccess;
+}
+
 // Unpivoted blocked LU of `batch` n x n matrices F (ld n, batch stride n*n).  With
 // tc (binary32 only) the trailing updates run on the tensor cores.
 template <class T>
 static cudaError_t lu_blocked(int n, int batch, cx<T> *F, cudaStream_t st, Profiler &prof,
                               const TcScratch *tc = nullptr) {
+    // bf16x3 only: with 3xTF32 (twice the truncated accumulation steps per unit of K, 22
+    // split bits instead of 24) the K = 256 updates cost a second refinement sweep
+    // (measured), so 3xTF32 keeps the rank-64 updates
+    if constexpr (std::is_same<T, float>::value)
+        if (tc != nullptr && tc->bf16 && n > DN_PNB) return lu_panels_tc(n, batch, F, st, prof, tc);
     const int64_t bs = (int64_t)n * n;
     const size_t sm1 = tri_smem_bytes<T>(), sm2 = 2 * tri_smem_bytes<T>();
     EXPM_TRY(set_smem(lu_diag<T>, sm1));
@@ -504,8 +614,9 @@ static DenseLayout dense_layout(const DenseGeom &g) {
     L.F = off; off += align_up(npz * nn * (g.mixed ? sizeof(cx<float>) : sizeof(cx<double>)));
     L.tcA = L.tcB = L.tcflag = off;
     if (g.mixed && g.tc) {  // trailing-update operands for the largest step (rest < n)
-        L.tcA = off; off += align_up(npz * (size_t)g.n * 6 * DN_NB * sizeof(float));
-        L.tcB = off; off += align_up(npz * (size_t)g.n * 2 * 6 * DN_NB * sizeof(float));
+        const size_t kw = g.tc == 2 ? DN_PNB : DN_NB;  // bf16x3: 256-column panels
+        L.tcA = off; off += align_up(npz * (size_t)g.n * 6 * kw * sizeof(float));
+        L.tcB = off; off += align_up(npz * (size_t)g.n * 2 * 6 * kw * sizeof(float));
         L.tcflag = off; off += align_up(sizeof(int));
     }
     L.factor_total = off;
