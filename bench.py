@@ -64,6 +64,16 @@ def _hbm_peak() -> float:
 
 
 HBM_GBS = _hbm_peak()
+
+
+def _bf16_peak() -> tuple:
+    """Measured dense bf16 TFLOP/s (burst, sustained) from MEASURED_PEAKS.json, else the fallback."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["bf16_tflops"]), float(d["bf16_tflops_sustained"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 1900.0, 1700.0, "fallback"
 # the binary32 + refinement path: one correction pass at most, stopping test 1e-10
 MIXED_OPTS = dict(tol=1e-10, max_refine=1)
 # algorithmic HBM bytes of one evaluation: d, e, V read, Y written (binary64)
@@ -455,6 +465,30 @@ def run_dense(args):
         Ys[name] = Y.clone()
         out[name] = {"s_per_eval": round(statistics.median(ts), 5), "evals_per_s": round(1 / statistics.median(ts), 4),
                      "kernels_ms_total": {k: round(v[1], 3) for k, v in prof.items()}}
+    # tensor-pipe rooflines of the two tensor-core kernels of the bf16x3 step (algorithmic
+    # bf16 flops of the split products / their CUDA-event time; the kernels run inside a
+    # long step, so the sustained peak is the denominator)
+    n, kc, nsys = args.dense_n, 256, 16
+    burst, sustained, src = _bf16_peak()
+    prof = out["mixed_bf16x3"]["kernels_ms_total"]
+    sweeps = out["mixed_bf16x3"]["refine_sweeps"]
+    steps = max(1, args.steps)
+    if "oz_gemm" in prof:
+        # 28 slice products of the real product (n x 2n) (2n x 2 nsys kc), two launches per sweep
+        fl = 2.0 * 28 * n * (2 * n) * (2 * nsys * kc) * (sweeps + 1) * steps
+        tf = fl / (prof["oz_gemm"] * 1e-3) / 1e12
+        out["roofline_oz_gemm"] = {"kernel": "oz_gemm_kernel", "bound": "tensor", "achieved": round(tf, 1),
+                                   "peak": sustained, "unit": "TFLOP/s", "frac": round(tf / sustained, 4),
+                                   "peak_source": f"{src} bf16 sustained",
+                                   "algorithmic": "2 x 28 slice products x n x 2n x (2 x 16 systems x 256 columns)"}
+    if "tc_gemm_bf16x3" in prof:
+        # trailing updates of the 256-column panels: 8 pairs, real (right) x (2 right) x (12 x 256)
+        fl = sum(2.0 * 8 * r * (2 * r) * (12 * 256) for r in range(n - 256, 0, -256)) * steps
+        tf = fl / (prof["tc_gemm_bf16x3"] * 1e-3) / 1e12
+        out["roofline_tc_lu"] = {"kernel": "tc_gemm_kernel<bf16>", "bound": "tensor", "achieved": round(tf, 1),
+                                 "peak": sustained, "unit": "TFLOP/s", "frac": round(tf / sustained, 4),
+                                 "peak_source": f"{src} bf16 sustained",
+                                 "algorithmic": "sum over panels of 8 pairs x 2 x right x 2 right x 12 x 256"}
     for name in ("mixed", "mixed_tc", "mixed_bf16x3", "reduced", "reduced_mixed"):
         d = (Ys[name] - Ys["fp64"]).abs().pow(2).sum().sqrt() / Ys["fp64"].abs().pow(2).sum().sqrt()
         out[f"{name}_vs_fp64_rel"] = float(d)

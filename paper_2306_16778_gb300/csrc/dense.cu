@@ -290,6 +290,60 @@ __global__ void split_tc_operands_bf16(int rest, int nb, const cx<float> *__rest
     }
 }
 
+// Operands of a triangular-solve update X[r0 .. r0+m) -= op(F)[r0.., k0 .. k0+K) X[k0 .. k0+K)
+// on the tensor cores with the bf16x3 split (same segment order as above).  A' rows
+// i < m: op(F) = F (conj = false) or the conjugate transpose of F (conj = true: entry
+// (i, k) is conj F[k0+k][r0+i]), K-major, 12 K bf16 per row; batch z at Ap + z m 12K.
+__global__ void split_solve_a_bf16(int m, int K, const cx<float> *__restrict__ F, int n, int64_t fstride, int r0,
+                                   int k0, int conj, uint16_t *__restrict__ Ap) {
+    const int z = blockIdx.z;
+    const cx<float> *f = F + (int64_t)z * fstride;
+    const int K12 = 12 * K;
+    const int64_t na = (int64_t)m * K;
+    // consecutive threads write consecutive (re, im) pairs of a row (one 4-byte store per
+    // segment); the transposed reads of the conjugate case are the strided side
+    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < na; idx += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(idx / K), k = (int)(idx % K);
+        cx<float> a = conj ? f[(int64_t)(k0 + k) * n + r0 + i] : f[(int64_t)(r0 + i) * n + k0 + k];
+        if (conj) a.im = -a.im;
+        uint16_t rh, rm, rl, ih, im, il;
+        bf16x3(a.re, rh, rm, rl);
+        bf16x3(a.im, ih, im, il);
+        uint32_t *row = reinterpret_cast<uint32_t *>(Ap + ((int64_t)z * m + i) * K12 + 2 * k);
+        const uint16_t segr[6] = {rl, rm, rh, rm, rh, rh}, segi[6] = {il, im, ih, im, ih, ih};
+#pragma unroll
+        for (int q = 0; q < 6; ++q) row[q * K] = (uint32_t)segr[q] | ((uint32_t)segi[q] << 16);
+    }
+}
+
+// B' of that update from X rows k0 .. k0+K (kc complex columns, batch stride xstride):
+// row 2c (real output): (Re x, -Im x), row 2c+1 (imaginary output): (Im x, Re x); batch z
+// at Bp + z 2kc 12K.
+__global__ void split_solve_b_bf16(int K, int kc, const cx<float> *__restrict__ X, int64_t xstride, int k0,
+                                   uint16_t *__restrict__ Bp) {
+    const int z = blockIdx.z;
+    const cx<float> *x = X + (int64_t)z * xstride;
+    const int K12 = 12 * K;
+    const int64_t na = (int64_t)K * kc;
+    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < na; idx += (int64_t)gridDim.x * blockDim.x) {
+        const int c = (int)(idx / K), k = (int)(idx % K);  // consecutive threads: consecutive k of a row
+        const cx<float> u = x[(int64_t)(k0 + k) * kc + c];
+        uint16_t uh, um, ul, vh, vm, vl, wh, wm, wl;
+        bf16x3(u.re, uh, um, ul);
+        bf16x3(-u.im, vh, vm, vl);
+        bf16x3(u.im, wh, wm, wl);
+        uint32_t *r0 = reinterpret_cast<uint32_t *>(Bp + ((int64_t)z * 2 * kc + 2 * c) * K12 + 2 * k);
+        uint32_t *r1 = r0 + K12 / 2;
+        const uint16_t s0r[6] = {uh, um, ul, uh, um, uh}, s0i[6] = {vh, vm, vl, vh, vm, vh};
+        const uint16_t s1r[6] = {wh, wm, wl, wh, wm, wh}, s1i[6] = {uh, um, ul, uh, um, uh};
+#pragma unroll
+        for (int q = 0; q < 6; ++q) {
+            r0[q * K] = (uint32_t)s0r[q] | ((uint32_t)s0i[q] << 16);
+            r1[q * K] = (uint32_t)s1r[q] | ((uint32_t)s1i[q] << 16);
+        }
+    }
+}
+
 // ------------------------------------------------------------------ host helpers
 
 static unsigned grid1d(int64_t total, int threads = 256) {
@@ -315,6 +369,23 @@ struct TcScratch {
 };
 
 constexpr int DN_PNB = 4 * DN_NB;  // outer panel of the tensor-core LU
+
+// C_z -= A_z B_z^T for z < batch (A_z: M x K, B_z: N x K, K-major with ld K; batch
+// strides in elements) on the tensor cores: one launch when the strides meet the TMA
+// rules, else one launch per product.
+static cudaError_t tc_update(bool bf16, int M, int N, int K, const void *A, int64_t sA, const void *B, int64_t sB,
+                             float *C, int ldc, int64_t sC, int batch, int *err, cudaStream_t st) {
+    if (tc_gemm_supported(M, N, K, A, K, B, K, C, ldc, bf16, sA, sB, sC))
+        return tc_gemm_batched(bf16, M, N, K, A, K, sA, B, K, sB, C, ldc, sC, batch, err, st);
+    const size_t es = bf16 ? 2 : 4;
+    for (int z = 0; z < batch; ++z) {
+        const void *Az = (const unsigned char *)A + (size_t)z * sA * es;
+        const void *Bz = (const unsigned char *)B + (size_t)z * sB * es;
+        cudaError_t e = tc_gemm_batched(bf16, M, N, K, Az, K, 0, Bz, K, 0, C + (int64_t)z * sC, ldc, 0, 1, err, st);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
 
 // Binary32 LU with the trailing updates on the tensor cores (bf16x3), in 256-column outer panels:
 // inside a panel, 64-column steps (diagonal LU, L21 for every row below, U12 and the
@@ -399,21 +470,9 @@ static cudaError_t lu_panels_tc(int n, int batch, cx<float> *F, cudaStream_t st,
                                                                                              tc->Ap, tc->Bp);
             return cudaGetLastError();
         }));
-        EXPM_TRY(prof.timed(tc->bf16 ? "tc_gemm_bf16x3" : "tc_gemm_tf32x3", st, [&]() -> cudaError_t {
-            for (int z = 0; z < batch; ++z) {
-                float *Cz = reinterpret_cast<float *>(F + (int64_t)z * bs + (int64_t)pe * n + pe);
-                cudaError_t e;
-                if (tc->bf16) {
-                    const uint16_t *Ab = reinterpret_cast<const uint16_t *>(tc->Ap) + (int64_t)z * right * kr;
-                    const uint16_t *Bb = reinterpret_cast<const uint16_t *>(tc->Bp) + (int64_t)z * 2 * right * kr;
-                    e = tc_gemm_bf16_sub(right, 2 * right, kr, Ab, kr, Bb, kr, Cz, 2 * n, tc->err, st);
-                } else {
-                    e = tc_gemm_tf32_sub(right, 2 * right, kr, tc->Ap + (int64_t)z * right * kr, kr,
-                                         tc->Bp + (int64_t)z * 2 * right * kr, kr, Cz, 2 * n, tc->err, st);
-                }
-                if (e != cudaSuccess) return e;
-            }
-            return cudaSuccess;
+        EXPM_TRY(prof.timed(tc->bf16 ? "tc_gemm_bf16x3" : "tc_gemm_tf32x3", st, [&] {
+            return tc_update(tc->bf16, right, 2 * right, kr, tc->Ap, (int64_t)right * kr, tc->Bp,
+                             (int64_t)2 * right * kr, C0, 2 * n, 2 * bs, batch, tc->err, st);
         }));
     }
     return cudaSuccess;
@@ -463,15 +522,10 @@ static cudaError_t lu_blocked(int n, int batch, cx<T> *F, cudaStream_t st, Profi
                     rest, nb, reinterpret_cast<const cx<float> *>(diag), n, bs, Ab, Bb);
                 return cudaGetLastError();
             }));
-            EXPM_TRY(prof.timed("tc_gemm_bf16x3", st, [&]() -> cudaError_t {
-                for (int z = 0; z < batch; ++z) {
-                    float *Cz = reinterpret_cast<float *>(F + (int64_t)z * bs + (int64_t)(p + nb) * n + p + nb);
-                    cudaError_t e = tc_gemm_bf16_sub(rest, 2 * rest, 12 * nb, Ab + (int64_t)z * rest * 12 * nb,
-                                                     12 * nb, Bb + (int64_t)z * 2 * rest * 12 * nb, 12 * nb, Cz,
-                                                     2 * n, tc->err, st);
-                    if (e != cudaSuccess) return e;
-                }
-                return cudaSuccess;
+            EXPM_TRY(prof.timed("tc_gemm_bf16x3", st, [&] {
+                float *C0 = reinterpret_cast<float *>(F + (int64_t)(p + nb) * n + p + nb);
+                return tc_update(true, rest, 2 * rest, 12 * nb, Ab, (int64_t)rest * 12 * nb, Bb,
+                                 (int64_t)2 * rest * 12 * nb, C0, 2 * n, 2 * bs, batch, tc->err, st);
             }));
             continue;
         }
@@ -484,15 +538,10 @@ static cudaError_t lu_blocked(int n, int batch, cx<T> *F, cudaStream_t st, Profi
                     rest, nb, reinterpret_cast<const cx<float> *>(diag), n, bs, tc->Ap, tc->Bp);
                 return cudaGetLastError();
             }));
-            EXPM_TRY(prof.timed("tc_gemm_tf32x3", st, [&]() -> cudaError_t {
-                for (int z = 0; z < batch; ++z) {
-                    float *Cz = reinterpret_cast<float *>(F + (int64_t)z * bs + (int64_t)(p + nb) * n + p + nb);
-                    cudaError_t e = tc_gemm_tf32_sub(rest, 2 * rest, 6 * nb, tc->Ap + (int64_t)z * rest * 6 * nb,
-                                                     6 * nb, tc->Bp + (int64_t)z * 2 * rest * 6 * nb, 6 * nb, Cz,
-                                                     2 * n, tc->err, st);
-                    if (e != cudaSuccess) return e;
-                }
-                return cudaSuccess;
+            EXPM_TRY(prof.timed("tc_gemm_tf32x3", st, [&] {
+                float *C0 = reinterpret_cast<float *>(F + (int64_t)(p + nb) * n + p + nb);
+                return tc_update(false, rest, 2 * rest, 6 * nb, tc->Ap, (int64_t)rest * 6 * nb, tc->Bp,
+                                 (int64_t)2 * rest * 6 * nb, C0, 2 * n, 2 * bs, batch, tc->err, st);
             }));
             continue;
         }
@@ -507,13 +556,21 @@ static cudaError_t lu_blocked(int n, int batch, cx<T> *F, cudaStream_t st, Profi
     return cudaSuccess;
 }
 
+// Tensor-core scratch of the binary32 triangular solves (bf16x3 mode): the split operands
+// of one panel update for every batch entry, and the kernel's time-out flag.
+struct SolveTc {
+    uint16_t *Ap = nullptr, *Bp = nullptr;
+    int *err = nullptr;
+};
+
 // In-place solve of the kc columns of X[b] (n x kc) with the factors in F.
 // conj = false: L U x = b (forward unit-lower, back upper).
 // conj = true : U^H L^H x = b (forward with U^H, back with unit L^H).
 // Factor of system b is F[fidx[b]] -- systems of one pair share a factor.
 template <class T>
 static cudaError_t lu_solve(int n, int kc, int batch, const cx<T> *F, int64_t fstride, bool conj, cx<T> *X,
-                            int64_t xstride, cudaStream_t st, Profiler &prof, const int *skip = nullptr) {
+                            int64_t xstride, cudaStream_t st, Profiler &prof, const int *skip = nullptr,
+                            const SolveTc *tcs = nullptr) {
     const size_t smn = narrow_smem_bytes<T>(n, kc);
     if (kc <= 8 && smn <= (200u << 10)) {  // few right-hand sides: one fused kernel per batch entry
         // the attribute is a ceiling, set to the largest size used so that concurrent
@@ -562,6 +619,25 @@ static cudaError_t lu_solve(int n, int kc, int batch, const cx<T> *F, int64_t fs
             cgemm_launch<T, cx<T>, true, false>(m, kc, K, ones, T(1), F + (int64_t)k0 * n + r0, n, fstride, xk, kc,
                                                 xstride, xr, kc, xstride, 1, batch, st);
     };
+    // the K = 256 updates past a panel: on the tensor cores with the bf16x3 split when
+    // scratch is given (binary32 only) and the shapes meet the TMA rules, else as above
+    auto big_update = [&](int r0, int m, int k0, int K) -> cudaError_t {
+        if constexpr (std::is_same<T, float>::value) {
+            const int kr = 12 * K;
+            float *C0 = reinterpret_cast<float *>(X + (int64_t)r0 * kc);
+            if (tcs != nullptr && tc_gemm_supported(m, 2 * kc, kr, tcs->Ap, kr, tcs->Bp, kr, C0, 2 * kc, true)) {
+                split_solve_a_bf16<<<dim3(grid1d((int64_t)m * K), 1, batch), 256, 0, st>>>(
+                    m, K, F, n, fstride, r0, k0, conj ? 1 : 0, tcs->Ap);
+                split_solve_b_bf16<<<dim3(grid1d((int64_t)K * kc), 1, batch), 256, 0, st>>>(K, kc, X, xstride, k0,
+                                                                                         tcs->Bp);
+                EXPM_TRY(cudaGetLastError());
+                return tc_update(true, m, 2 * kc, kr, tcs->Ap, (int64_t)m * kr, tcs->Bp, (int64_t)2 * kc * kr, C0,
+                                 2 * kc, 2 * xstride, batch, tcs->err, st);
+            }
+        }
+        update(r0, m, k0, K);
+        return cudaGetLastError();
+    };
     // forward sweep (unit L, or U^H)
     for (int p0 = 0; p0 < n; p0 += PNB) {
         const int pe = std::min(n, p0 + PNB);
@@ -570,7 +646,7 @@ static cudaError_t lu_solve(int n, int kc, int batch, const cx<T> *F, int64_t fs
             trsm(p, nb, true);
             if (pe - p - nb > 0) update(p + nb, pe - p - nb, p, nb);
         }
-        if (n - pe > 0) update(pe, n - pe, p0, pe - p0);
+        if (n - pe > 0) EXPM_TRY(big_update(pe, n - pe, p0, pe - p0));
     }
     // backward sweep (U, or unit L^H), panels from the bottom
     for (int pe = n; pe > 0; pe -= PNB) {
@@ -581,7 +657,7 @@ static cudaError_t lu_solve(int n, int kc, int batch, const cx<T> *F, int64_t fs
             trsm(p, nb, false);
             if (p > p0) update(p0, p - p0, p, nb);
         }
-        if (p0 > 0) update(0, p0, p0, pe - p0);
+        if (p0 > 0) EXPM_TRY(big_update(0, p0, p0, pe - p0));
     }
     return cudaGetLastError();
 }
@@ -593,7 +669,7 @@ static cudaError_t lu_solve(int n, int kc, int batch, const cx<T> *F, int64_t fs
 // the poles and can be kept for later right-hand sides.
 struct DenseLayout {
     size_t amax, umax, F, tcA, tcB, tcflag, factor_total;  // factor part
-    size_t rn2, xn2, an2, ctl, X, R, D, oz, solve_total;  // solve part (offsets from its own base)
+    size_t rn2, xn2, an2, ctl, X, R, D, oz, stA, stB, sterr, solve_total;  // solve part (offsets from its own base)
 };
 static inline size_t align_up(size_t x) { return (x + 255) & ~size_t(255); }
 
@@ -603,6 +679,10 @@ static inline size_t align_up(size_t x) { return (x + 255) & ~size_t(255); }
 static bool dense_uses_oz(const DenseGeom &g) {
     return g.mixed && g.kc > 8 && g.ninst == 1 && oz_resid_supported(g.n, g.kc, g.nsys);
 }
+
+// Binary32 triangular solves with many columns in bf16x3 mode: panel updates on the
+// tensor cores.
+static bool dense_tc_solves(const DenseGeom &g) { return g.mixed && g.tc == 2 && g.kc > 8; }
 
 static DenseLayout dense_layout(const DenseGeom &g) {
     DenseLayout L{};
@@ -635,6 +715,13 @@ static DenseLayout dense_layout(const DenseGeom &g) {
     }
     L.oz = off;
     if (dense_uses_oz(g)) off += align_up(oz_resid_bytes(g.n, g.kc, g.nsys, g.complex_a));
+    L.stA = L.stB = L.sterr = off;
+    if (dense_tc_solves(g)) {  // two sets (the plain and the conjugate half run concurrently)
+        const size_t batch = (size_t)g.ninst * g.npairs, kr = 12 * DN_PNB;
+        L.stA = off; off += 2 * align_up(batch * (size_t)g.n * kr * sizeof(uint16_t));
+        L.stB = off; off += 2 * align_up(batch * 2 * (size_t)g.kc * kr * sizeof(uint16_t));
+        L.sterr = off; off += align_up(sizeof(int));
+    }
     L.solve_total = off;
     return L;
 }
@@ -689,20 +776,24 @@ static cudaStream_t aux_stream() {
 
 template <class T>
 static cudaError_t solve_systems(const DenseGeom &g, const cx<T> *F, cx<T> *X, int64_t xstride, cudaStream_t st,
-                                 Profiler &prof, const int *skip = nullptr) {
+                                 Profiler &prof, const int *skip = nullptr, const SolveTc *tcs = nullptr) {
     const int64_t fs = (int64_t)g.n * g.n;
     const int batch = g.ninst * g.npairs;
     const char *name = sizeof(T) == 8 ? "lu_solve<f64>" : "lu_solve<f32>";
     Profiler quiet;  // the inner launches are timed as a whole here
+    // tcs (optional): two scratch sets, one per concurrently running half
+    const SolveTc *tc0 = tcs, *tc1 = tcs != nullptr ? tcs + 1 : nullptr;
     if (!g.complex_a)
-        return prof.timed(name, st, [&] { return lu_solve<T>(g.n, g.kc, batch, F, fs, false, X, xstride, st, quiet, skip); });
+        return prof.timed(name, st, [&] {
+            return lu_solve<T>(g.n, g.kc, batch, F, fs, false, X, xstride, st, quiet, skip, tc0);
+        });
     // systems 2s (theta) and 2s+1 (conj theta) of every instance share factor s: the
     // even and the odd systems each form a batch with stride 2*xstride
     cudaStream_t aux = aux_stream();
     if (!aux)
         return prof.timed(name, st, [&]() -> cudaError_t {
-            EXPM_TRY(lu_solve<T>(g.n, g.kc, batch, F, fs, false, X, 2 * xstride, st, quiet, skip));
-            return lu_solve<T>(g.n, g.kc, batch, F, fs, true, X + xstride, 2 * xstride, st, quiet, skip);
+            EXPM_TRY(lu_solve<T>(g.n, g.kc, batch, F, fs, false, X, 2 * xstride, st, quiet, skip, tc0));
+            return lu_solve<T>(g.n, g.kc, batch, F, fs, true, X + xstride, 2 * xstride, st, quiet, skip, tc0);
         });
     // the two halves are independent and run concurrently (fork / join through events,
     // so the work stays ordered on st for the caller; also inside a stream capture)
@@ -712,8 +803,9 @@ static cudaError_t solve_systems(const DenseGeom &g, const cx<T> *F, cx<T> *X, i
         cudaError_t e = cudaEventCreateWithFlags(&join, cudaEventDisableTiming);
         if (e == cudaSuccess) e = cudaEventRecord(fork, st);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(aux, fork, 0);
-        if (e == cudaSuccess) e = lu_solve<T>(g.n, g.kc, batch, F, fs, false, X, 2 * xstride, st, quiet, skip);
-        if (e == cudaSuccess) e = lu_solve<T>(g.n, g.kc, batch, F, fs, true, X + xstride, 2 * xstride, aux, quiet, skip);
+        if (e == cudaSuccess) e = lu_solve<T>(g.n, g.kc, batch, F, fs, false, X, 2 * xstride, st, quiet, skip, tc0);
+        if (e == cudaSuccess)
+            e = lu_solve<T>(g.n, g.kc, batch, F, fs, true, X + xstride, 2 * xstride, aux, quiet, skip, tc1);
         if (e == cudaSuccess) e = cudaEventRecord(join, aux);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(st, join, 0);
         cudaEventDestroy(fork);
@@ -789,6 +881,18 @@ cudaError_t dense_solve(const DenseGeom &g, const DenseIO &io, const DenseSystem
         const bool use_oz = dense_uses_oz(g);
         void *oz_ws = p + L.oz;
         bool oz_a_ready = false;  // A's slices are formed at the first residual product
+        SolveTc stc[2];
+        const SolveTc *tcs = nullptr;
+        if (dense_tc_solves(g)) {
+            const size_t batch = (size_t)g.ninst * g.npairs, kr = 12 * DN_PNB;
+            const size_t ab = align_up(batch * (size_t)g.n * kr * sizeof(uint16_t));
+            const size_t bb = align_up(batch * 2 * (size_t)g.kc * kr * sizeof(uint16_t));
+            int *flag = (int *)(p + L.sterr);
+            stc[0] = {(uint16_t *)(p + L.stA), (uint16_t *)(p + L.stB), flag};
+            stc[1] = {(uint16_t *)(p + L.stA + ab), (uint16_t *)(p + L.stB + bb), flag};
+            EXPM_TRY(cudaMemsetAsync(flag, 0, sizeof(int), st));
+            tcs = stc;
+        }
         EXPM_TRY(cudaMemsetAsync(X, 0, (size_t)nsz * nk * sizeof(cx<double>), st));
         std::vector<double> h(2 * (size_t)nsz), an(g.ninst);
         // ||tA||_F of every instance for the relative residual of the stopping test
@@ -883,12 +987,18 @@ cudaError_t dense_solve(const DenseGeom &g, const DenseIO &io, const DenseSystem
                 for (int i = 0; i < g.ninst; ++i) res->inst_iters[i] = it - 1;
                 if (done || it > g.max_refine) break;
             }
-            EXPM_TRY(solve_systems<float>(g, (const cx<float> *)F, D, nk, st, prof));
+            EXPM_TRY(solve_systems<float>(g, (const cx<float> *)F, D, nk, st, prof, nullptr, tcs));
             EXPM_TRY(prof.timed("add_correction", st, [&] {
                 add_correction<<<dim3(gx, 1, nsz), 256, 0, st>>>(nk, D, X, nk, nullptr);
                 return cudaGetLastError();
             }));
         }
+    }
+    if (dense_tc_solves(g)) {  // a bounded wait in a tensor-core solve update gave up
+        int flag = 0;
+        EXPM_TRY(cudaMemcpyAsync(&flag, p + L.sterr, sizeof(int), cudaMemcpyDeviceToHost, st));
+        EXPM_TRY(cudaStreamSynchronize(st));
+        if (flag) res->tc_timeout = 1;
     }
     EXPM_TRY(prof.timed("accumulate", st, [&] {
         accumulate<<<dim3(gx, 1, g.ninst), 256, 0, st>>>(g.n, g.kc, g.nsys, X, nk, sys, io);

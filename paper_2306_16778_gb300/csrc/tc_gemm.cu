@@ -45,7 +45,7 @@ using tcu::mbar_expect_tx;
 using tcu::mbar_init;
 using tcu::mbar_wait;
 using tcu::smem_u32;
-using tcu::tma_load_2d;
+using tcu::tma_load_3d;
 
 __device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t saddr) { return tcu::smem_desc(saddr, 128); }
 
@@ -65,8 +65,10 @@ template <bool BF16>
 __global__ void __launch_bounds__(128, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
                    const __grid_constant__ CUtensorMap mapC, int M, int N, int K, float *__restrict__ C, int ldc,
-                   int *__restrict__ err_flag) {
+                   int64_t cstride, int *__restrict__ err_flag) {
     constexpr int TC_BK = BF16 ? 64 : 32;
+    const int bz = blockIdx.z;  // batch entry: the third coordinate of every tensor map
+    C += (int64_t)bz * cstride;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     // 1024-byte aligned stage buffers (required by the 128-byte swizzle)
     unsigned char *base = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -111,7 +113,7 @@ __global__ void __launch_bounds__(128, 1)
     if (warp == 0 && lane == 0) {
         // TMA producer: the C tile first (consumed only by the epilogue), then the K ring
         mbar_expect_tx(cbar, TC_CTILE_BYTES);
-        tma_load_2d(&mapC, cbar, sC, n0, m0);
+        tma_load_3d(&mapC, cbar, sC, n0, m0, bz);
         for (int kb = 0; kb < nk; ++kb) {
             const int s = kb % TC_STAGES;
             const uint32_t ph = (uint32_t)(kb / TC_STAGES) & 1u;
@@ -121,8 +123,8 @@ __global__ void __launch_bounds__(128, 1)
             }
             if (*(volatile int *)&abort_flag) break;
             mbar_expect_tx(&full[s], 2 * TC_TILE_BYTES);
-            tma_load_2d(&mapA, &full[s], sA + s * TC_TILE_BYTES, kb * TC_BK, m0);
-            tma_load_2d(&mapB, &full[s], sB + s * TC_TILE_BYTES, kb * TC_BK, n0);
+            tma_load_3d(&mapA, &full[s], sA + s * TC_TILE_BYTES, kb * TC_BK, m0, bz);
+            tma_load_3d(&mapB, &full[s], sB + s * TC_TILE_BYTES, kb * TC_BK, n0, bz);
             produced = kb + 1;
         }
     } else if (warp == 1 && lane == 0) {
@@ -235,26 +237,33 @@ using tcu::encode_fn;
 // K-major operand tiles (one 128-byte swizzled row of K per tile row: 32 fp32 or 64
 // bf16) or the plain fp32 C tile (TC_BN x TC_BM, no swizzle); out-of-range elements read
 // as zero.
-bool make_map(CUtensorMap *map, const void *ptr, int rows, int cols, int ld, bool ctile, bool bf16) {
+bool make_map(CUtensorMap *map, const void *ptr, int rows, int cols, int ld, int64_t bstride, int batch, bool ctile,
+              bool bf16) {
     EncodeFn enc = encode_fn();
     if (!enc) return false;
     const size_t es = bf16 ? 2 : 4;
-    const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
-    const cuuint64_t strides[1] = {(cuuint64_t)ld * es};
-    const cuuint32_t box[2] = {ctile ? (cuuint32_t)TC_BN : (cuuint32_t)(TC_ROW_BYTES / es), (cuuint32_t)TC_BM};
-    const cuuint32_t estr[2] = {1, 1};
-    return enc(map, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void *)ptr, dims,
+    const cuuint64_t dims[3] = {(cuuint64_t)cols, (cuuint64_t)rows, (cuuint64_t)batch};
+    const cuuint64_t strides[2] = {(cuuint64_t)ld * es, (cuuint64_t)bstride * es};
+    const cuuint32_t box[3] = {ctile ? (cuuint32_t)TC_BN : (cuuint32_t)(TC_ROW_BYTES / es), (cuuint32_t)TC_BM, 1};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    return enc(map, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, (void *)ptr, dims,
                strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                ctile ? CU_TENSOR_MAP_SWIZZLE_NONE : CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 template <bool BF16>
-cudaError_t tc_gemm_sub(int M, int N, int K, const void *A, int lda, const void *B, int ldb, float *C, int ldc,
-                        int *err_flag, cudaStream_t st) {
+cudaError_t tc_gemm_sub(int M, int N, int K, const void *A, int lda, int64_t sA, const void *B, int ldb, int64_t sB,
+                        float *C, int ldc, int64_t sC, int batch, int *err_flag, cudaStream_t st) {
+    // a single matrix still gets a valid third stride (one matrix's extent)
+    if (batch == 1) {
+        sA = (int64_t)M * lda;
+        sB = (int64_t)N * ldb;
+        sC = (int64_t)M * ldc;
+    }
     CUtensorMap ma, mb, mc;
-    if (!make_map(&ma, A, M, K, lda, false, BF16) || !make_map(&mb, B, N, K, ldb, false, BF16) ||
-        !make_map(&mc, C, M, N, ldc, true, false))
+    if (!make_map(&ma, A, M, K, lda, sA, batch, false, BF16) || !make_map(&mb, B, N, K, ldb, sB, batch, false, BF16) ||
+        !make_map(&mc, C, M, N, ldc, sC, batch, true, false))
         return cudaErrorInvalidValue;
     static std::once_flag once;
     static cudaError_t attr = cudaSuccess;
@@ -262,8 +271,8 @@ cudaError_t tc_gemm_sub(int M, int N, int K, const void *A, int lda, const void 
         attr = cudaFuncSetAttribute(tc_gemm_kernel<BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
     });
     if (attr != cudaSuccess) return attr;
-    dim3 grid((N + TC_BN - 1) / TC_BN, (M + TC_BM - 1) / TC_BM, 1);
-    tc_gemm_kernel<BF16><<<grid, 128, TC_SMEM, st>>>(ma, mb, mc, M, N, K, C, ldc, err_flag);
+    dim3 grid((N + TC_BN - 1) / TC_BN, (M + TC_BM - 1) / TC_BM, batch);
+    tc_gemm_kernel<BF16><<<grid, 128, TC_SMEM, st>>>(ma, mb, mc, M, N, K, C, ldc, sC, err_flag);
     return cudaGetLastError();
 }
 
@@ -272,8 +281,8 @@ int run_hook(bool bf16, int M, int N, int K, const void *A, int lda, const void 
     int *flag = nullptr;
     if (cudaMalloc(&flag, sizeof(int)) != cudaSuccess) return 1;
     cudaMemset(flag, 0, sizeof(int));
-    cudaError_t e = bf16 ? tc_gemm_sub<true>(M, N, K, A, lda, B, ldb, C, ldc, flag, 0)
-                         : tc_gemm_sub<false>(M, N, K, A, lda, B, ldb, C, ldc, flag, 0);
+    cudaError_t e = bf16 ? tc_gemm_sub<true>(M, N, K, A, lda, 0, B, ldb, 0, C, ldc, 0, 1, flag, 0)
+                         : tc_gemm_sub<false>(M, N, K, A, lda, 0, B, ldb, 0, C, ldc, 0, 1, flag, 0);
     int h = 0;
     if (e == cudaSuccess) e = cudaMemcpy(&h, flag, sizeof(int), cudaMemcpyDeviceToHost);
     cudaFree(flag);
@@ -284,22 +293,29 @@ int run_hook(bool bf16, int M, int N, int K, const void *A, int lda, const void 
 }  // namespace
 
 bool tc_gemm_supported(int M, int N, int K, const void *A, int lda, const void *B, int ldb, const void *C, int ldc,
-                       bool bf16) {
+                       bool bf16, int64_t sA, int64_t sB, int64_t sC) {
     if (M < 1 || N < 1 || K < 1) return false;
-    const int q = bf16 ? 8 : 4;  // operand rows a multiple of 16 bytes
+    const int q = bf16 ? 8 : 4;  // operand rows (and batch strides) a multiple of 16 bytes
     if ((lda % q) || (ldb % q) || (ldc % 4) || ((uintptr_t)A % 16) || ((uintptr_t)B % 16) || ((uintptr_t)C % 16))
         return false;
+    if ((sA % q) || (sB % q) || (sC % 4)) return false;
     return encode_fn() != nullptr;
 }
 
 cudaError_t tc_gemm_tf32_sub(int M, int N, int K, const float *A, int lda, const float *B, int ldb, float *C, int ldc,
                              int *err_flag, cudaStream_t st) {
-    return tc_gemm_sub<false>(M, N, K, A, lda, B, ldb, C, ldc, err_flag, st);
+    return tc_gemm_sub<false>(M, N, K, A, lda, 0, B, ldb, 0, C, ldc, 0, 1, err_flag, st);
 }
 
 cudaError_t tc_gemm_bf16_sub(int M, int N, int K, const uint16_t *A, int lda, const uint16_t *B, int ldb, float *C,
                              int ldc, int *err_flag, cudaStream_t st) {
-    return tc_gemm_sub<true>(M, N, K, A, lda, B, ldb, C, ldc, err_flag, st);
+    return tc_gemm_sub<true>(M, N, K, A, lda, 0, B, ldb, 0, C, ldc, 0, 1, err_flag, st);
+}
+
+cudaError_t tc_gemm_batched(bool bf16, int M, int N, int K, const void *A, int lda, int64_t sA, const void *B, int ldb,
+                            int64_t sB, float *C, int ldc, int64_t sC, int batch, int *err_flag, cudaStream_t st) {
+    return bf16 ? tc_gemm_sub<true>(M, N, K, A, lda, sA, B, ldb, sB, C, ldc, sC, batch, err_flag, st)
+                : tc_gemm_sub<false>(M, N, K, A, lda, sA, B, ldb, sB, C, ldc, sC, batch, err_flag, st);
 }
 
 }  // namespace expm

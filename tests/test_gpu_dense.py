@@ -260,3 +260,17 @@ def test_tensor_core_residual_scaling_and_special_values():
     assert np.isnan(R2[bad]).all()
     ref2 = R0 - np.einsum("il,slc->sic", np.nan_to_num(A2), np.nan_to_num(X2))
     assert np.abs(R2[~bad] - ref2[~bad]).max() <= 1e-12 * np.abs(ref2[~bad]).max()
+
+
+@pytest.mark.parametrize("n,k", [(600, 20), (777, 64)])
+def test_bf16x3_tensor_core_solves(plans, n, k):
+    """EXPM_MIXED_BF16X3 with many columns: LU trailing updates and the triangular solves'
+    panel updates on the tensor cores (several 256-row panels, a ragged last panel), both
+    halves of the complex solve; against the oracle and the binary64 path."""
+    g = workloads.rng(330 + n)
+    A, Q, mu, V = workloads.dense_symmetric(n, -40.0, 0.0, k, g, True)
+    Ybf, info = _gpu(plans[16], A, V, P.EXPM_MIXED_BF16X3)
+    Y64, _ = _gpu(plans[16], A, V, P.EXPM_FP64)
+    assert info.status_worst == 0 and 1 <= info.refine_iters_max <= 3
+    assert matrix.rel_err(Ybf, Y64) <= 1e-10
+    assert matrix.rel_err(Ybf, _oracle(A, V, 16)) <= 1e-10
