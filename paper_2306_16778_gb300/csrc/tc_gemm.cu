@@ -9,16 +9,19 @@
 // (h, m, l) the six products h h + h m + m h + h l + m m + l h (the bf16x3 scheme) --
 // an update with binary32-level accuracy either way.
 //
-// One CTA computes one 128 x 128 tile of C: warp 0 issues TMA loads of 128-row tiles of
-// A and B, one 128-byte row of K each (32 fp32 or 64 bf16; 128-byte swizzle), into a
-// 4-stage shared-memory ring; one thread of warp 1 issues tcgen05.mma (M = 128, N = 128,
-// 32 bytes of K per instruction)
-// into a 128 x 128 fp32 accumulator in tensor memory and releases each stage with
-// tcgen05.commit; the C tile is fetched by TMA into shared memory while the K loop runs.
-// Then all four warps read the accumulator back with tcgen05.ld (warp w owns TMEM lanes
-// 32w..32w+31, i.e. rows 32w..32w+31 of the tile), subtract it from the staged C tile
-// and write the result back with coalesced row stores.  Every mbarrier wait is bounded: on time-out the kernel records an error flag,
-// stops issuing work, drains what it issued, frees its tensor memory and returns.
+// One CTA computes one 128 x 256 tile of C: warp 0 issues TMA loads of tiles of A (128
+// rows) and B (256 rows), one 128-byte row of K each (32 fp32 or 64 bf16; 128-byte
+// swizzle), into a 4-stage shared-memory ring (48 KB a stage); one thread of warp 1
+// issues tcgen05.mma (M = 128, N = 256, 32 bytes of K per instruction) into a 128 x 256
+// fp32 accumulator in tensor memory and releases each stage with tcgen05.commit.  Then
+// all four warps read the accumulator back with tcgen05.ld (warp w owns TMEM lanes
+// 32w..32w+31, i.e. rows 32w..32w+31 of the tile), transpose 32-column chunks through
+// shared memory (the ring is idle by then) and subtract them from C with coalesced row
+// reads and writes.  The wide tile halves the operand bytes per MAC against 128 x 128
+// (the operands of a K step come from L2, which does not feed every SM at the tensor
+// pipe's rate).  The batch entry is the third coordinate of both tensor maps (grid z).
+// Every mbarrier wait is bounded: on time-out the kernel records an error flag, stops
+// issuing work, drains what it issued, frees its tensor memory and returns.
 #include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -34,13 +37,13 @@ namespace expm {
 
 namespace {
 
-constexpr int TC_BM = 128, TC_BN = 128;
+constexpr int TC_BM = 128, TC_BN = 256;
 constexpr int TC_ROW_BYTES = 128;                     // one 128-byte swizzled row per tile row and stage:
                                                       // 32 fp32 (TF32) or 64 bf16 elements of K
 constexpr int TC_STAGES = 4;
-constexpr int TC_TILE_BYTES = TC_BM * TC_ROW_BYTES;   // 16 KB for A, same for B (BN == BM)
-constexpr int TC_CTILE_BYTES = TC_BM * TC_BN * 4;     // the C tile, prefetched by TMA
-constexpr int TC_SMEM = TC_STAGES * 2 * TC_TILE_BYTES + TC_CTILE_BYTES + 1024 + 256;
+constexpr int TC_A_BYTES = TC_BM * TC_ROW_BYTES;      // 16 KB of A per stage
+constexpr int TC_B_BYTES = TC_BN * TC_ROW_BYTES;      // 32 KB of B per stage
+constexpr int TC_SMEM = TC_STAGES * (TC_A_BYTES + TC_B_BYTES) + 1024 + 256;
 using tcu::mbar_expect_tx;
 using tcu::mbar_init;
 using tcu::mbar_wait;
@@ -63,9 +66,8 @@ __host__ __device__ constexpr uint32_t idesc_tc(bool bf16, int M, int N) {
 // Either way four MMAs of 32 bytes of K per stage.
 template <bool BF16>
 __global__ void __launch_bounds__(128, 1)
-    tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
-                   const __grid_constant__ CUtensorMap mapC, int M, int N, int K, float *__restrict__ C, int ldc,
-                   int64_t cstride, int *__restrict__ err_flag) {
+    tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, int M, int N,
+                   int K, float *__restrict__ C, int ldc, int64_t cstride, int *__restrict__ err_flag) {
     constexpr int TC_BK = BF16 ? 64 : 32;
     const int bz = blockIdx.z;  // batch entry: the third coordinate of every tensor map
     C += (int64_t)bz * cstride;
@@ -73,13 +75,11 @@ __global__ void __launch_bounds__(128, 1)
     // 1024-byte aligned stage buffers (required by the 128-byte swizzle)
     unsigned char *base = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     unsigned char *sA = base;
-    unsigned char *sB = base + TC_STAGES * TC_TILE_BYTES;
-    float *sC = reinterpret_cast<float *>(sB + TC_STAGES * TC_TILE_BYTES);  // [TC_BM][TC_BN]
-    uint64_t *full = (uint64_t *)((unsigned char *)sC + TC_CTILE_BYTES);
+    unsigned char *sB = base + TC_STAGES * TC_A_BYTES;
+    uint64_t *full = (uint64_t *)(sB + TC_STAGES * TC_B_BYTES);
     uint64_t *empty = full + TC_STAGES;
     uint64_t *accum = empty + TC_STAGES;
-    uint64_t *cbar = accum + 1;
-    uint32_t *tmem_slot = (uint32_t *)(cbar + 1);
+    uint32_t *tmem_slot = (uint32_t *)(accum + 1);
     __shared__ int abort_flag;
     __shared__ int consumed;   // k-blocks whose stage the MMA issuer has taken
     __shared__ int produced;   // k-blocks whose TMA loads were issued
@@ -97,11 +97,10 @@ __global__ void __launch_bounds__(128, 1)
             mbar_init(&empty[s], 1);
         }
         mbar_init(accum, 1);
-        mbar_init(cbar, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (warp == 1) {  // allocate 128 TMEM columns (the 128 x 128 fp32 accumulator)
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 128;" ::"r"(smem_u32(tmem_slot))
+    if (warp == 1) {  // allocate 256 TMEM columns (the 128 x 256 fp32 accumulator)
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 256;" ::"r"(smem_u32(tmem_slot))
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -111,9 +110,7 @@ __global__ void __launch_bounds__(128, 1)
     const uint32_t tmem = *tmem_slot;
 
     if (warp == 0 && lane == 0) {
-        // TMA producer: the C tile first (consumed only by the epilogue), then the K ring
-        mbar_expect_tx(cbar, TC_CTILE_BYTES);
-        tma_load_3d(&mapC, cbar, sC, n0, m0, bz);
+        // TMA producer: the K ring
         for (int kb = 0; kb < nk; ++kb) {
             const int s = kb % TC_STAGES;
             const uint32_t ph = (uint32_t)(kb / TC_STAGES) & 1u;
@@ -122,10 +119,18 @@ __global__ void __launch_bounds__(128, 1)
                 break;
             }
             if (*(volatile int *)&abort_flag) break;
-            mbar_expect_tx(&full[s], 2 * TC_TILE_BYTES);
-            tma_load_3d(&mapA, &full[s], sA + s * TC_TILE_BYTES, kb * TC_BK, m0, bz);
-            tma_load_3d(&mapB, &full[s], sB + s * TC_TILE_BYTES, kb * TC_BK, n0, bz);
+            mbar_expect_tx(&full[s], TC_A_BYTES + TC_B_BYTES);
+            tma_load_3d(&mapA, &full[s], sA + s * TC_A_BYTES, kb * TC_BK, m0, bz);
+            tma_load_3d(&mapB, &full[s], sB + s * TC_B_BYTES, kb * TC_BK, n0, bz);
             produced = kb + 1;
+        }
+    } else if (warp >= 2) {
+        // idle during the K loop: pull this CTA's C tile (128 rows x 1 KB) into L2 for the
+        // epilogue
+        for (int e = threadIdx.x - 64; e < TC_BM * (TC_BN * 4 / 128); e += 64) {
+            const int r = e / (TC_BN * 4 / 128), seg = e % (TC_BN * 4 / 128);
+            const int row = m0 + r, col = n0 + seg * 32;
+            if (row < M && col < N) asm volatile("prefetch.global.L2 [%0];" ::"l"(C + (int64_t)row * ldc + col));
         }
     } else if (warp == 1 && lane == 0) {
         // MMA issuer
@@ -139,7 +144,7 @@ __global__ void __launch_bounds__(128, 1)
                 break;
             }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint32_t a0 = smem_u32(sA + s * TC_TILE_BYTES), b0 = smem_u32(sB + s * TC_TILE_BYTES);
+            const uint32_t a0 = smem_u32(sA + s * TC_A_BYTES), b0 = smem_u32(sB + s * TC_B_BYTES);
 #pragma unroll
             for (int kk = 0; kk < 4; ++kk) {  // 32 bytes of K per instruction (8 TF32 or 16 bf16)
                 const uint64_t ad = smem_desc_sw128(a0 + kk * 32), bd = smem_desc_sw128(b0 + kk * 32);
@@ -180,8 +185,6 @@ __global__ void __launch_bounds__(128, 1)
     const int aborted = *(volatile int *)&abort_flag;
     if (!ok || aborted) {
         if (threadIdx.x == 0) atomicExch(err_flag, 1);
-    } else if (!mbar_wait(cbar, 0u)) {
-        if (lane == 0) atomicExch(err_flag, 1);
     } else {
         // Each warp owns rows m0 + 32w .. +31.  Per 32-column chunk: tcgen05.ld gives each
         // lane one row of the accumulator; it is subtracted from the prefetched C tile in
@@ -207,11 +210,16 @@ __global__ void __launch_bounds__(128, 1)
             for (int j = 0; j < 32; ++j) stage[lane * 33 + j] = __uint_as_float(v[j]);
             __syncwarp();
             const int col = n0 + c0 + lane;
-#pragma unroll 8
+            float cv[32];  // the chunk's 32 C values in flight together, then the stores
+#pragma unroll
             for (int r = 0; r < 32; ++r) {
                 const int row = m0 + warp * 32 + r;
-                if (row < M && col < N)
-                    C[(int64_t)row * ldc + col] = sC[(warp * 32 + r) * TC_BN + c0 + lane] - stage[r * 33 + lane];
+                cv[r] = (row < M && col < N) ? C[(int64_t)row * ldc + col] : 0.f;
+            }
+#pragma unroll
+            for (int r = 0; r < 32; ++r) {
+                const int row = m0 + warp * 32 + r;
+                if (row < M && col < N) C[(int64_t)row * ldc + col] = cv[r] - stage[r * 33 + lane];
             }
             __syncwarp();
         }
@@ -227,7 +235,7 @@ __global__ void __launch_bounds__(128, 1)
     __syncthreads();
     if (warp == 1) {
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 128;" ::"r"(tmem) : "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 256;" ::"r"(tmem) : "memory");
     }
 }
 
@@ -237,19 +245,18 @@ using tcu::encode_fn;
 // K-major operand tiles (one 128-byte swizzled row of K per tile row: 32 fp32 or 64
 // bf16) or the plain fp32 C tile (TC_BN x TC_BM, no swizzle); out-of-range elements read
 // as zero.
-bool make_map(CUtensorMap *map, const void *ptr, int rows, int cols, int ld, int64_t bstride, int batch, bool ctile,
+bool make_map(CUtensorMap *map, const void *ptr, int rows, int cols, int ld, int64_t bstride, int batch, int box_rows,
               bool bf16) {
     EncodeFn enc = encode_fn();
     if (!enc) return false;
     const size_t es = bf16 ? 2 : 4;
     const cuuint64_t dims[3] = {(cuuint64_t)cols, (cuuint64_t)rows, (cuuint64_t)batch};
     const cuuint64_t strides[2] = {(cuuint64_t)ld * es, (cuuint64_t)bstride * es};
-    const cuuint32_t box[3] = {ctile ? (cuuint32_t)TC_BN : (cuuint32_t)(TC_ROW_BYTES / es), (cuuint32_t)TC_BM, 1};
+    const cuuint32_t box[3] = {(cuuint32_t)(TC_ROW_BYTES / es), (cuuint32_t)box_rows, 1};
     const cuuint32_t estr[3] = {1, 1, 1};
     return enc(map, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, (void *)ptr, dims,
-               strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-               ctile ? CU_TENSOR_MAP_SWIZZLE_NONE : CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+               strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 template <bool BF16>
@@ -261,9 +268,8 @@ cudaError_t tc_gemm_sub(int M, int N, int K, const void *A, int lda, int64_t sA,
         sB = (int64_t)N * ldb;
         sC = (int64_t)M * ldc;
     }
-    CUtensorMap ma, mb, mc;
-    if (!make_map(&ma, A, M, K, lda, sA, batch, false, BF16) || !make_map(&mb, B, N, K, ldb, sB, batch, false, BF16) ||
-        !make_map(&mc, C, M, N, ldc, sC, batch, true, false))
+    CUtensorMap ma, mb;
+    if (!make_map(&ma, A, M, K, lda, sA, batch, TC_BM, BF16) || !make_map(&mb, B, N, K, ldb, sB, batch, TC_BN, BF16))
         return cudaErrorInvalidValue;
     static std::once_flag once;
     static cudaError_t attr = cudaSuccess;
@@ -272,7 +278,7 @@ cudaError_t tc_gemm_sub(int M, int N, int K, const void *A, int lda, int64_t sA,
     });
     if (attr != cudaSuccess) return attr;
     dim3 grid((N + TC_BN - 1) / TC_BN, (M + TC_BM - 1) / TC_BM, batch);
-    tc_gemm_kernel<BF16><<<grid, 128, TC_SMEM, st>>>(ma, mb, mc, M, N, K, C, ldc, sC, err_flag);
+    tc_gemm_kernel<BF16><<<grid, 128, TC_SMEM, st>>>(ma, mb, M, N, K, C, ldc, sC, err_flag);
     return cudaGetLastError();
 }
 
