@@ -70,6 +70,20 @@ __global__ void residual_diag(int n, int kc, DenseIO io, int nsys, const cx<doub
     }
 }
 
+// R[z] -= (theta_b - c) D[z]: the diagonal part of the residual update for a correction D
+// (binary32) that has just been added to X
+__global__ void residual_diag_step(int64_t total, int nsys, cx<double> *R, const cx<float> *D, int64_t stride,
+                                   DenseSystems sys) {
+    const int z = blockIdx.z, b = z % nsys;
+    const cx<double> sh = {sys.th_re[b] - sys.cshift, sys.th_im[b]};
+    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        const cx<float> d = D[(int64_t)z * stride + idx];
+        cx<double> &r = R[(int64_t)z * stride + idx];
+        r = r - sh * cx<double>{(double)d.re, (double)d.im};
+    }
+}
+
 // Xc (binary32) = R (binary64) and sums of |R|^2, |X|^2 per batch entry
 __global__ void demote_and_norms(int64_t total, const cx<double> *R, const cx<double> *X, cx<float> *Xc,
                                  int64_t stride, double *rn2, double *xn2, const int *skip) {
@@ -905,6 +919,26 @@ cudaError_t dense_solve(const DenseGeom &g, const DenseIO &io, const DenseSystem
         // it = 0: initial solve; it = 1 .. max_refine: refinement sweeps; the residual
         // of the current X is checked before every sweep and once after the last one
         for (int it = 0;; ++it) {
+            if (use_oz && it >= 2) {
+                // after a correction D (~1e-6 of X): R -= (tA - cI + theta I) D, the product
+                // on the tensor cores in its light form (four slices of A, three of D)
+                EXPM_TRY(prof.timed("residual_diag", st, [&] {
+                    residual_diag_step<<<dim3(gx, 1, nsz), 256, 0, st>>>(nk, g.nsys, R, D, nk, sys);
+                    return cudaGetLastError();
+                }));
+                int to = 0;
+                EXPM_TRY(prof.timed("oz_split_d", st, [&] {
+                    return oz_split_d(g.n, g.kc, g.nsys, g.complex_a, D, nk, oz_ws, st);
+                }));
+                EXPM_TRY(prof.timed("oz_gemm_light", st, [&] {
+                    return oz_product_light(g.n, g.kc, g.nsys, g.complex_a, g.t, nk, R, oz_ws, st, nullptr);
+                }));
+                EXPM_TRY(oz_read_timeout(g.n, g.kc, g.nsys, g.complex_a, oz_ws, st, &to));
+                if (to) {
+                    res->tc_timeout = 1;
+                    return cudaSuccess;
+                }
+            } else {
             // R = V - (tA - cI + theta I) X, binary64
             EXPM_TRY(prof.timed("residual_diag", st, [&] {
                 residual_diag<<<dim3(gx, 1, nsz), 256, 0, st>>>(g.n, g.kc, io, g.nsys, X, R, nk, sys, nullptr);
@@ -959,6 +993,7 @@ cudaError_t dense_solve(const DenseGeom &g, const DenseIO &io, const DenseSystem
                     }
                     return e != cudaSuccess ? e : cudaGetLastError();
                 }));
+            }
             }
             EXPM_TRY(cudaMemsetAsync(rn2, 0, sizeof(double) * nsz, st));
             EXPM_TRY(cudaMemsetAsync(xn2, 0, sizeof(double) * nsz, st));

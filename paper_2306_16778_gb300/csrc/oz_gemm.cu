@@ -61,30 +61,48 @@ namespace {
 
 using namespace tcu;
 
-constexpr int OZ_S = 7;                       // slices per operand
+constexpr int OZ_S = 7;                       // slices of a binary64 operand
 constexpr int OZ_BM = 128, OZ_BN = 96;        // output tile (5 accumulators x 96 <= 512 TMEM columns)
-constexpr int OZ_NACC = 5;
 constexpr int OZ_BK = 32;                     // K per stage: 32 bf16 = 64-byte rows
 constexpr int OZ_KW = 64;                     // K per accumulator window (two stages)
 constexpr int OZ_ASLICE = OZ_BM * OZ_BK * 2;  // 8 KB: one slice of A per stage
 constexpr int OZ_BSLICE = OZ_BN * OZ_BK * 2;  // 6 KB: one slice of B' per stage
-constexpr int OZ_AHALF = OZ_S * OZ_ASLICE;    // 56 KB
-constexpr int OZ_BHALF = OZ_S * OZ_BSLICE;    // 42 KB
-constexpr int OZ_STAGE = OZ_AHALF + OZ_BHALF; // 98 KB (a multiple of 1024)
-constexpr int OZ_STAGES = 2;
-constexpr int OZ_SMEM = OZ_STAGES * OZ_STAGE + 1024 + 256;
 constexpr int OZ_THREADS = 320;
-constexpr int OZ_NPAIR = 28;
 
-// slice pairs (p, q) with p + q <= 6, grouped by accumulator (p+q = 0, 1, 2, 3, >= 4)
-__constant__ unsigned char c_pp[OZ_NPAIR] = {0, 0, 1, 0, 1, 2, 0, 1, 2, 3, 0, 1, 2, 3, 4,
-                                             0, 1, 2, 3, 4, 5, 0, 1, 2, 3, 4, 5, 6};
-__constant__ unsigned char c_qq[OZ_NPAIR] = {0, 1, 0, 2, 1, 0, 3, 2, 1, 0, 4, 3, 2, 1, 0,
-                                             5, 4, 3, 2, 1, 0, 6, 5, 4, 3, 2, 1, 0};
-__constant__ unsigned char c_acc[OZ_NPAIR] = {0, 1, 1, 2, 2, 2, 3, 3, 3, 3, 4, 4, 4, 4, 4,
-                                              4, 4, 4, 4, 4, 4, 4, 4, 4, 4, 4, 4, 4};
-__constant__ unsigned char c_first[OZ_NPAIR] = {1, 1, 0, 1, 0, 0, 1, 0, 0, 0, 1, 0, 0, 0, 0,
-                                                0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+// Kernel configurations.  Full: the residual V - M X, seven slices of A and of X, the 28
+// products with p + q <= 6, accumulators p+q = 0, 1, 2, 3 exact and p+q >= 4 rounded.
+// Light: the update -M D of a residual by a binary32 correction D (|D| ~ 1e-6 |X|, so
+// its product is needed to about 2^-30 only): four slices of A and of D (32 bits below
+// the row / column scale: three would hold a binary32 value exactly only near its
+// column's largest entry), the 10 products with p + q <= 3, accumulators p+q = 0, 1, 2
+// exact and 3 rounded.
+#define OZ_TABLE(name, ...)                                              \
+    static __host__ __device__ constexpr int name(int i) {               \
+        constexpr unsigned char t[] = {__VA_ARGS__};                     \
+        return t[i];                                                     \
+    }
+struct OzFull {
+    static constexpr int SA = 7, SB = 7, NPAIR = 28, NACC = 5, STAGES = 2;
+    static constexpr bool EXACT3 = true;
+    OZ_TABLE(pp, 0, 0, 1, 0, 1, 2, 0, 1, 2, 3, 0, 1, 2, 3, 4, 0, 1, 2, 3, 4, 5, 0, 1, 2, 3, 4, 5, 6)
+    OZ_TABLE(qq, 0, 1, 0, 2, 1, 0, 3, 2, 1, 0, 4, 3, 2, 1, 0, 5, 4, 3, 2, 1, 0, 6, 5, 4, 3, 2, 1, 0)
+    OZ_TABLE(acc, 0, 1, 1, 2, 2, 2, 3, 3, 3, 3, 4, 4, 4, 4, 4, 4, 4, 4, 4, 4, 4, 4, 4, 4, 4, 4, 4, 4)
+    OZ_TABLE(first, 1, 1, 0, 1, 0, 0, 1, 0, 0, 0, 1, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0)
+};
+struct OzLight {
+    static constexpr int SA = 4, SB = 4, NPAIR = 10, NACC = 4, STAGES = 4;
+    static constexpr bool EXACT3 = false;
+    OZ_TABLE(pp, 0, 0, 1, 0, 1, 2, 0, 1, 2, 3)
+    OZ_TABLE(qq, 0, 1, 0, 2, 1, 0, 3, 2, 1, 0)
+    OZ_TABLE(acc, 0, 1, 1, 2, 2, 2, 3, 3, 3, 3)
+    OZ_TABLE(first, 1, 1, 0, 1, 0, 0, 1, 0, 0, 0)
+};
+#undef OZ_TABLE
+template <class C> __host__ __device__ constexpr int oz_ahalf() { return C::SA * OZ_ASLICE; }
+template <class C> __host__ __device__ constexpr int oz_stage() {  // a multiple of 1024
+    return C::SA * OZ_ASLICE + C::SB * OZ_BSLICE;
+}
+template <class C> __host__ __device__ constexpr int oz_smem() { return C::STAGES * oz_stage<C>() + 1024 + 256; }
 
 // kind::f16 instruction descriptor: D fp32, A and B bf16, both K-major, M x N
 __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
@@ -166,22 +184,26 @@ __global__ void oz_split_rows(int rows, int K2, int K2p, const double *__restric
     }
 }
 
-// max biased exponent of each complex column (s, c) of X (F preset to zero)
-__global__ void oz_col_exp(int n, int kc, const cx<double> *__restrict__ X, int64_t nk, int *__restrict__ F) {
+// max biased exponent (binary64 terms) of each complex column (s, c) of X, binary64 or
+// binary32 (F preset to zero)
+template <class XT>
+__global__ void oz_col_exp(int n, int kc, const cx<XT> *__restrict__ X, int64_t nk, int *__restrict__ F) {
     const int c = blockIdx.x * blockDim.x + threadIdx.x, s = blockIdx.z;
     if (c >= kc) return;
     const int l0 = blockIdx.y * 64, l1 = min(n, l0 + 64);
     int m = 1;
     for (int l = l0; l < l1; ++l) {
-        const cx<double> x = X[(int64_t)s * nk + (int64_t)l * kc + c];
-        m = max(m, max(biased_exp(x.re), biased_exp(x.im)));
+        const cx<XT> x = X[(int64_t)s * nk + (int64_t)l * kc + c];
+        m = max(m, max(biased_exp((double)x.re), biased_exp((double)x.im)));
     }
     atomicMax(&F[s * kc + c], m);
 }
 
-// slices of B': Bs[q][j][k] (ld K2p), one complex X value per thread (l fastest)
+// slices of B': Bs[q][j][k] (ld K2p), q < NS (the leading NS of the seven digits),
+// one complex X value per thread (l fastest)
+template <class XT, int NS>
 __global__ void oz_split_cols(int n, int kc, int nsys, int complex_a, int K2p, int64_t N2,
-                              const cx<double> *__restrict__ X, int64_t nk, const int *__restrict__ F,
+                              const cx<XT> *__restrict__ X, int64_t nk, const int *__restrict__ F,
                               uint16_t *__restrict__ Bs) {
     const int64_t total = (int64_t)nsys * kc * n;
     const int64_t plane = N2 * K2p;
@@ -190,16 +212,16 @@ __global__ void oz_split_cols(int n, int kc, int nsys, int complex_a, int K2p, i
         const int l = (int)(idx % n);
         const int64_t sc = idx / n;
         const int c = (int)(sc % kc), s = (int)(sc / kc);
-        const cx<double> x = X[(int64_t)s * nk + (int64_t)l * kc + c];
+        const cx<XT> x = X[(int64_t)s * nk + (int64_t)l * kc + c];
         const int fb = F[s * kc + c];
         uint16_t dr[OZ_S], di[OZ_S];
-        oz_digits(x.re, fb, dr);
-        oz_digits(x.im, fb, di);
+        oz_digits((double)x.re, fb, dr);
+        oz_digits((double)x.im, fb, di);
         const int64_t jre = (int64_t)s * 2 * kc + 2 * c;
         if (complex_a) {
             uint16_t *o0 = Bs + jre * K2p + 2 * l, *o1 = o0 + K2p;
 #pragma unroll
-            for (int q = 0; q < OZ_S; ++q) {
+            for (int q = 0; q < NS; ++q) {
                 const uint32_t ndi = (uint32_t)(di[q] ^ (di[q] ? 0x8000u : 0u));  // -Im (exact: a sign flip)
                 *reinterpret_cast<uint32_t *>(o0 + q * plane) = (uint32_t)dr[q] | (ndi << 16);
                 *reinterpret_cast<uint32_t *>(o1 + q * plane) = (uint32_t)di[q] | ((uint32_t)dr[q] << 16);
@@ -207,7 +229,7 @@ __global__ void oz_split_cols(int n, int kc, int nsys, int complex_a, int K2p, i
         } else {
             uint16_t *o0 = Bs + jre * K2p + l, *o1 = o0 + K2p;
 #pragma unroll
-            for (int q = 0; q < OZ_S; ++q) {
+            for (int q = 0; q < NS; ++q) {
                 o0[q * plane] = dr[q];
                 o1[q * plane] = di[q];
             }
@@ -225,16 +247,18 @@ __device__ __forceinline__ void tmem_ld4(uint32_t addr, uint32_t (&v)[4]) {
                  : "r"(addr));
 }
 
+template <class Cfg>
 __global__ void __launch_bounds__(OZ_THREADS, 1)
     oz_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, int M,
                    int64_t N2, int K2, int kc, int64_t nk, double t, const int *__restrict__ E,
                    const int *__restrict__ F, double *__restrict__ R, int *__restrict__ err_flag) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char *base = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    // stage s: A slices at base + s * OZ_STAGE, B' slices OZ_AHALF after them
-    uint64_t *full = (uint64_t *)(base + OZ_STAGES * OZ_STAGE);
-    uint64_t *empty = full + OZ_STAGES;
-    uint64_t *tfull = empty + OZ_STAGES;  // MMA -> drain: a window's accumulators are complete
+    constexpr int STAGES = Cfg::STAGES, STAGE = oz_stage<Cfg>(), AHALF = oz_ahalf<Cfg>();
+    // stage s: A slices at base + s * STAGE, B' slices AHALF after them
+    uint64_t *full = (uint64_t *)(base + STAGES * STAGE);
+    uint64_t *empty = full + STAGES;
+    uint64_t *tfull = empty + STAGES;     // MMA -> drain: a window's accumulators are complete
     uint64_t *tempty = tfull + 1;         // drain -> MMA: the accumulators have been read
     uint64_t *done = tempty + 1;          // every MMA issued has completed
     uint32_t *tmem_slot = (uint32_t *)(done + 1);
@@ -250,7 +274,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
     if (threadIdx.x == 0) {
         abort_flag = 0;
         consumed = produced = 0;
-        for (int s = 0; s < OZ_STAGES; ++s) {
+        for (int s = 0; s < STAGES; ++s) {
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], 1);
         }
@@ -272,17 +296,17 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
     if (warp == 8) {
         if (lane == 0) {  // TMA producer
             for (int kb = 0; kb < nst; ++kb) {
-                const int s = kb % OZ_STAGES;
-                const uint32_t ph = (uint32_t)(kb / OZ_STAGES) & 1u;
+                const int s = kb % STAGES;
+                const uint32_t ph = (uint32_t)(kb / STAGES) & 1u;
                 if (!mbar_wait(&empty[s], ph ^ 1u)) {
                     atomicExch(&abort_flag, 1);
                     break;
                 }
                 if (*(volatile int *)&abort_flag) break;
-                unsigned char *st = base + s * OZ_STAGE;
-                mbar_expect_tx(&full[s], OZ_STAGE);
+                unsigned char *st = base + s * STAGE;
+                mbar_expect_tx(&full[s], STAGE);
                 tma_load_3d(&mapA, &full[s], st, kb * OZ_BK, m0, 0);
-                tma_load_3d(&mapB, &full[s], st + OZ_AHALF, kb * OZ_BK, (int)n0, 0);
+                tma_load_3d(&mapB, &full[s], st + AHALF, kb * OZ_BK, (int)n0, 0);
                 produced = kb + 1;
             }
         }
@@ -290,8 +314,8 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
         if (lane == 0) {  // MMA issuer
             constexpr uint32_t idesc = idesc_bf16(OZ_BM, OZ_BN);
             for (int kb = 0; kb < nst; ++kb) {
-                const int s = kb % OZ_STAGES;
-                const uint32_t ph = (uint32_t)(kb / OZ_STAGES) & 1u;
+                const int s = kb % STAGES;
+                const uint32_t ph = (uint32_t)(kb / STAGES) & 1u;
                 const bool wstart = (kb & 1) == 0;
                 if ((wstart && kb > 0 && !mbar_wait(tempty, (uint32_t)((kb / 2 - 1) & 1))) ||
                     !mbar_wait(&full[s], ph) || *(volatile int *)&abort_flag) {
@@ -300,19 +324,19 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
                     break;
                 }
                 fence_after_sync();
-                const uint32_t a0 = smem_u32(base + s * OZ_STAGE), b0 = a0 + OZ_AHALF;
+                const uint32_t a0 = smem_u32(base + s * STAGE), b0 = a0 + AHALF;
 #pragma unroll
                 for (int kk = 0; kk < OZ_BK / 16; ++kk) {  // K = 16 bf16 = 32 bytes per instruction
 #pragma unroll
-                    for (int pr = 0; pr < OZ_NPAIR; ++pr) {
-                        const uint64_t ad = smem_desc(a0 + c_pp[pr] * OZ_ASLICE + kk * 32, 64);
-                        const uint64_t bd = smem_desc(b0 + c_qq[pr] * OZ_BSLICE + kk * 32, 64);
-                        const uint32_t acc = (wstart && kk == 0 && c_first[pr]) ? 0u : 1u;
+                    for (int pr = 0; pr < Cfg::NPAIR; ++pr) {
+                        const uint64_t ad = smem_desc(a0 + Cfg::pp(pr) * OZ_ASLICE + kk * 32, 64);
+                        const uint64_t bd = smem_desc(b0 + Cfg::qq(pr) * OZ_BSLICE + kk * 32, 64);
+                        const uint32_t acc = (wstart && kk == 0 && Cfg::first(pr)) ? 0u : 1u;
                         asm volatile(
                             "{\n\t.reg .pred p;\n\t"
                             "setp.ne.u32 p, %4, 0;\n\t"
                             "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(
-                                tmem + (uint32_t)c_acc[pr] * OZ_BN),
+                                tmem + (uint32_t)Cfg::acc(pr) * OZ_BN),
                             "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
                             : "memory");
                     }
@@ -353,22 +377,29 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
                 tmem_ld4(tbase + 1 * OZ_BN + 4 * g, v1);
                 tmem_ld4(tbase + 2 * OZ_BN + 4 * g, v2);
                 tmem_ld4(tbase + 3 * OZ_BN + 4 * g, v3);
-                tmem_ld4(tbase + 4 * OZ_BN + 4 * g, v4);
+                if (Cfg::EXACT3) tmem_ld4(tbase + 4 * OZ_BN + 4 * g, v4);
                 asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
                 for (int e = 0; e < 4; ++e) {
                     const int i0 = magic_int(__uint_as_float(v0[e]), M0);  // |.| <= 2^20
                     const int i1 = magic_int(__uint_as_float(v1[e]), M1);  // |.| <= 2^21
                     const int i2 = magic_int(__uint_as_float(v2[e]), M2);  // |.| <= 3 * 2^20
-                    // p+q = 3: a multiple of 2^-24 with |.| <= 2^-2, in two exact steps (to
-                    // 2^-23, then the remainder 0 or +-2^-24)
-                    const float x3 = __uint_as_float(v3[e]);
-                    const float h3 = __fsub_rn(__fadd_rn(x3, M3), M3);
-                    const int i3 = 2 * magic_int(x3, M3) + magic_int(__fsub_rn(x3, h3), M4);  // x3 * 2^24
+                    int i3 = 0;
+                    float xr;  // the rounded accumulator: p+q >= 4 (full) or p+q = 3 (light)
+                    if (Cfg::EXACT3) {
+                        // p+q = 3: a multiple of 2^-24 with |.| <= 2^-2, in two exact steps
+                        // (to 2^-23, then the remainder 0 or +-2^-24)
+                        const float x3 = __uint_as_float(v3[e]);
+                        const float h3 = __fsub_rn(__fadd_rn(x3, M3), M3);
+                        i3 = 2 * magic_int(x3, M3) + magic_int(__fsub_rn(x3, h3), M4);  // x3 * 2^24
+                        xr = __uint_as_float(v4[e]);
+                    } else {
+                        xr = __uint_as_float(v3[e]);
+                    }
                     const int a = i0 * 256 + i1;  // |a| < 2^28.1
                     const int c = i2 * 256 + i3;  // |c| < 2^29.7
                     T[4 * g + e] += (long long)a * 65536 + (long long)c;
-                    S[4 * g + e] = __fadd_rn(S[4 * g + e], __uint_as_float(v4[e]));
+                    S[4 * g + e] = __fadd_rn(S[4 * g + e], xr);
                 }
             }
             fence_before_sync();
@@ -420,7 +451,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
         if (aborted) {
             atomicExch(err_flag, 1);
             for (int kb = consumed; kb < produced; ++kb)
-                mbar_wait(&full[kb % OZ_STAGES], (uint32_t)(kb / OZ_STAGES) & 1u);
+                mbar_wait(&full[kb % STAGES], (uint32_t)(kb / STAGES) & 1u);
         }
     }
     __syncthreads();
@@ -430,14 +461,16 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
     }
 }
 
-// 3-D map over the slices: dims (K2, rows, 6), row stride K2p bf16, box 32 x box_rows x 6,
+// 3-D map over the slices: dims (K2, rows, nslices), row stride K2p bf16, box 32 x box_rows x
+// box_slices (the leading slices),
 // 64-byte swizzle; out-of-range elements read as zero
-bool make_slice_map(CUtensorMap *map, const uint16_t *ptr, int64_t rows, int K2, int K2p, int box_rows) {
+bool make_slice_map(CUtensorMap *map, const uint16_t *ptr, int64_t rows, int K2, int K2p, int box_rows, int nslices,
+                    int box_slices) {
     EncodeFn enc = encode_fn();
     if (!enc) return false;
-    const cuuint64_t dims[3] = {(cuuint64_t)K2, (cuuint64_t)rows, (cuuint64_t)OZ_S};
+    const cuuint64_t dims[3] = {(cuuint64_t)K2, (cuuint64_t)rows, (cuuint64_t)nslices};
     const cuuint64_t strides[2] = {(cuuint64_t)K2p * 2, (cuuint64_t)rows * K2p * 2};
-    const cuuint32_t box[3] = {(cuuint32_t)OZ_BK, (cuuint32_t)box_rows, (cuuint32_t)OZ_S};
+    const cuuint32_t box[3] = {(cuuint32_t)OZ_BK, (cuuint32_t)box_rows, (cuuint32_t)box_slices};
     const cuuint32_t estr[3] = {1, 1, 1};
     return enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, (void *)ptr, dims, strides, box, estr,
                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -497,35 +530,64 @@ cudaError_t oz_split_x(int n, int kc, int nsys, int complex_a, const cx<double> 
     int *F = (int *)(b + L.F);
     cudaError_t e = cudaMemsetAsync(F, 0, sizeof(int) * (size_t)nsys * kc, st);
     if (e != cudaSuccess) return e;
-    oz_col_exp<<<dim3((kc + 127) / 128, (n + 63) / 64, nsys), 128, 0, st>>>(n, kc, X, nk, F);
+    oz_col_exp<double><<<dim3((kc + 127) / 128, (n + 63) / 64, nsys), 128, 0, st>>>(n, kc, X, nk, F);
     const int64_t work = (int64_t)nsys * kc * n;
     const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>((work + 255) / 256, 152 * 16));
-    oz_split_cols<<<grid, 256, 0, st>>>(n, kc, nsys, complex_a, L.K2p, L.N2, X, nk, F, (uint16_t *)(b + L.Bs));
+    oz_split_cols<double, OZ_S><<<grid, 256, 0, st>>>(n, kc, nsys, complex_a, L.K2p, L.N2, X, nk, F,
+                                                      (uint16_t *)(b + L.Bs));
     return cudaGetLastError();
 }
 
-cudaError_t oz_product(int n, int kc, int nsys, int complex_a, double t, int64_t nk, cx<double> *R, void *ws,
-                       cudaStream_t st, int *timeout) {
+cudaError_t oz_split_d(int n, int kc, int nsys, int complex_a, const cx<float> *D, int64_t nk, void *ws,
+                       cudaStream_t st) {
+    const OzLayout L = oz_layout(n, kc, nsys, complex_a);
+    unsigned char *b = (unsigned char *)ws;
+    int *F = (int *)(b + L.F);
+    cudaError_t e = cudaMemsetAsync(F, 0, sizeof(int) * (size_t)nsys * kc, st);
+    if (e != cudaSuccess) return e;
+    oz_col_exp<float><<<dim3((kc + 127) / 128, (n + 63) / 64, nsys), 128, 0, st>>>(n, kc, D, nk, F);
+    const int64_t work = (int64_t)nsys * kc * n;
+    const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>((work + 255) / 256, 152 * 16));
+    oz_split_cols<float, OzLight::SB><<<grid, 256, 0, st>>>(n, kc, nsys, complex_a, L.K2p, L.N2, D, nk, F,
+                                                            (uint16_t *)(b + L.Bs));
+    return cudaGetLastError();
+}
+
+template <class Cfg>
+static cudaError_t oz_launch(int n, int kc, int nsys, int complex_a, double t, int64_t nk, cx<double> *R, void *ws,
+                             cudaStream_t st, int *timeout) {
     const OzLayout L = oz_layout(n, kc, nsys, complex_a);
     unsigned char *b = (unsigned char *)ws;
     int *F = (int *)(b + L.F), *flag = (int *)(b + L.flag);
     cudaError_t e;
     CUtensorMap ma, mb;
-    if (!make_slice_map(&ma, (const uint16_t *)(b + L.As), n, L.K2, L.K2p, OZ_BM) ||
-        !make_slice_map(&mb, (const uint16_t *)(b + L.Bs), L.N2, L.K2, L.K2p, OZ_BN))
+    // A's stored seven slices (the leading Cfg::SA read); B' holds Cfg::SB planes
+    if (!make_slice_map(&ma, (const uint16_t *)(b + L.As), n, L.K2, L.K2p, OZ_BM, OZ_S, Cfg::SA) ||
+        !make_slice_map(&mb, (const uint16_t *)(b + L.Bs), L.N2, L.K2, L.K2p, OZ_BN, Cfg::SB, Cfg::SB))
         return cudaErrorInvalidValue;
-    static cudaError_t attr = cudaFuncSetAttribute(oz_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SMEM);
+    static cudaError_t attr =
+        cudaFuncSetAttribute(oz_gemm_kernel<Cfg>, cudaFuncAttributeMaxDynamicSharedMemorySize, oz_smem<Cfg>());
     if (attr != cudaSuccess) return attr;
     if ((e = cudaMemsetAsync(flag, 0, sizeof(int), st)) != cudaSuccess) return e;
     const dim3 gg((unsigned)((n + OZ_BM - 1) / OZ_BM), (unsigned)((L.N2 + OZ_BN - 1) / OZ_BN), 1);
-    oz_gemm_kernel<<<gg, OZ_THREADS, OZ_SMEM, st>>>(ma, mb, n, L.N2, L.K2, kc, nk, t, (const int *)(b + L.E), F,
-                                                     (double *)R, flag);
+    oz_gemm_kernel<Cfg><<<gg, OZ_THREADS, oz_smem<Cfg>(), st>>>(ma, mb, n, L.N2, L.K2, kc, nk, t,
+                                                                (const int *)(b + L.E), F, (double *)R, flag);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (timeout) {
         e = cudaMemcpyAsync(timeout, flag, sizeof(int), cudaMemcpyDeviceToHost, st);
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     }
     return e;
+}
+
+cudaError_t oz_product(int n, int kc, int nsys, int complex_a, double t, int64_t nk, cx<double> *R, void *ws,
+                       cudaStream_t st, int *timeout) {
+    return oz_launch<OzFull>(n, kc, nsys, complex_a, t, nk, R, ws, st, timeout);
+}
+
+cudaError_t oz_product_light(int n, int kc, int nsys, int complex_a, double t, int64_t nk, cx<double> *R, void *ws,
+                             cudaStream_t st, int *timeout) {
+    return oz_launch<OzLight>(n, kc, nsys, complex_a, t, nk, R, ws, st, timeout);
 }
 
 cudaError_t oz_read_timeout(int n, int kc, int nsys, int complex_a, void *ws, cudaStream_t st, int *timeout) {
@@ -550,6 +612,25 @@ extern "C" int expm_internal_oz_resid(int n, int kc, int nsys, int complex_a, do
     cudaError_t e = oz_split_a(n, A, lda, complex_a, ws, 0);
     if (e == cudaSuccess) e = oz_split_x(n, kc, nsys, complex_a, (const cx<double> *)X, (int64_t)n * kc, ws, 0);
     if (e == cudaSuccess) e = oz_product(n, kc, nsys, complex_a, t, (int64_t)n * kc, (cx<double> *)R, ws, 0, &to);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    cudaFree(ws);
+    if (e != cudaSuccess) return 1;
+    return to ? 2 : 0;
+}
+
+// Test hook (not part of the documented interface): R_s -= t A D_s with the light product
+// (D_s binary32 complex n x kc, system stride n kc).  Returns as the hook above.
+extern "C" int expm_internal_oz_resid_light(int n, int kc, int nsys, int complex_a, double t, const double *A,
+                                            int64_t lda, const float *D, double *R) {
+    using namespace expm;
+    if (!oz_resid_supported(n, kc, nsys) || lda < n) return 1;
+    void *ws = nullptr;
+    if (cudaMalloc(&ws, oz_resid_bytes(n, kc, nsys, complex_a)) != cudaSuccess) return 1;
+    int to = 0;
+    cudaError_t e = oz_split_a(n, A, lda, complex_a, ws, 0);
+    if (e == cudaSuccess) e = oz_split_d(n, kc, nsys, complex_a, (const cx<float> *)D, (int64_t)n * kc, ws, 0);
+    if (e == cudaSuccess)
+        e = oz_product_light(n, kc, nsys, complex_a, t, (int64_t)n * kc, (cx<double> *)R, ws, 0, &to);
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     cudaFree(ws);
     if (e != cudaSuccess) return 1;

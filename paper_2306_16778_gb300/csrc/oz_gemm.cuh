@@ -22,6 +22,13 @@ cudaError_t oz_split_x(int n, int kc, int nsys, int complex_a, const cx<double> 
 cudaError_t oz_product(int n, int kc, int nsys, int complex_a, double t, int64_t nk, cx<double> *R, void *ws,
                        cudaStream_t st, int *timeout);
 
+// The light update for a binary32 correction D (|D| << |X|): four slices of D into ws,
+// then R_s -= t A D_s with four slices of A and the 10 products of order <= 3 -- about
+// 2^-30 of max|A_i.| max|D_.j| K, enough once D is ~1e-6 of X.
+cudaError_t oz_split_d(int n, int kc, int nsys, int complex_a, const cx<float> *D, int64_t nk, void *ws,
+                       cudaStream_t st);
+cudaError_t oz_product_light(int n, int kc, int nsys, int complex_a, double t, int64_t nk, cx<double> *R, void *ws,
+                             cudaStream_t st, int *timeout);
 // the product's time-out flag (1 if a bounded wait gave up); synchronises st
 cudaError_t oz_read_timeout(int n, int kc, int nsys, int complex_a, void *ws, cudaStream_t st, int *timeout);
 

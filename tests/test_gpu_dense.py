@@ -274,3 +274,27 @@ def test_bf16x3_tensor_core_solves(plans, n, k):
     assert info.status_worst == 0 and 1 <= info.refine_iters_max <= 3
     assert matrix.rel_err(Ybf, Y64) <= 1e-10
     assert matrix.rel_err(Ybf, _oracle(A, V, 16)) <= 1e-10
+
+
+@pytest.mark.parametrize("n,kc,nsys,complex_a", [(100, 9, 2, True), (300, 16, 3, False), (700, 20, 4, True)])
+def test_tensor_core_residual_light(n, kc, nsys, complex_a):
+    """The light residual update R_s -= t A D_s for a binary32 D (four slices of A and of
+    D, the 10 slice products of order <= 3): about 2^-30 of the product, the accuracy a
+    correction ~1e-6 of the solution needs."""
+    import ctypes
+    f = P.lib.expm_internal_oz_resid_light
+    f.restype = ctypes.c_int
+    f.argtypes = [ctypes.c_int] * 4 + [ctypes.c_double, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
+                                       ctypes.c_void_p]
+    g = np.random.default_rng(4200 + n)
+    A = _cgauss(g, (n, n)) if complex_a else g.standard_normal((n, n))
+    D = _cgauss(g, (nsys, n, kc)).astype(np.complex64)
+    R0 = _cgauss(g, (nsys, n, kc))
+    dA = torch.from_numpy(np.ascontiguousarray(A)).to(DEV)
+    dD = torch.from_numpy(np.ascontiguousarray(D)).to(DEV)
+    dR = torch.from_numpy(np.ascontiguousarray(R0)).to(DEV)
+    assert f(n, kc, nsys, int(complex_a), 0.5, dA.data_ptr(), n, dD.data_ptr(), dR.data_ptr()) == 0
+    torch.cuda.synchronize()
+    prod = 0.5 * np.einsum("il,slc->sic", A, D.astype(np.complex128))
+    err = np.linalg.norm(dR.cpu().numpy() - (R0 - prod)) / np.linalg.norm(prod)
+    assert err <= 1e-8, err
