@@ -450,7 +450,8 @@ def run_dense(args):
         out[name] = {"s_per_eval": round(statistics.median(ts), 5), "evals_per_s": round(1 / statistics.median(ts), 4),
                      "refine_sweeps": info.refine_iters_max, "resid_rel": info.resid_rel_max,
                      "growth": info.growth_max_seen,
-                     "kernels_ms_total": {k: round(v[1], 3) for k, v in prof.items()}}
+                     "kernels_ms_total": {k: round(v[1], 3) for k, v in prof.items()},
+                     "kernel_launches": {k: v[0] for k, v in prof.items()}}
     # the same through the reduction of A to real tridiagonal form (binary64 reduction and
     # reflector products; binary64 or binary32 + refinement tridiagonal solves)
     for name, prec, kw in (("reduced", P.EXPM_FP64, {}),
@@ -471,16 +472,19 @@ def run_dense(args):
     n, kc, nsys = args.dense_n, 256, 16
     burst, sustained, src = _bf16_peak()
     prof = out["mixed_bf16x3"]["kernels_ms_total"]
-    sweeps = out["mixed_bf16x3"]["refine_sweeps"]
+    launches = out["mixed_bf16x3"]["kernel_launches"]
     steps = max(1, args.steps)
-    if "oz_gemm" in prof:
-        # 28 slice products of the real product (n x 2n) (2n x 2 nsys kc), two launches per sweep
-        fl = 2.0 * 28 * n * (2 * n) * (2 * nsys * kc) * (sweeps + 1) * steps
-        tf = fl / (prof["oz_gemm"] * 1e-3) / 1e12
-        out["roofline_oz_gemm"] = {"kernel": "oz_gemm_kernel", "bound": "tensor", "achieved": round(tf, 1),
-                                   "peak": sustained, "unit": "TFLOP/s", "frac": round(tf / sustained, 4),
-                                   "peak_source": f"{src} bf16 sustained",
-                                   "algorithmic": "2 x 28 slice products x n x 2n x (2 x 16 systems x 256 columns)"}
+    # slice products of the real product (n x 2n) (2n x 2 nsys kc): 28 in the full residual
+    # (seven slices per operand), 10 in the light update after a correction (four per operand)
+    for key, kname, pairs in (("oz_gemm", "oz_gemm_kernel<OzFull>", 28), ("oz_gemm_light", "oz_gemm_kernel<OzLight>", 10)):
+        if key not in prof:
+            continue
+        fl = 2.0 * pairs * n * (2 * n) * (2 * nsys * kc) * launches[key]
+        tf = fl / (prof[key] * 1e-3) / 1e12
+        out["roofline_" + key] = {"kernel": kname, "bound": "tensor", "achieved": round(tf, 1), "peak": sustained,
+                                  "unit": "TFLOP/s", "frac": round(tf / sustained, 4),
+                                  "peak_source": f"{src} bf16 sustained", "launches": launches[key],
+                                  "algorithmic": f"{pairs} slice products x 2 x n x 2n x (2 x 16 systems x 256 columns)"}
     if "tc_gemm_bf16x3" in prof:
         # trailing updates of the 256-column panels: 8 pairs, real (right) x (2 right) x (12 x 256)
         fl = sum(2.0 * 8 * r * (2 * r) * (12 * 256) for r in range(n - 256, 0, -256)) * steps

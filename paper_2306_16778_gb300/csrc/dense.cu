@@ -921,7 +921,7 @@ cudaError_t dense_solve(const DenseGeom &g, const DenseIO &io, const DenseSystem
         for (int it = 0;; ++it) {
             if (use_oz && it >= 2) {
                 // after a correction D (~1e-6 of X): R -= (tA - cI + theta I) D, the product
-                // on the tensor cores in its light form (four slices of A, three of D)
+                // on the tensor cores in its light form (four slices of A and of D)
                 EXPM_TRY(prof.timed("residual_diag", st, [&] {
                     residual_diag_step<<<dim3(gx, 1, nsz), 256, 0, st>>>(nk, g.nsys, R, D, nk, sys);
                     return cudaGetLastError();
