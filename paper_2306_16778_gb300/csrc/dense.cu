@@ -577,16 +577,28 @@ struct SolveTc {
     int *err = nullptr;
 };
 
-// In-place solve of the kc columns of X[b] (n x kc) with the factors in F.
+// Explicit inverses of the diagonal panels for the wide solves: Inv[z][q][0] = L_q^{-1},
+// Inv[z][q][1] = U_q^{-1} (B x B each, z the factor, q the panel), and the scratch T
+// (batch x B x kc) that one panel's product goes through.
+struct SolveInv {
+    const void *inv = nullptr;
+    void *T = nullptr;
+    int B = 0, npan = 0;
+};
+
+// In-place solve of the kc columns of X[b] (n x kc) with the factors in F[b].
 // conj = false: L U x = b (forward unit-lower, back upper).
 // conj = true : U^H L^H x = b (forward with U^H, back with unit L^H).
-// Factor of system b is F[fidx[b]] -- systems of one pair share a factor.
+// sweeps: 1 forward only, 2 backward only, 3 both.  With `inv`, each diagonal panel is
+// applied as one product by its inverse (or the inverse's conjugate transpose);
+// without it, as 64-row triangular solves and the updates inside the panel.
 template <class T>
 static cudaError_t lu_solve(int n, int kc, int batch, const cx<T> *F, int64_t fstride, bool conj, cx<T> *X,
                             int64_t xstride, cudaStream_t st, Profiler &prof, const int *skip = nullptr,
-                            const SolveTc *tcs = nullptr) {
+                            const SolveTc *tcs = nullptr, Profiler *parts = nullptr, const SolveInv *inv = nullptr,
+                            int sweeps = 3) {
     const size_t smn = narrow_smem_bytes<T>(n, kc);
-    if (kc <= 8 && smn <= (200u << 10)) {  // few right-hand sides: one fused kernel per batch entry
+    if (sweeps == 3 && kc <= 8 && smn <= (200u << 10)) {  // few right-hand sides: one fused kernel per batch entry
         // the attribute is a ceiling, set to the largest size used so that concurrent
         // callers (server workers) never lower it under one another's launch
         EXPM_TRY(set_smem(lu_solve_narrow<T, false>, 200u << 10));
@@ -652,27 +664,96 @@ static cudaError_t lu_solve(int n, int kc, int batch, const cx<T> *F, int64_t fs
         update(r0, m, k0, K);
         return cudaGetLastError();
     };
+    // optional per-part timing (diagonal blocks, in-panel updates, updates past a panel)
+    Profiler none;
+    Profiler &pp = parts ? *parts : none;
+    const bool f64 = sizeof(T) == 8;
+    auto t_trsm = [&](int p, int nb, bool lower) {
+        return pp.timed(f64 ? "solve_diag<f64>" : "solve_diag<f32>", st, [&] {
+            trsm(p, nb, lower);
+            return cudaGetLastError();
+        });
+    };
+    auto t_update = [&](int r0, int m, int k0, int K) {
+        return pp.timed(f64 ? "solve_panel_update<f64>" : "solve_panel_update<f32>", st, [&] {
+            update(r0, m, k0, K);
+            return cudaGetLastError();
+        });
+    };
+    auto t_big = [&](int r0, int m, int k0, int K) {
+        return pp.timed(f64 ? "solve_big_update<f64>" : "solve_big_update<f32>", st,
+                        [&] { return big_update(r0, m, k0, K); });
+    };
+    if (inv != nullptr) {
+        // X[p0 : pe] <- op(Inv_q) X[p0 : pe] through the scratch T.  Non-conjugate: forward
+        // by L_q^{-1} (slot 0), backward by U_q^{-1} (slot 1); conjugate: forward by
+        // (U_q^H)^{-1} = (U_q^{-1})^H, backward by (L_q^{-1})^H.  A padded panel's inverse
+        // is block diagonal with the identity, so its leading nb x nb block is the inverse
+        // of the panel itself.
+        const int B = inv->B;
+        const int64_t bb = (int64_t)B * B, dstride = (int64_t)inv->npan * 2 * bb;
+        cx<T> *Ts = static_cast<cx<T> *>(inv->T);
+        const cx<T> one{T(1), T(0)};
+        auto apply = [&](int q, bool lower) -> cudaError_t {
+            const int p0 = q * B, nb = std::min(B, n - p0);
+            const cx<T> *D = static_cast<const cx<T> *>(inv->inv) + (int64_t)q * 2 * bb + ((lower != conj) ? 0 : bb);
+            cx<T> *xp = X + (int64_t)p0 * kc;
+            return pp.timed(f64 ? "solve_diag<f64>" : "solve_diag<f32>", st, [&]() -> cudaError_t {
+                if (!conj)
+                    cgemm_launch<T, cx<T>, false, false>(nb, kc, nb, one, T(0), D, B, dstride, xp, kc, xstride, Ts, kc,
+                                                         (int64_t)B * kc, 1, batch, st);
+                else
+                    cgemm_launch<T, cx<T>, true, false>(nb, kc, nb, one, T(0), D, B, dstride, xp, kc, xstride, Ts, kc,
+                                                        (int64_t)B * kc, 1, batch, st);
+                EXPM_TRY(cudaGetLastError());
+                const size_t w = (size_t)nb * kc * sizeof(cx<T>), dp = (size_t)xstride * sizeof(cx<T>),
+                             sp = (size_t)B * kc * sizeof(cx<T>);
+                if (dp <= (size_t)INT32_MAX)
+                    return cudaMemcpy2DAsync(xp, dp, Ts, sp, w, (size_t)batch, cudaMemcpyDeviceToDevice, st);
+                for (int z = 0; z < batch; ++z)  // pitches past the 2-D copy's limit: one copy per entry
+                    EXPM_TRY(cudaMemcpyAsync(xp + z * xstride, Ts + (int64_t)z * B * kc, w, cudaMemcpyDeviceToDevice,
+                                             st));
+                return cudaSuccess;
+            });
+        };
+        const int npan = (n + B - 1) / B;
+        if (sweeps & 1)
+            for (int q = 0; q < npan; ++q) {
+                const int p0 = q * B, pe = std::min(n, p0 + B);
+                EXPM_TRY(apply(q, true));
+                if (n - pe > 0) EXPM_TRY(t_big(pe, n - pe, p0, pe - p0));
+            }
+        if (sweeps & 2)
+            for (int q = npan - 1; q >= 0; --q) {
+                const int p0 = q * B, pe = std::min(n, p0 + B);
+                EXPM_TRY(apply(q, false));
+                if (p0 > 0) EXPM_TRY(t_big(0, p0, p0, pe - p0));
+            }
+        return cudaGetLastError();
+    }
     // forward sweep (unit L, or U^H)
-    for (int p0 = 0; p0 < n; p0 += PNB) {
-        const int pe = std::min(n, p0 + PNB);
-        for (int p = p0; p < pe; p += DN_NB) {
-            const int nb = std::min(DN_NB, pe - p);
-            trsm(p, nb, true);
-            if (pe - p - nb > 0) update(p + nb, pe - p - nb, p, nb);
+    if (sweeps & 1)
+        for (int p0 = 0; p0 < n; p0 += PNB) {
+            const int pe = std::min(n, p0 + PNB);
+            for (int p = p0; p < pe; p += DN_NB) {
+                const int nb = std::min(DN_NB, pe - p);
+                EXPM_TRY(t_trsm(p, nb, true));
+                if (pe - p - nb > 0) EXPM_TRY(t_update(p + nb, pe - p - nb, p, nb));
+            }
+            if (n - pe > 0) EXPM_TRY(t_big(pe, n - pe, p0, pe - p0));
         }
-        if (n - pe > 0) EXPM_TRY(big_update(pe, n - pe, p0, pe - p0));
-    }
     // backward sweep (U, or unit L^H), panels from the bottom
-    for (int pe = n; pe > 0; pe -= PNB) {
-        const int p0 = std::max(0, pe - PNB);
-        const int nblk = (pe - p0 + DN_NB - 1) / DN_NB;
-        for (int bi = nblk - 1; bi >= 0; --bi) {
-            const int p = p0 + bi * DN_NB, nb = std::min(DN_NB, pe - p);
-            trsm(p, nb, false);
-            if (p > p0) update(p0, p - p0, p, nb);
+    if (sweeps & 2)
+        for (int pe = n; pe > 0; pe -= PNB) {
+            const int p0 = std::max(0, pe - PNB);
+            const int nblk = (pe - p0 + DN_NB - 1) / DN_NB;
+            for (int bi = nblk - 1; bi >= 0; --bi) {
+                const int p = p0 + bi * DN_NB, nb = std::min(DN_NB, pe - p);
+                EXPM_TRY(t_trsm(p, nb, false));
+                if (p > p0) EXPM_TRY(t_update(p0, p - p0, p, nb));
+            }
+            if (p0 > 0) EXPM_TRY(t_big(0, p0, p0, pe - p0));
         }
-        if (p0 > 0) EXPM_TRY(big_update(0, p0, p0, pe - p0));
-    }
     return cudaGetLastError();
 }
 
@@ -682,8 +763,8 @@ static cudaError_t lu_solve(int n, int kc, int batch, const cx<T> *F, int64_t fs
 // R binary64 and D binary32 (mixed)].  The factor part depends only on A, t, c and
 // the poles and can be kept for later right-hand sides.
 struct DenseLayout {
-    size_t amax, umax, F, tcA, tcB, tcflag, factor_total;  // factor part
-    size_t rn2, xn2, an2, ctl, X, R, D, oz, stA, stB, sterr, solve_total;  // solve part (offsets from its own base)
+    size_t amax, umax, F, tcA, tcB, tcflag, P, inv, factor_total;             // factor part
+    size_t rn2, xn2, an2, ctl, X, R, D, oz, stA, stB, sterr, Ts, solve_total;  // solve part (offsets from its own base)
 };
 static inline size_t align_up(size_t x) { return (x + 255) & ~size_t(255); }
 
@@ -697,6 +778,21 @@ static bool dense_uses_oz(const DenseGeom &g) {
 // Binary32 triangular solves with many columns in bf16x3 mode: panel updates on the
 // tensor cores.
 static bool dense_tc_solves(const DenseGeom &g) { return g.mixed && g.tc == 2 && g.kc > 8; }
+
+// Diagonal-panel inverses of the wide solves: panels of B = min(n, 128) rows, used for
+// every solve that does not take the fused narrow kernel (as long as the (factor, panel)
+// pairs fit one grid dimension of the inversion).  128 rather than 256: the residual a
+// product by an explicit inverse leaves grows with the inverted block's condition, and
+// with 128-row blocks the binary32 solves refine as well as substitution does.
+constexpr int DN_IB = 128;
+static int inv_block(int n) { return std::min(n, DN_IB); }
+
+bool dense_uses_inv(const DenseGeom &g) {
+    const size_t smn = g.mixed ? narrow_smem_bytes<float>(g.n, g.kc) : narrow_smem_bytes<double>(g.n, g.kc);
+    if (g.kc <= 8 && smn <= (200u << 10)) return false;
+    const int B = inv_block(g.n);
+    return (int64_t)g.ninst * g.npairs * ((g.n + B - 1) / B) <= 65535;
+}
 
 static DenseLayout dense_layout(const DenseGeom &g) {
     DenseLayout L{};
@@ -712,6 +808,13 @@ static DenseLayout dense_layout(const DenseGeom &g) {
         L.tcA = off; off += align_up(npz * (size_t)g.n * 6 * kw * sizeof(float));
         L.tcB = off; off += align_up(npz * (size_t)g.n * 2 * 6 * kw * sizeof(float));
         L.tcflag = off; off += align_up(sizeof(int));
+    }
+    const size_t es = g.mixed ? sizeof(cx<float>) : sizeof(cx<double>);
+    L.P = L.inv = off;
+    if (dense_uses_inv(g)) {  // the gathered panels, then the two inverses of each
+        const size_t B = inv_block(g.n), blocks = npz * ((g.n + B - 1) / B);
+        L.P = off; off += align_up(blocks * B * B * es);
+        L.inv = off; off += align_up(2 * blocks * B * B * es);
     }
     L.factor_total = off;
     off = 0;
@@ -736,6 +839,9 @@ static DenseLayout dense_layout(const DenseGeom &g) {
         L.stB = off; off += 2 * align_up(batch * 2 * (size_t)g.kc * kr * sizeof(uint16_t));
         L.sterr = off; off += align_up(sizeof(int));
     }
+    L.Ts = off;
+    if (dense_uses_inv(g))  // one product scratch per concurrently running half
+        off += 2 * align_up((size_t)g.ninst * g.npairs * inv_block(g.n) * g.kc * es);
     L.solve_total = off;
     return L;
 }
@@ -790,24 +896,27 @@ static cudaStream_t aux_stream() {
 
 template <class T>
 static cudaError_t solve_systems(const DenseGeom &g, const cx<T> *F, cx<T> *X, int64_t xstride, cudaStream_t st,
-                                 Profiler &prof, const int *skip = nullptr, const SolveTc *tcs = nullptr) {
+                                 Profiler &prof, const int *skip = nullptr, const SolveTc *tcs = nullptr,
+                                 const SolveInv *inv = nullptr) {
     const int64_t fs = (int64_t)g.n * g.n;
     const int batch = g.ninst * g.npairs;
     const char *name = sizeof(T) == 8 ? "lu_solve<f64>" : "lu_solve<f32>";
-    Profiler quiet;  // the inner launches are timed as a whole here
+    Profiler quiet;  // the whole solve is timed here, its parts by lu_solve
     // tcs (optional): two scratch sets, one per concurrently running half
     const SolveTc *tc0 = tcs, *tc1 = tcs != nullptr ? tcs + 1 : nullptr;
+    const SolveInv *iv0 = inv, *iv1 = inv != nullptr ? inv + 1 : nullptr;  // likewise the inverse scratch
     if (!g.complex_a)
         return prof.timed(name, st, [&] {
-            return lu_solve<T>(g.n, g.kc, batch, F, fs, false, X, xstride, st, quiet, skip, tc0);
+            return lu_solve<T>(g.n, g.kc, batch, F, fs, false, X, xstride, st, quiet, skip, tc0, &prof, iv0);
         });
     // systems 2s (theta) and 2s+1 (conj theta) of every instance share factor s: the
     // even and the odd systems each form a batch with stride 2*xstride
     cudaStream_t aux = aux_stream();
     if (!aux)
         return prof.timed(name, st, [&]() -> cudaError_t {
-            EXPM_TRY(lu_solve<T>(g.n, g.kc, batch, F, fs, false, X, 2 * xstride, st, quiet, skip, tc0));
-            return lu_solve<T>(g.n, g.kc, batch, F, fs, true, X + xstride, 2 * xstride, st, quiet, skip, tc0);
+            EXPM_TRY(lu_solve<T>(g.n, g.kc, batch, F, fs, false, X, 2 * xstride, st, quiet, skip, tc0, &prof, iv0));
+            return lu_solve<T>(g.n, g.kc, batch, F, fs, true, X + xstride, 2 * xstride, st, quiet, skip, tc0,
+                               &prof, iv0);
         });
     // the two halves are independent and run concurrently (fork / join through events,
     // so the work stays ordered on st for the caller; also inside a stream capture)
@@ -817,14 +926,35 @@ static cudaError_t solve_systems(const DenseGeom &g, const cx<T> *F, cx<T> *X, i
         cudaError_t e = cudaEventCreateWithFlags(&join, cudaEventDisableTiming);
         if (e == cudaSuccess) e = cudaEventRecord(fork, st);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(aux, fork, 0);
-        if (e == cudaSuccess) e = lu_solve<T>(g.n, g.kc, batch, F, fs, false, X, 2 * xstride, st, quiet, skip, tc0);
         if (e == cudaSuccess)
-            e = lu_solve<T>(g.n, g.kc, batch, F, fs, true, X + xstride, 2 * xstride, aux, quiet, skip, tc1);
+            e = lu_solve<T>(g.n, g.kc, batch, F, fs, false, X, 2 * xstride, st, quiet, skip, tc0, &prof, iv0);
+        if (e == cudaSuccess)
+            e = lu_solve<T>(g.n, g.kc, batch, F, fs, true, X + xstride, 2 * xstride, aux, quiet, skip, tc1, &prof, iv1);
         if (e == cudaSuccess) e = cudaEventRecord(join, aux);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(st, join, 0);
         cudaEventDestroy(fork);
         cudaEventDestroy(join);
         return e;
+    });
+}
+
+// L_q^{-1} and U_q^{-1} of every diagonal panel of every factor: the panels gathered
+// into B x B blocks (identity-padded), then one forward and one backward blocked solve
+// on identities, all (factor, panel) blocks as one batch.
+template <class T>
+static cudaError_t invert_panels(const DenseGeom &g, const cx<T> *F, cx<T> *P, cx<T> *Inv, cudaStream_t st,
+                                 Profiler &prof) {
+    const int B = inv_block(g.n), npan = (g.n + B - 1) / B, npz = g.ninst * g.npairs;
+    const int64_t bb = (int64_t)B * B;
+    return prof.timed(sizeof(T) == 8 ? "invert_panels<f64>" : "invert_panels<f32>", st, [&]() -> cudaError_t {
+        const unsigned gx = (unsigned)std::min<int64_t>((bb + 255) / 256, 64);
+        gather_diag_panels<T><<<dim3(gx, npan, npz), 256, 0, st>>>(g.n, B, npan, F, (int64_t)g.n * g.n, P, Inv);
+        EXPM_TRY(cudaGetLastError());
+        Profiler quiet;
+        const int batch = npz * npan;
+        EXPM_TRY(lu_solve<T>(B, B, batch, P, bb, false, Inv, 2 * bb, st, quiet, nullptr, nullptr, nullptr, nullptr, 1));
+        return lu_solve<T>(B, B, batch, P, bb, false, Inv + bb, 2 * bb, st, quiet, nullptr, nullptr, nullptr, nullptr,
+                           2);
     });
 }
 
@@ -834,13 +964,39 @@ cudaError_t dense_factor(const DenseGeom &g, const DenseIO &io, const DenseSyste
     unsigned char *p = (unsigned char *)fwork;
     unsigned *amax = (unsigned *)(p + L.amax);
     unsigned *umax = (unsigned *)(p + L.umax);
-    if (g.mixed && g.tc) {
-        TcScratch tc{(float *)(p + L.tcA), (float *)(p + L.tcB), (int *)(p + L.tcflag), g.tc == 2};
-        EXPM_TRY(cudaMemsetAsync(tc.err, 0, sizeof(int), st));
-        return factor_pairs<float>(g, io, sys, (cx<float> *)(p + L.F), amax, umax, st, prof, &tc);
+    const bool inv = dense_uses_inv(g);
+    if (g.mixed) {
+        cx<float> *F = (cx<float> *)(p + L.F);
+        if (g.tc) {
+            TcScratch tc{(float *)(p + L.tcA), (float *)(p + L.tcB), (int *)(p + L.tcflag), g.tc == 2};
+            EXPM_TRY(cudaMemsetAsync(tc.err, 0, sizeof(int), st));
+            EXPM_TRY(factor_pairs<float>(g, io, sys, F, amax, umax, st, prof, &tc));
+        } else {
+            EXPM_TRY(factor_pairs<float>(g, io, sys, F, amax, umax, st, prof));
+        }
+        if (inv) EXPM_TRY(invert_panels<float>(g, F, (cx<float> *)(p + L.P), (cx<float> *)(p + L.inv), st, prof));
+        return cudaSuccess;
     }
-    if (g.mixed) return factor_pairs<float>(g, io, sys, (cx<float> *)(p + L.F), amax, umax, st, prof);
-    return factor_pairs<double>(g, io, sys, (cx<double> *)(p + L.F), amax, umax, st, prof);
+    cx<double> *F = (cx<double> *)(p + L.F);
+    EXPM_TRY(factor_pairs<double>(g, io, sys, F, amax, umax, st, prof));
+    if (inv) EXPM_TRY(invert_panels<double>(g, F, (cx<double> *)(p + L.P), (cx<double> *)(p + L.inv), st, prof));
+    return cudaSuccess;
+}
+
+// the inverse part of a solve: the factor's inverses and this solve's two scratch halves
+static const SolveInv *solve_inv(const DenseGeom &g, const DenseLayout &L, const void *fwork, void *swork,
+                                 SolveInv out[2]) {
+    if (!dense_uses_inv(g)) return nullptr;
+    const int B = inv_block(g.n);
+    const size_t es = g.mixed ? sizeof(cx<float>) : sizeof(cx<double>);
+    const size_t half = align_up((size_t)g.ninst * g.npairs * B * g.kc * es);
+    for (int h = 0; h < 2; ++h) {
+        out[h].inv = (const unsigned char *)fwork + L.inv;
+        out[h].T = (unsigned char *)swork + L.Ts + h * half;
+        out[h].B = B;
+        out[h].npan = (g.n + B - 1) / B;
+    }
+    return out;
 }
 
 cudaError_t dense_growth(const DenseGeom &g, const void *fwork, cudaStream_t st, DenseResult *res) {
@@ -888,7 +1044,9 @@ cudaError_t dense_solve(const DenseGeom &g, const DenseIO &io, const DenseSystem
     if (!g.mixed) {
         load_rhs<double><<<dim3(gx, 1, nsz), 256, 0, st>>>(g.n, g.kc, io, g.nsys, X, nk);
         EXPM_TRY(cudaGetLastError());
-        EXPM_TRY(solve_systems<double>(g, (const cx<double> *)F, X, nk, st, prof));
+        SolveInv sv[2];
+        EXPM_TRY(solve_systems<double>(g, (const cx<double> *)F, X, nk, st, prof, nullptr, nullptr,
+                                       solve_inv(g, L, fwork, swork, sv)));
     } else {
         cx<double> *R = (cx<double> *)(p + L.R);
         cx<float> *D = (cx<float> *)(p + L.D);
@@ -907,6 +1065,8 @@ cudaError_t dense_solve(const DenseGeom &g, const DenseIO &io, const DenseSystem
             EXPM_TRY(cudaMemsetAsync(flag, 0, sizeof(int), st));
             tcs = stc;
         }
+        SolveInv siv[2];
+        const SolveInv *sinv = solve_inv(g, L, fwork, swork, siv);
         EXPM_TRY(cudaMemsetAsync(X, 0, (size_t)nsz * nk * sizeof(cx<double>), st));
         std::vector<double> h(2 * (size_t)nsz), an(g.ninst);
         // ||tA||_F of every instance for the relative residual of the stopping test
@@ -1022,7 +1182,7 @@ cudaError_t dense_solve(const DenseGeom &g, const DenseIO &io, const DenseSystem
                 for (int i = 0; i < g.ninst; ++i) res->inst_iters[i] = it - 1;
                 if (done || it > g.max_refine) break;
             }
-            EXPM_TRY(solve_systems<float>(g, (const cx<float> *)F, D, nk, st, prof, nullptr, tcs));
+            EXPM_TRY(solve_systems<float>(g, (const cx<float> *)F, D, nk, st, prof, nullptr, tcs, sinv));
             EXPM_TRY(prof.timed("add_correction", st, [&] {
                 add_correction<<<dim3(gx, 1, nsz), 256, 0, st>>>(nk, D, X, nk, nullptr);
                 return cudaGetLastError();

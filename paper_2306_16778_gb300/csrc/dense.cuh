@@ -84,6 +84,9 @@ cudaError_t dense_run(const DenseGeom &g, const DenseIO &io, const DenseSystems 
 // whether the fused narrow triangular solve (kc <= 8, solution in shared memory) takes
 // an n x kc right-hand side in binary32 -- the requirement of a devctl solve
 bool dense_narrow_fits(int n, int kc);
+// whether the solves of geometry g multiply by explicit inverses of the LU's diagonal
+// panels (kept in the factor part: factor parts with and without them differ)
+bool dense_uses_inv(const DenseGeom &g);
 // devctl form: factor + growth + solve fully enqueued on st (nothing read back); results to out
 cudaError_t dense_run_devctl(const DenseGeom &g, const DenseIO &io, const DenseSystems &sys, void *work,
                              cudaStream_t st, Profiler &prof, const DenseDevOut &out);

@@ -372,6 +372,34 @@ inline void cgemm_launch(int m, int n, int K, cx<T> alpha, T beta, const AE *A, 
     }
 }
 
+// ------------------------------------------------------------------ diagonal-panel inverses
+// The wide triangular solves multiply by explicit inverses of the LU's diagonal panels
+// (block triangular substitution with inverted diagonal blocks).  Panel q of batch entry z
+// covers rows and columns q B .. q B + nb - 1, nb = min(B, n - q B).  This kernel copies
+// it into the B x B block P[z][q] (packed unit-lower L and upper U, as in F), padded with
+// the identity past nb so that every block is a full B x B LU, and sets both inverse slots
+// Inv[z][q][0] (for L) and Inv[z][q][1] (for U) to the identity; the blocked solves on
+// those identities then leave L_q^{-1} and U_q^{-1} there.
+template <class T>
+__global__ void __launch_bounds__(256) gather_diag_panels(int n, int B, int npan, const cx<T> *__restrict__ F,
+                                                          int64_t fstride, cx<T> *__restrict__ P,
+                                                          cx<T> *__restrict__ Inv) {
+    const int q = blockIdx.y;
+    const int64_t z = blockIdx.z;
+    const int p0 = q * B, nb = min(B, n - p0);
+    const int64_t zq = z * npan + q, bb = (int64_t)B * B;
+    cx<T> *Pq = P + zq * bb;
+    cx<T> *Iq = Inv + zq * 2 * bb;
+    const cx<T> *Fq = F + z * fstride + (int64_t)p0 * n + p0;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < bb; e += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(e / B), j = (int)(e % B);
+        const cx<T> id = {i == j ? T(1) : T(0), T(0)};
+        Pq[e] = (i < nb && j < nb) ? Fq[(int64_t)i * n + j] : id;
+        Iq[e] = id;
+        Iq[bb + e] = id;
+    }
+}
+
 // ------------------------------------------------------------------ lu_solve_narrow
 // X <- (L U)^{-1} X (CONJ = false) or (L U)^{-H} X = U^{-H} L^{-H} X (CONJ = true) for an
 // LU stored in place (unit L below the diagonal, U on and above), at most 8 columns.

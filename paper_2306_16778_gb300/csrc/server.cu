@@ -269,8 +269,12 @@ Request *admit(expm_server_s *sv, Worker &w, FactorEntry **fe_out, bool *build_o
         Request *r = *it;
         // factor parts differ by precision: binary64; float-float; binary32 (the dense mixed
         // precisions share one binary32 LU; the tridiagonal binary32 factors are their own)
-        const int fprec = r->opts.prec == EXPM_FP64 ? 0
-                          : (r->opv.kind == EXPM_OP_TRIDIAG && r->opts.prec == EXPM_MIXED_FP32) ? 2 : 1;
+        int fprec = r->opts.prec == EXPM_FP64 ? 0
+                    : (r->opv.kind == EXPM_OP_TRIDIAG && r->opts.prec == EXPM_MIXED_FP32) ? 2 : 1;
+        // a dense factor part that carries the diagonal-panel inverses of the wide solves
+        // (more than 8 columns) is an entry of its own
+        if (r->opv.kind != EXPM_OP_TRIDIAG && dense_uses_inv(dense_geom(r->opv, r->plan, r->opts, r->k, r->v_cplx)))
+            fprec += 8;
         const FactorKey key{r->op, (const void *)r->plan, fprec, r->opts.t, r->opts.shift_c};
         auto ce = sv->cache.find(key);
         const bool cached = ce != sv->cache.end();

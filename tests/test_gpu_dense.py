@@ -91,6 +91,26 @@ def test_real_symmetric_with_real_and_complex_rhs(plans, prec):
     assert Yc.dtype == np.complex128 and matrix.rel_err(Yc, _oracle(A, Vc, 16)) <= tol
 
 
+@pytest.mark.parametrize("prec", [P.EXPM_FP64, P.EXPM_MIXED_FP32])
+@pytest.mark.parametrize("n", [40, 256, 520])
+def test_wide_solves_with_panel_inverses(plans, prec, n):
+    """More than 8 columns: the triangular solves multiply by the inverses of the LU's
+    128-row diagonal panels (one panel smaller than that, two full panels, four full panels
+    and an 8-row one); real symmetric A (one solve per pair) with a real and a complex
+    right-hand side, and the same columns solved narrow (4 at a time)."""
+    g = workloads.rng(315 + n)
+    A, Q, mu, V = workloads.dense_symmetric(n, -35.0, 0.0, 12, g, False)
+    tol = 1e-12 if prec == P.EXPM_FP64 else 1e-10
+    Y, info = _gpu(plans[16], A, V, prec)
+    Yo = _oracle(A, V, 16)
+    assert matrix.rel_err(Y, Yo) <= tol
+    Yn = np.concatenate([_gpu(plans[16], A, V[:, c:c + 4], prec)[0] for c in range(0, 12, 4)], axis=1)
+    assert matrix.rel_err(Yn, Yo) <= tol and matrix.rel_err(Y, Yn) <= 2 * tol
+    Vc = V + 1j * g.standard_normal(V.shape)
+    Yc, _ = _gpu(plans[12], A, Vc, prec)
+    assert matrix.rel_err(Yc, _oracle(A, Vc, 12)) <= tol
+
+
 def test_time_and_shift(plans):
     """e^c R_n(tA - cI)V with spectrum of tA in [0, 10] and c = 10 (Remark 3.2)."""
     g = workloads.rng(311)

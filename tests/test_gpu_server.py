@@ -89,6 +89,37 @@ def test_mixed_stream_same_alone_and_in_the_mix():
     server.close()
 
 
+def test_narrow_and_wide_requests_on_one_dense_operator():
+    """Requests of 3 and of 12 columns on one dense operator: the wide ones need the
+    factor part with the diagonal-panel inverses, the narrow ones the plain one; each must
+    equal the same computation done alone."""
+    g = workloads.rng(640)
+    plan = P.Plan(degree=16)
+    server = P.Server(hbm_budget_bytes=8 << 30, max_inflight=2)
+    A, Q, mu, _ = workloads.dense_symmetric(300, -40.0, 0.0, 1, g, True)
+    dA = torch.from_numpy(A).to(DEV)
+    oid = server.register_dense(dA)
+    reqs = []
+    for i, (k, prec) in enumerate([(3, P.EXPM_FP64), (12, P.EXPM_FP64), (12, P.EXPM_MIXED_FP32),
+                                   (3, P.EXPM_MIXED_FP32), (12, P.EXPM_FP64), (3, P.EXPM_FP64)]):
+        V = torch.from_numpy(workloads.request_rhs(300, k, 800 + i, True)).to(DEV)
+        reqs.append((V, prec))
+    outs = [torch.empty_like(V) for V, _ in reqs]
+    torch.cuda.synchronize()
+    tickets = [server.submit(oid, plan, V, y, prec=prec) for (V, prec), y in zip(reqs, outs)]
+    results = _wait(server, tickets)
+    th, a = coeffs.theta(16), coeffs.residues(16)
+    for (V, prec), y, tk in zip(reqs, outs, tickets):
+        assert results[tk][0] == 0
+        alone = torch.empty_like(y)
+        P.expm_apply_dense(plan, dA, V, alone, prec=prec)
+        torch.cuda.synchronize()
+        assert torch.equal(alone, y)
+        Yo, _ = matrix.apply_dense(A, V.cpu().numpy(), th, a)
+        assert matrix.rel_err(y.cpu().numpy(), Yo) <= (1e-12 if prec == P.EXPM_FP64 else 1e-8)
+    server.close()
+
+
 def test_server_rejections():
     server = P.Server(hbm_budget_bytes=1 << 20, max_inflight=1)
     plan = P.Plan(degree=16)
