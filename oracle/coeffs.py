@@ -18,7 +18,8 @@ Everything is done in Python ``decimal`` arithmetic with a working precision of
 at least 40 significant digits (more for large n), then rounded once to binary64.
 The paper's Fig. 4.1 caption uses coefficients computed with 32 significant
 digits and truncated to 16; rounding a >= 40-digit value to binary64 is that
-recipe with round-to-nearest (reading recorded in the design notes).
+recipe with round-to-nearest in place of truncation (the caption's "truncated" is
+read as "rounded to 16 digits": truncation would bias every coefficient downward).
 
 Root finding: the Weierstrass (Durand-Kerner) simultaneous iteration
     z_i <- z_i - q(z_i) / prod_{j != i} (z_i - z_j)
