@@ -296,6 +296,22 @@ int run_hook(bool bf16, int M, int N, int K, const void *A, int lda, const void 
     return h ? 2 : 0;
 }
 
+// The time-out path of the bounded waits, with nothing in flight: one thread waits on an
+// mbarrier that expects one arrival.  arrive = 0: nothing arrives, so mbar_wait gives up
+// after `limit` polls; arrive = 1: the thread arrives first and the wait succeeds.
+// status[0] = 1 if the wait gave up, status[1] = elapsed SM clocks / 1024.
+__global__ void wait_probe_kernel(long long limit, int arrive, int *status) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x != 0) return;
+    tcu::mbar_init(&bar, 1);
+    if (arrive) tcu::mbar_arrive(&bar);
+    const long long t0 = clock64();
+    const bool ok = mbar_wait(&bar, 0u, limit);
+    const long long dt = (clock64() - t0) >> 10;
+    status[0] = ok ? 0 : 1;
+    status[1] = (int)(dt < 0x7fffffffLL ? dt : 0x7fffffffLL);
+}
+
 }  // namespace
 
 bool tc_gemm_supported(int M, int N, int K, const void *A, int lda, const void *B, int ldb, const void *C, int ldc,
@@ -336,4 +352,21 @@ extern "C" int expm_internal_tc_gemm_tf32(int M, int N, int K, const float *A, i
 extern "C" int expm_internal_tc_gemm_bf16(int M, int N, int K, const uint16_t *A, int lda, const uint16_t *B, int ldb,
                                           float *C, int ldc) {
     return expm::run_hook(true, M, N, K, A, lda, B, ldb, C, ldc);
+}
+
+// Test hook: runs the probe above on the current device; returns 0 (the wait completed),
+// 2 (it gave up: the status the tensor-core kernels turn into EXPM_ETIMEOUT) or 1 (bad
+// arguments, CUDA error).  elapsed_kclk (host, optional) receives the wait's SM clocks / 1024.
+extern "C" int expm_internal_wait_probe(long long limit, int arrive, int *elapsed_kclk) {
+    if (limit < 1 || limit > expm::tcu::SPIN_LIMIT) return 1;
+    int *d = nullptr;
+    if (cudaMalloc(&d, 2 * sizeof(int)) != cudaSuccess) return 1;
+    expm::wait_probe_kernel<<<1, 32>>>(limit, arrive ? 1 : 0, d);
+    int h[2] = {0, 0};
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpy(h, d, sizeof(h), cudaMemcpyDeviceToHost);
+    cudaFree(d);
+    if (e != cudaSuccess) return 1;
+    if (elapsed_kclk) *elapsed_kclk = h[1];
+    return h[0] ? 2 : 0;
 }

@@ -11,7 +11,10 @@
 namespace expm {
 namespace tcu {
 
-constexpr long long SPIN_LIMIT = 1ll << 26;  // bounded mbarrier waits
+// Bounded mbarrier waits: a poll that finds the phase incomplete suspends for a
+// system-dependent time (measured on GB300: about 7,800 SM clocks, 3.8 us), so 2^18 polls
+// give up after about one second -- far beyond any stage hand-off of these kernels.
+constexpr long long SPIN_LIMIT = 1ll << 18;
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -28,10 +31,10 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
-// true once the phase with the given parity has completed; false after the spin limit
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+// true once the phase with the given parity has completed; false after `limit` polls
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, long long limit = SPIN_LIMIT) {
     const uint32_t addr = smem_u32(bar);
-    for (long long it = 0; it < SPIN_LIMIT; ++it) {
+    for (long long it = 0; it < limit; ++it) {
         uint32_t done;
         asm volatile(
             "{\n\t.reg .pred p;\n\t"

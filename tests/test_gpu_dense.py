@@ -184,6 +184,27 @@ def test_tensor_core_gemm_against_torch():
         assert err < 1e-5, (M, N, K, err)
 
 
+def test_bounded_wait_gives_up_and_reports(plans):
+    """The bounded mbarrier wait the tensor-core kernels use, on a barrier that nothing
+    completes (a flag nothing sets): it gives up after its poll limit and the host reads
+    the time-out status; with the arrival made first it completes.  The context stays
+    usable: a dense apply afterwards is still correct."""
+    import ctypes
+    f = P.lib.expm_internal_wait_probe
+    f.restype = ctypes.c_int
+    f.argtypes = [ctypes.c_longlong, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
+    kclk = ctypes.c_int(-1)
+    assert f(1 << 12, 1, ctypes.byref(kclk)) == 0
+    assert f(1 << 12, 0, ctypes.byref(kclk)) == 2
+    print(f"bounded wait: 4096 polls gave up after {kclk.value * 1024} SM clocks")
+    assert kclk.value >= 0
+    assert f(0, 0, None) == 1 and f((1 << 18) + 1, 0, None) == 1  # limits outside [1, 2^18]
+    g = workloads.rng(318)
+    A, Q, mu, V = workloads.dense_symmetric(96, -20.0, 0.0, 2, g, True)
+    Y, info = _gpu(plans[12], A, V, P.EXPM_MIXED_FP32)
+    assert info.status_worst == 0 and matrix.rel_err(Y, _oracle(A, V, 12)) <= 1e-10
+
+
 def test_tensor_core_gemm_bf16_against_torch():
     """The tcgen05 kind::f16 kernel with bf16 operands: C -= A B^T equals the product of
     the bf16 operands (exact in binary32 per term; float64 reference) to fp32
