@@ -553,9 +553,20 @@ cudaError_t oz_split_d(int n, int kc, int nsys, int complex_a, const cx<float> *
     return cudaGetLastError();
 }
 
+// every product within the slice counts and accumulators, ordered by p + q, and the
+// last accumulator used
+template <class Cfg> constexpr bool oz_tables_ok() {
+    for (int i = 0; i < Cfg::NPAIR; ++i) {
+        if (Cfg::pp(i) >= Cfg::SA || Cfg::qq(i) >= Cfg::SB || Cfg::acc(i) >= Cfg::NACC) return false;
+        if (i > 0 && Cfg::pp(i) + Cfg::qq(i) < Cfg::pp(i - 1) + Cfg::qq(i - 1)) return false;
+    }
+    return Cfg::acc(Cfg::NPAIR - 1) == Cfg::NACC - 1;
+}
+
 template <class Cfg>
 static cudaError_t oz_launch(int n, int kc, int nsys, int complex_a, double t, int64_t nk, cx<double> *R, void *ws,
                              cudaStream_t st, int *timeout) {
+    static_assert(oz_tables_ok<Cfg>(), "slice-product tables");
     const OzLayout L = oz_layout(n, kc, nsys, complex_a);
     unsigned char *b = (unsigned char *)ws;
     int *F = (int *)(b + L.F), *flag = (int *)(b + L.flag);
