@@ -242,10 +242,17 @@ expm_status expm_apply_tridiag_noalloc(expm_plan plan, int64_t N, const double *
  *                 ||R_k||_F <= tol (||tA||_F + |theta_k - c|) ||X_k||_F, at most
  *                 max_refine sweeps); growth_max bounds max|U| / max|tA - cI + theta I|.
  *   info          optional: refinement sweeps, worst relative residual, worst growth.
+ * Device workspace (held by the plan, grown on demand): the factors, n^2 complex per
+ * pole pair (binary64, or binary32 in the mixed modes); for k > 8 also the inverses of
+ * the factors' 128-row diagonal panels (the triangular solves multiply by them), about
+ * 3 n min(n, 128) complex per pair; the solutions (and, mixed, residuals and corrections)
+ * n k complex per solved pole; the tensor-core modes' split operands.
  * The call synchronises opts->stream before returning (it reads back the growth
  * factors and, in mixed precision, the residual norms).  Returns EXPM_EGROWTH if a
  * growth factor exceeds growth_max, EXPM_ENOCONV if refinement did not reach tol
- * (Y is written in both cases), EXPM_EINVAL for bad sizes.
+ * (Y is written in both cases), EXPM_ETIMEOUT if a bounded wait inside a tensor-core
+ * kernel gave up (about one second without progress; Y is not valid), EXPM_EINVAL for
+ * bad sizes.
  */
 expm_status expm_apply_dense(expm_plan plan, int n, const void *A, int lda, int a_is_complex, const void *V,
                              int ldv, int k, int v_is_complex, void *Y, int ldy, const expm_opts *opts,
