@@ -15,7 +15,10 @@
 //
 // Blocked right-looking LU, panel width DN_NB, per step: diagonal-block LU,
 // the two panel triangular solves, and the trailing update as a batched complex
-// GEMM (all pole pairs in one launch).
+// GEMM (all pole pairs in one launch).  Triangular solves with more than 8 columns
+// multiply each 128-row diagonal panel by its explicit inverse (formed once per
+// factorization, all panels of all factors as one batch) and update the rows past the
+// panel with one batched GEMM; up to 8 columns, one fused kernel per system.
 #include <cmath>
 #include <cstdio>
 #include <algorithm>
