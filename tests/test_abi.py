@@ -39,6 +39,19 @@ def test_every_declared_symbol_is_exported(P):
     assert not missing, f"declared but not exported: {missing}"
 
 
+def test_every_public_export_is_declared(P):
+    """The reverse: every exported expm_* entry point other than the expm_internal_* test
+    hooks is declared (and documented) in include/*.h."""
+    import subprocess
+    out = subprocess.run(["nm", "-D", "--defined-only", P.library_path], capture_output=True, text=True)
+    if out.returncode != 0:
+        pytest.skip("nm not available")
+    exported = {ln.split()[-1] for ln in out.stdout.splitlines() if ln.split() and ln.split()[-1].startswith("expm_")}
+    public = {n for n in exported if not n.startswith("expm_internal_")}
+    undeclared = sorted(public - set(_declared_functions()))
+    assert not undeclared, f"exported but not declared: {undeclared}"
+
+
 @pytest.mark.parametrize("n", [2, 4, 8, 12, 16, 20, 24, 32, 40, 48, 56])
 def test_library_coefficients_equal_oracle(P, n):
     """The library's double-double Aberth-Ehrlich coefficients, rounded to
