@@ -209,7 +209,7 @@ def run_peaks():
     lib.expm_probe_fma_tflops.restype = ctypes.c_double
     lib.expm_probe_fma_tflops.argtypes = [ctypes.c_int] * 4
     out = {}
-    for kind, name, iters in ((0, "fp64", 200), (1, "fp32", 4000)):
+    for kind, name, iters in ((0, "fp64", 200), (1, "fp32", 4000), (2, "fp32x2", 2000)):
         for bps in (4, 8, 16):
             tf = lib.expm_probe_fma_tflops(kind, iters, bps, 5)
             out[f"{name}_tflops_bps{bps}"] = round(tf, 4)
