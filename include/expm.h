@@ -204,8 +204,14 @@ expm_status expm_apply_tridiag(expm_plan plan, int64_t N, const double *d, const
  *   N * (400 + 136 r) bytes for degree 16 and r >= 2 real right-hand sides, so N up
  *   to about 22,000 for r = 8).
  *   Set-up: the first call on each device looks up the array's device address
- *   (cudaGetSymbolAddress) with that device current; make that first call before any
- *   stream capture.
+ *   (cudaGetSymbolAddress) with that device current and caches it.  With CUDA's lazy
+ *   module loading (the default) that first lookup is also when the library's module,
+ *   and with it the fixed array, is loaded onto the device: the first call may
+ *   allocate device memory and synchronise.  Callers that need no allocation at all
+ *   should make one warm-up call at start-up, outside any stream capture and any
+ *   latency-critical loop; later calls allocate nothing.  The cached address belongs
+ *   to the device's current context: after cudaDeviceReset in the same process the
+ *   library must not be used on that device again (the cache is not refreshed).
  *   Sharing: all calls on a device share the one array and it keeps whatever the last
  *   call left in it (every kernel writes the scratch it later reads; nothing needs to
  *   start at zero).  Calls whose work overlaps on the GPU -- different streams, or
@@ -388,6 +394,10 @@ expm_status expm_batched_graph_destroy(expm_batch_graph graph);
  * Factorizations (tridiagonal block LUs and spikes; dense per-pair LUs) are cached per
  * (operator, plan, precision class, t, c), counted in the budget and evicted least
  * recently used; a request whose factorization is cached runs only its solve part.
+ * Plans are told apart by an id that is never reused (a plan destroyed and another
+ * created at the same address do not share factors); a factorization whose build
+ * failed is dropped once unused, so the next request rebuilds it.  A worker thread that
+ * has stopped between requests is restarted by the next submit or poll.
  * Each result depends only on its own inputs (deterministic kernels, no reduction
  * across requests), so it is the same alone and in the mix.
  *
@@ -397,8 +407,9 @@ expm_status expm_batched_graph_destroy(expm_batch_graph graph);
  *   expm_server_register_op  desc: EXPM_OP_TRIDIAG (d, e as in expm_apply_tridiag;
  *                          real e only) or EXPM_OP_DENSE (A, lda, a_is_complex); the
  *                          data may be host or device memory and is copied.
- *   expm_server_submit     V and Y device memory, valid until poll reports the request
- *                          finished; 1 <= k <= 64; opts as for the matching apply call
+ *   expm_server_submit     V and Y device memory (EXPM_EINVAL otherwise), valid until
+ *                          poll reports the request finished, as is the plan; 1 <= k <= 64;
+ *                          opts as for the matching apply call
  *                          (opts->stream is ignored).  EXPM_EAGAIN when the queue is
  *                          full, EXPM_ENOMEM when one request exceeds the whole budget,
  *                          EXPM_ENOTFOUND for an unknown operator.
@@ -427,6 +438,10 @@ expm_status expm_server_submit(expm_server server, uint64_t op_id, const expm_pl
                                int v_is_complex, void *Y, const expm_opts *opts, uint64_t *ticket);
 expm_status expm_server_poll(expm_server server, uint64_t ticket, expm_info *info, double ts[4]);
 expm_status expm_server_destroy(expm_server server);
+/*   expm_server_set_queue_limit  at most max_queue requests wait for admission (default
+ *                          2^16, 1 <= max_queue <= 2^20); a submit beyond it returns
+ *                          EXPM_EAGAIN and queues nothing (the caller retries later). */
+expm_status expm_server_set_queue_limit(expm_server server, int max_queue);
 
 /*
  * Measurement hooks (no counterpart in the paper).  When enabled on a plan, every

@@ -111,6 +111,13 @@ def _load() -> ctypes.CDLL:
     L.expm_server_poll.restype = i
     L.expm_server_destroy.argtypes = [vp]
     L.expm_server_destroy.restype = i
+    L.expm_server_set_queue_limit.argtypes = [vp, i]
+    L.expm_server_set_queue_limit.restype = i
+    for hook in ("expm_internal_server_fail_next_factor", "expm_internal_server_workers_alive"):
+        getattr(L, hook).argtypes = [vp]
+        getattr(L, hook).restype = i
+    L.expm_internal_server_stop_worker.argtypes = [vp, i]
+    L.expm_internal_server_stop_worker.restype = i
     L.expm_profile_enable.argtypes = [vp, i]
     L.expm_profile_enable.restype = i
     L.expm_profile_read.argtypes = [vp, i, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(ctypes.c_int64),
@@ -448,6 +455,9 @@ class Server:
                                       ctypes.byref(o), ctypes.byref(tk)), "expm_server_submit")
         self._keep[int(tk.value)] = (V, Y, plan)
         return int(tk.value)
+
+    def set_queue_limit(self, max_queue: int) -> None:
+        _check(lib.expm_server_set_queue_limit(self._h, int(max_queue)), "expm_server_set_queue_limit")
 
     def poll(self, ticket: int):
         """None while pending, else (status, expm_info, timestamps[4])."""

@@ -1,5 +1,6 @@
 // api.cu -- the C interface declared in include/expm.h: plans, validation,
 // host/device staging and dispatch to the kernels.
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -192,6 +193,8 @@ expm_status expm_plan_create(const double *poles_ri, const double *residues_ri, 
         return set_error(EXPM_EINVAL, "plan_create: pole data does not satisfy R_n(0) = 1");
     expm_plan p = new (std::nothrow) expm_plan_s();
     if (!p) return set_error(EXPM_ENOMEM, "plan_create: host allocation");
+    static std::atomic<uint64_t> next_id{1};
+    p->id = next_id.fetch_add(1);
     p->degree = degree;
     p->lam.assign(poles_ri, poles_ri + 2 * degree);
     p->w.assign(residues_ri, residues_ri + 2 * degree);

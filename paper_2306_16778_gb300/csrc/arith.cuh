@@ -53,7 +53,11 @@ EXPM_D f32x2 operator*(f32x2 x, f32x2 y) {
     float cl3 = __fadd_rn(cl, cl2);
     return fast_two_sum(ch, cl3);
 }
-// reciprocal: binary32 seed, one Newton step carried out in double-word
+// reciprocal: binary32 seed r0 = 1/y_hi, then one Newton-Raphson step for the reciprocal,
+// r1 = r0 + r0 (1 - y r0) (the correction used for division by Markstein, IBM J. Res. Dev.
+// 34(1), 1990), carried out in double-word arithmetic as in the reciprocal and division
+// algorithms of Joldes, Muller and Popescu (ACM TOMS 2017): one step doubles the ~24
+// correct bits of the seed, which is the precision of the pair.
 EXPM_D f32x2 recip(f32x2 y) {
     float r0 = __frcp_rn(y.hi);
     f32x2 r = {r0, 0.f};

@@ -1,6 +1,7 @@
 // plan.cuh -- the opaque plan object behind expm_plan and shared host helpers.
 #pragma once
 #include <cuda_runtime.h>
+#include <stdint.h>
 
 #include <string>
 #include <vector>
@@ -39,6 +40,7 @@ struct Profiler {
 }  // namespace expm
 
 struct expm_plan_s {
+    uint64_t id = 0;          // unique per plan over the process (never reused, unlike the address)
     int degree = 0;
     int device = 0;
     int sm_count = 0;

@@ -7,9 +7,14 @@
 // that arrives while others run is admitted when a worker and enough memory are free,
 // and its kernels overlap on the device with the others'.  Factorizations (the
 // per-pole block LUs and spikes of the tridiagonal path, the per-pair LUs of the dense
-// path) are kept resident in an LRU cache keyed by (operator, plan, precision, t, c)
+// path) are kept resident in an LRU cache keyed by (operator, plan id, precision, t, c)
 // and counted in the budget; a request finding its factor part cached runs only the
-// solve part.  A factor part is built once, by the worker that first needs it, on
+// solve part.  The plan id is unique over the process, so a plan destroyed and another
+// created at the same address never meets the first one's factors; an entry whose build
+// failed or whose tensor-core waits gave up is dropped as soon as no request uses it,
+// so the next request for that operator rebuilds it.  Workers are supervised: a worker
+// thread found stopped (between requests) is joined and started again by the next
+// submit or poll, and the queued requests go on.  A factor part is built once, by the worker that first needs it, on
 // its own stream; other workers order their use after it with a CUDA event, without
 // blocking the host.  Each request's result depends only on its own inputs -- the
 // kernels are deterministic and nothing is reduced across requests -- so it is the
@@ -46,11 +51,12 @@ struct Op {
     size_t bytes = 0;
 };
 
-using FactorKey = std::tuple<uint64_t, const void *, int, double, double>;  // op, plan, prec, t, c
+using FactorKey = std::tuple<uint64_t, uint64_t, int, double, double>;  // op, plan id, prec, t, c
 
 struct FactorEntry {
     void *buf = nullptr;
     size_t bytes = 0;
+    int degree = 0;              // the plan degree it was built for (a hit must match it and `bytes`)
     cudaEvent_t done = nullptr;  // recorded after the factor kernels
     bool ready = false;          // kernels enqueued and `done` recorded
     bool failed = false;
@@ -82,6 +88,8 @@ struct Worker {
     cudaStream_t stream = nullptr;
     void *work = nullptr;
     size_t work_bytes = 0;
+    bool alive = false;          // its thread runs worker_loop (server lock)
+    bool stop_after = false;     // test hook: leave the loop after the current request
 };
 
 }  // namespace
@@ -96,6 +104,7 @@ struct expm_server_s {
     size_t in_use = 0;  // admitted solve scratch + cached factor parts
     int max_inflight = 1;
     int max_queue = 1 << 16;
+    bool fail_next_factor = false;  // test hook: the next factor build reports a failure
     Clock::time_point t0;
     std::mutex mu;
     std::condition_variable cv;
@@ -171,6 +180,15 @@ DenseIO dense_io(const Op &op, const Request &r) {
     return io;
 }
 
+// The test hook of expm_internal_server_fail_next_factor: true once, for the first
+// factor build after it was set (the build is then reported as failed).
+bool take_fail_hook(expm_server_s *sv) {
+    std::lock_guard<std::mutex> lk(sv->mu);
+    const bool f = sv->fail_next_factor;
+    sv->fail_next_factor = false;
+    return f;
+}
+
 // Marks a factor part as usable by other workers (its kernels are enqueued and its
 // event recorded, or its build failed).
 void publish(expm_server_s *sv, FactorEntry &fe, bool failed) {
@@ -200,6 +218,7 @@ void run_request(expm_server_s *sv, Worker &w, Request &r, FactorEntry &fe, bool
         if (build) {
             err = tri_mixed_factor(g, d, d + op.n, ps, fe.buf, w.stream, off);
             if (err == cudaSuccess) err = cudaEventRecord(fe.done, w.stream);
+            if (err == cudaSuccess && take_fail_hook(sv)) err = cudaErrorUnknown;
             publish(sv, fe, err != cudaSuccess);
         } else {
             err = fe.failed ? cudaErrorUnknown : cudaStreamWaitEvent(w.stream, fe.done, 0);
@@ -223,6 +242,7 @@ void run_request(expm_server_s *sv, Worker &w, Request &r, FactorEntry &fe, bool
         if (build) {
             err = tri_factor(g, ff, d, d + op.n, ps, fe.buf, w.stream, off);
             if (err == cudaSuccess) err = cudaEventRecord(fe.done, w.stream);
+            if (err == cudaSuccess && take_fail_hook(sv)) err = cudaErrorUnknown;
             publish(sv, fe, err != cudaSuccess);
         } else {
             err = fe.failed ? cudaErrorUnknown : cudaStreamWaitEvent(w.stream, fe.done, 0);
@@ -239,6 +259,7 @@ void run_request(expm_server_s *sv, Worker &w, Request &r, FactorEntry &fe, bool
             err = dense_factor(g, io, sys, fe.buf, w.stream, off);
             if (err == cudaSuccess) err = dense_growth(g, fe.buf, w.stream, &fe.growth);
             if (err == cudaSuccess) err = cudaEventRecord(fe.done, w.stream);
+            if (err == cudaSuccess && take_fail_hook(sv)) err = cudaErrorUnknown;
             publish(sv, fe, err != cudaSuccess);
         } else {
             err = fe.failed ? cudaErrorUnknown : cudaStreamWaitEvent(w.stream, fe.done, 0);
@@ -263,6 +284,18 @@ void run_request(expm_server_s *sv, Worker &w, Request &r, FactorEntry &fe, bool
     r.ts[3] = sv->now();
 }
 
+// Frees a cache entry that no request uses (its kernels are finished or never ran).
+// Lock held.
+void drop_entry(expm_server_s *sv, std::map<FactorKey, FactorEntry>::iterator it) {
+    if (it->second.done) {
+        cudaEventSynchronize(it->second.done);
+        cudaEventDestroy(it->second.done);
+    }
+    if (it->second.buf) cudaFree(it->second.buf);
+    sv->in_use -= it->second.bytes;
+    sv->cache.erase(it);
+}
+
 // Picks the first queued request that fits; reserves its memory.  Lock held.
 Request *admit(expm_server_s *sv, Worker &w, FactorEntry **fe_out, bool *build_out) {
     for (auto it = sv->queue.begin(); it != sv->queue.end(); ++it) {
@@ -275,8 +308,15 @@ Request *admit(expm_server_s *sv, Worker &w, FactorEntry **fe_out, bool *build_o
         // (more than 8 columns) is an entry of its own
         if (r->opv.kind != EXPM_OP_TRIDIAG && dense_uses_inv(dense_geom(r->opv, r->plan, r->opts, r->k, r->v_cplx)))
             fprec += 8;
-        const FactorKey key{r->op, (const void *)r->plan, fprec, r->opts.t, r->opts.shift_c};
+        const FactorKey key{r->op, r->plan->id, fprec, r->opts.t, r->opts.shift_c};
         auto ce = sv->cache.find(key);
+        if (ce != sv->cache.end() && ce->second.ready &&
+            (ce->second.degree != r->plan->degree || ce->second.bytes != r->factor_bytes)) {
+            // not this request's factorization: drop it once unused, build a fresh one
+            if (ce->second.users > 0) continue;
+            drop_entry(sv, ce);
+            ce = sv->cache.end();
+        }
         const bool cached = ce != sv->cache.end();
         if (cached && !ce->second.ready) continue;  // its factor is being built: wait for it
         const size_t grow = r->solve_bytes > w.work_bytes ? r->solve_bytes - w.work_bytes : 0;
@@ -289,11 +329,7 @@ Request *admit(expm_server_s *sv, Worker &w, FactorEntry **fe_out, bool *build_o
                     (victim == sv->cache.end() || c->second.last_use < victim->second.last_use))
                     victim = c;
             if (victim == sv->cache.end()) break;
-            cudaEventSynchronize(victim->second.done);
-            cudaFree(victim->second.buf);
-            cudaEventDestroy(victim->second.done);
-            sv->in_use -= victim->second.bytes;
-            sv->cache.erase(victim);
+            drop_entry(sv, victim);
         }
         if (sv->in_use + need > sv->budget) continue;
         // admitted: grow the worker's scratch, create the cache entry if needed
@@ -314,6 +350,7 @@ Request *admit(expm_server_s *sv, Worker &w, FactorEntry **fe_out, bool *build_o
         if (!cached) {
             FactorEntry fe;
             fe.bytes = r->factor_bytes;
+            fe.degree = r->plan->degree;
             if (cudaMalloc(&fe.buf, fe.bytes) != cudaSuccess) {
                 cudaGetLastError();
                 continue;
@@ -341,14 +378,39 @@ void worker_loop(expm_server_s *sv, Worker *w) {
         FactorEntry *fe = nullptr;
         bool build = false;
         Request *r = nullptr;
-        sv->cv.wait(lk, [&] { return sv->stop || (r = admit(sv, *w, &fe, &build)) != nullptr; });
-        if (!r) return;  // stop requested
+        sv->cv.wait(lk, [&] { return sv->stop || w->stop_after || (r = admit(sv, *w, &fe, &build)) != nullptr; });
+        if (!r) break;  // stop requested (server shutdown, or the test hook)
         lk.unlock();
         run_request(sv, *w, *r, *fe, build);
         lk.lock();
         fe->users -= 1;
+        if (fe->users == 0 && (fe->failed || fe->growth.tc_timeout)) {
+            // a failed build (or a tensor-core wait that gave up) must not serve later
+            // requests: drop it so that the next one rebuilds
+            for (auto it = sv->cache.begin(); it != sv->cache.end(); ++it)
+                if (&it->second == fe) {
+                    drop_entry(sv, it);
+                    break;
+                }
+        }
         r->done = true;
         sv->cv.notify_all();
+        if (w->stop_after) break;
+    }
+    w->alive = false;
+}
+
+// Starts the thread of every worker found stopped (server lock held).  A worker stops
+// only between requests, so nothing it had admitted is lost; the queued requests wait
+// for the restarted (or any other) worker.
+void respawn_workers(expm_server_s *sv) {
+    if (sv->stop) return;
+    for (auto &w : sv->workers) {
+        if (w->alive) continue;
+        if (w->th.joinable()) w->th.join();  // it has left worker_loop: returns at once
+        w->stop_after = false;
+        w->alive = true;
+        w->th = std::thread(worker_loop, sv, w.get());
     }
 }
 
@@ -379,7 +441,13 @@ expm_status expm_server_create(size_t hbm_budget_bytes, int max_inflight, expm_s
         delete sv;
         return cuda_error(e, "server_create");
     }
-    for (auto &w : sv->workers) w->th = std::thread(worker_loop, sv, w.get());
+    {
+        std::lock_guard<std::mutex> lk(sv->mu);
+        for (auto &w : sv->workers) {
+            w->alive = true;
+            w->th = std::thread(worker_loop, sv, w.get());
+        }
+    }
     *out = sv;
     return EXPM_OK;
 }
@@ -433,6 +501,11 @@ expm_status expm_server_submit(expm_server sv, uint64_t op_id, const expm_plan p
     if ((opts.flags != 0 && opts.flags != EXPM_FLAG_SKIP_FINAL_RESIDUAL) || !std::isfinite(opts.t) ||
         !std::isfinite(opts.shift_c))
         return set_error(EXPM_EINVAL, "server_submit: bad options");
+    {
+        DeviceGuard guard(sv->device);
+        if (!is_device_ptr(V) || !is_device_ptr(Y))
+            return set_error(EXPM_EINVAL, "server_submit: V and Y must be device memory");
+    }
     auto r = std::make_unique<Request>();
     r->op = op_id;
     r->plan = plan;
@@ -442,6 +515,7 @@ expm_status expm_server_submit(expm_server sv, uint64_t op_id, const expm_plan p
     r->v_cplx = v_is_complex ? 1 : 0;
     r->opts = opts;
     std::lock_guard<std::mutex> lk(sv->mu);
+    respawn_workers(sv);
     auto oi = sv->ops.find(op_id);
     if (oi == sv->ops.end()) return set_error(EXPM_ENOTFOUND, "server_submit: unknown operator id");
     const Op &op = oi->second;
@@ -485,6 +559,7 @@ expm_status expm_server_submit(expm_server sv, uint64_t op_id, const expm_plan p
 expm_status expm_server_poll(expm_server sv, uint64_t ticket, expm_info *info, double ts[4]) {
     if (!sv) return set_error(EXPM_EINVAL, "server_poll: NULL server");
     std::lock_guard<std::mutex> lk(sv->mu);
+    respawn_workers(sv);
     auto it = sv->requests.find(ticket);
     if (it == sv->requests.end()) return EXPM_ENOTFOUND;
     Request &r = *it->second;
@@ -494,6 +569,38 @@ expm_status expm_server_poll(expm_server sv, uint64_t ticket, expm_info *info, d
     const expm_status s = r.status;
     sv->requests.erase(it);
     return s;
+}
+
+expm_status expm_server_set_queue_limit(expm_server sv, int max_queue) {
+    if (!sv) return set_error(EXPM_EINVAL, "server_set_queue_limit: NULL server");
+    if (max_queue < 1 || max_queue > (1 << 20))
+        return set_error(EXPM_EINVAL, "server_set_queue_limit: need 1 <= max_queue <= 2^20");
+    std::lock_guard<std::mutex> lk(sv->mu);
+    sv->max_queue = max_queue;
+    return EXPM_OK;
+}
+
+// Test hooks (not declared in include/expm.h): make the next factor build report a
+// failure; make worker `idx` leave its loop after its current request.
+int expm_internal_server_fail_next_factor(expm_server sv) {
+    if (!sv) return 1;
+    std::lock_guard<std::mutex> lk(sv->mu);
+    sv->fail_next_factor = true;
+    return 0;
+}
+int expm_internal_server_stop_worker(expm_server sv, int idx) {
+    if (!sv || idx < 0 || idx >= (int)sv->workers.size()) return 1;
+    std::lock_guard<std::mutex> lk(sv->mu);
+    sv->workers[idx]->stop_after = true;
+    sv->cv.notify_all();
+    return 0;
+}
+int expm_internal_server_workers_alive(expm_server sv) {
+    if (!sv) return -1;
+    std::lock_guard<std::mutex> lk(sv->mu);
+    int n = 0;
+    for (auto &w : sv->workers) n += w->alive ? 1 : 0;
+    return n;
 }
 
 expm_status expm_server_destroy(expm_server sv) {

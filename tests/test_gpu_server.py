@@ -135,3 +135,133 @@ def test_server_rejections():
     st, _, _ = server.poll(12345)
     assert st == 8                                    # unknown ticket
     server.close()
+
+
+def _tri_case(N, nrhs, offset):
+    w = workloads.laplacian_1d(N=N, nrhs=nrhs, offset=offset)
+    d, e, V = (torch.from_numpy(x).to(DEV) for x in (w["d"], w["e"], w["V"]))
+    return w, d, e, V
+
+
+def _oracle_tri(w, V, degree):
+    Yo, _ = matrix.apply_tridiag(w["d"], w["e"], V.cpu().numpy(), coeffs.theta(degree), coeffs.residues(degree))
+    return Yo
+
+
+def test_plan_recreated_does_not_reuse_the_old_factorization():
+    """A plan destroyed and one of another degree created (possibly at the same address):
+    the cached factorization of the first must not serve the second (the cache is keyed
+    by a plan id that is never reused)."""
+    server = P.Server(hbm_budget_bytes=4 << 30, max_inflight=1)
+    w, d, e, V = _tri_case(30_011, 2, 660)
+    oid = server.register_tridiag(d, e)
+    for prec in (P.EXPM_FP64, P.EXPM_MIXED_FP32):
+        plan12 = P.Plan(degree=12)
+        Y = torch.empty_like(V)
+        st, _, _ = _wait(server, [tk := server.submit(oid, plan12, V, Y, prec=prec)])[tk]
+        assert st == 0
+        assert matrix.rel_err(Y.cpu().numpy(), _oracle_tri(w, V, 12)) <= 1e-8
+        plan12.close()
+        for _ in range(4):   # plans of another degree; allocations may land on the old address
+            plan16 = P.Plan(degree=16)
+            Y = torch.empty_like(V)
+            st, _, _ = _wait(server, [tk := server.submit(oid, plan16, V, Y, prec=prec)])[tk]
+            assert st == 0
+            assert matrix.rel_err(Y.cpu().numpy(), _oracle_tri(w, V, 16)) <= 1e-8
+            plan16.close()
+    server.close()
+
+
+def test_submit_rejects_host_buffers():
+    server = P.Server(hbm_budget_bytes=1 << 30, max_inflight=1)
+    plan = P.Plan(degree=12)
+    w, d, e, V = _tri_case(1000, 1, 661)
+    oid = server.register_tridiag(d, e)
+    hV = V.cpu()
+    for args in ((hV, torch.empty_like(V)), (V, torch.empty_like(hV))):
+        with pytest.raises(P.ExpmError) as ei:
+            server.submit(oid, plan, *args)
+        assert ei.value.status == 1                   # EXPM_EINVAL
+    server.close()
+
+
+def test_full_queue_returns_eagain():
+    """One worker busy with a long request and a queue limit of 1: a submit that finds the
+    queue full returns EXPM_EAGAIN and queues nothing; accepted requests still complete,
+    and the rejected one succeeds when retried."""
+    server = P.Server(hbm_budget_bytes=8 << 30, max_inflight=1)
+    server.set_queue_limit(1)
+    with pytest.raises(P.ExpmError):
+        server.set_queue_limit(0)
+    plan = P.Plan(degree=16)
+    g = workloads.rng(662)
+    A, _, _, _ = workloads.dense_symmetric(1536, -40.0, 0.0, 1, g, True)
+    dA = torch.from_numpy(A).to(DEV)
+    big = server.register_dense(dA)
+    Vb = torch.from_numpy(workloads.request_rhs(1536, 64, 663, True)).to(DEV)
+    w, d, e, V = _tri_case(2000, 1, 664)
+    small = server.register_tridiag(d, e)
+    torch.cuda.synchronize()
+    accepted, rejected = [], 0
+    outs = []
+    for i in range(6):   # the first keeps the worker busy for far longer than these submits take
+        op, VV = (big, Vb) if i == 0 else (small, V)
+        Y = torch.empty_like(VV)
+        try:
+            accepted.append(server.submit(op, plan, VV, Y))
+            outs.append(Y)
+        except P.ExpmError as ex:
+            assert ex.status == 6                     # EXPM_EAGAIN
+            rejected += 1
+    assert rejected >= 1 and len(accepted) <= 3
+    res = _wait(server, accepted)
+    assert all(r[0] == 0 for r in res.values())
+    Y = torch.empty_like(V)
+    st, _, _ = _wait(server, [tk := server.submit(small, plan, V, Y)])[tk]
+    assert st == 0 and matrix.rel_err(Y.cpu().numpy(), _oracle_tri(w, V, 16)) <= 1e-12
+    server.close()
+
+
+def test_failed_factor_build_is_dropped_and_rebuilt():
+    """A factor build reported as failed (host-side fault injection) fails its request
+    with EXPM_ECUDA; the entry is dropped once unused, so the next request on the same
+    operator rebuilds it and succeeds."""
+    server = P.Server(hbm_budget_bytes=4 << 30, max_inflight=2)
+    plan = P.Plan(degree=16)
+    w, d, e, V = _tri_case(20_000, 2, 665)
+    oid = server.register_tridiag(d, e)
+    for prec in (P.EXPM_FP64, P.EXPM_MIXED_FP32):
+        assert P.lib.expm_internal_server_fail_next_factor(server._h) == 0
+        Y = torch.empty_like(V)
+        st, _, _ = _wait(server, [tk := server.submit(oid, plan, V, Y, prec=prec)])[tk]
+        assert st == 7                                # EXPM_ECUDA
+        for _ in range(2):
+            Y = torch.empty_like(V)
+            st, _, _ = _wait(server, [tk := server.submit(oid, plan, V, Y, prec=prec)])[tk]
+            assert st == 0
+            assert matrix.rel_err(Y.cpu().numpy(), _oracle_tri(w, V, 16)) <= 1e-8
+    server.close()
+
+
+def test_stopped_worker_is_restarted_and_queued_requests_complete():
+    """Workers made to leave their loop between requests (host-side fault injection) are
+    restarted by the next submit or poll; every queued request completes correctly."""
+    server = P.Server(hbm_budget_bytes=4 << 30, max_inflight=2)
+    plan = P.Plan(degree=12)
+    w, d, e, V = _tri_case(50_000, 3, 666)
+    oid = server.register_tridiag(d, e)
+    for idx in (0, 1):
+        assert P.lib.expm_internal_server_stop_worker(server._h, idx) == 0
+    t0 = time.time()
+    while P.lib.expm_internal_server_workers_alive(server._h) > 0:
+        assert time.time() - t0 < 30
+        time.sleep(0.01)
+    outs = [torch.empty_like(V) for _ in range(6)]
+    tickets = [server.submit(oid, plan, V, Y) for Y in outs]     # the first submit restarts them
+    assert P.lib.expm_internal_server_workers_alive(server._h) == 2
+    res = _wait(server, tickets)
+    Yo = _oracle_tri(w, V, 12)
+    for tk, Y in zip(tickets, outs):
+        assert res[tk][0] == 0
+        assert matrix.rel_err(Y.cpu().numpy(), Yo) <= 1e-12
+    server.close()
