@@ -33,6 +33,12 @@ import sys
 import tempfile
 import time
 
+# Host-side linear algebra here (input generation, oracle, closed forms) parallelises over
+# independent problems with its own threads; one BLAS thread per caller avoids
+# oversubscribing the cores.  Must be set before numpy loads its BLAS.
+os.environ.setdefault("OPENBLAS_NUM_THREADS", "1")
+os.environ.setdefault("OMP_NUM_THREADS", "1")
+
 import numpy as np
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -52,6 +58,14 @@ SM_MAX_MHZ = 2070.0
 # (x = z - c' x+: product 6, subtraction 2); Re(W x) is then Re(x) and costs nothing (the
 # reduce-scatter addition over the systems, < 1 per element, is not counted)
 FLOPS_K3 = 18
+# FP32 flops per (system, column, row) of the mixed path's dominant kernel (mx_main: pass 0
+# of the binary32 + refinement path), an FMA counting 2: the forward recurrence twice
+# (checkpoint pass and chunk recompute, 10 each), the back substitution with c' = e' g (10),
+# the float-float residual r_1 (8 error-free products with compensated sums, 129), Re(W x_0)
+# as a float pair with its share of the reduce-scatter (24), the last-row spike dot (16), the
+# bottom-up sweep for the first-row end value (10), the two norms (6)
+FLOPS_MX_MAIN = 215
+FP32_FLOP_PER_CLK_SM = 256
 
 
 def _hbm_peak() -> float:
@@ -83,6 +97,10 @@ MIXED_OPTS = dict(tol=1e-10, max_refine=1)
 # TRAFFIC_SRC_SHA (otherwise reported as null)
 TRAFFIC_K3 = 2.8495e9
 TRAFFIC_SRC_SHA = "b5a5c00d7042b497"
+# dram bytes (read + write) per launch of mx_main<8> at N = 2^20 (one ncu capture of the
+# headline command), valid while tridiag_mixed.cu hashes to TRAFFIC_MX_SHA
+TRAFFIC_MX = None
+TRAFFIC_MX_SHA = ""
 
 
 def log(*a):
@@ -97,6 +115,9 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--peaks", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="skip the other configurations' sub-objects (dense small, dense 4096, uneven batch, "
+                         "served stream)")
     ap.add_argument("--rows", type=int, default=N_ROWS,
                     help="rows of the Laplacian (smaller cases are for profiling only)")
     ap.add_argument("--fp64-only", action="store_true",
@@ -202,6 +223,12 @@ def kernel_sha() -> str:
     return hashlib.sha256(src[i:j].encode()).hexdigest()[:16]
 
 
+def mixed_sha() -> str:
+    """Hash of the mixed tridiagonal path's source file."""
+    src = open(os.path.join(ROOT, "paper_2306_16778_gb300", "csrc", "tridiag_mixed.cu")).read()
+    return hashlib.sha256(src.encode()).hexdigest()[:16]
+
+
 def run_peaks():
     import ctypes
     import __graft_entry__
@@ -214,6 +241,12 @@ def run_peaks():
             tf = lib.expm_probe_fma_tflops(kind, iters, bps, 5)
             out[f"{name}_tflops_bps{bps}"] = round(tf, 4)
     print(json.dumps({"probe": "fma_throughput", **out}))
+
+
+# the headline configuration, identical on both arms
+CONFIG = {"workload": "1D Laplacian 100*tridiag(1,-2,1), N=2^20, 8 Gaussian RHS, degree 16, FP64",
+          "N": N_ROWS, "nrhs": NRHS, "degree": DEGREE, "systems": (DEGREE // 2) * NRHS,
+          "l2": "256 MB buffer rewritten between timed steps (outside the step events)"}
 
 
 def cpu_oracle_eval(w, workers):
@@ -332,6 +365,19 @@ def run_ours(args):
     traffic = TRAFFIC_K3 if (TRAFFIC_K3 is not None and TRAFFIC_SRC_SHA == kernel_sha()) else None
     hbm_bytes = 8 * (rows + (rows - 1) + 2 * rows * NRHS)
 
+    # the mixed path's dominant kernel on the FP32 pipe
+    mx_name = "tri_mixed_main"
+    mx_roof = None
+    if mx_name in profmx:
+        mxl, mxms = profmx[mx_name]
+        mx_ach = FLOPS_MX_MAIN * S * NRHS * rows / (mxms / mxl / 1e3) / 1e12
+        mx_peak = SMS * FP32_FLOP_PER_CLK_SM * SM_MAX_MHZ * 1e6 / 1e12
+        mx_traffic = TRAFFIC_MX if (TRAFFIC_MX is not None and TRAFFIC_MX_SHA == mixed_sha()) else None
+        mx_roof = {"kernel": "mx_main<8> (pass 0: binary32 solve, float-float residual, Y update)", "bound": "alu",
+                   "achieved": round(mx_ach, 3), "peak": round(mx_peak, 3), "unit": "TFLOP/s",
+                   "frac": round(mx_ach / mx_peak, 4), "traffic": mx_traffic,
+                   "peak_source": "derived: 152 SMs x 256 FP32 flop/clk x 2070 MHz (probe: 78.4 TFLOP/s)",
+                   "algorithmic": f"{FLOPS_MX_MAIN} FP32 flop per (system, column, row) x {S}x{NRHS}x{rows}"}
     line = {
         "metric": METRIC,
         "value": round(value, 3),
@@ -345,10 +391,7 @@ def run_ours(args):
         "vs_baseline": None,
         "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": "1D Laplacian 100*tridiag(1,-2,1), N=2^20, 8 Gaussian RHS, degree 16, FP64",
-                   "N": N_ROWS, "nrhs": NRHS, "degree": DEGREE, "systems": S * NRHS,
-                   "l2": "256 MB buffer rewritten between timed steps (outside the step events)",
-                   "parallelism": f"replicas{world}"},
+        "config": dict(CONFIG, parallelism=f"replicas{world}"),
         "latency_ms": {"p50": round(pct(ms64, 50), 4), "p99": round(pct(ms64, 99), 4)},
         "mixed": {"prec": "binary32 factors and solves + float-float-residual refinement (EXPM_MIXED_FP32, "
                           f"tol {MIXED_OPTS['tol']:g}, max_refine {MIXED_OPTS['max_refine']})",
@@ -360,6 +403,7 @@ def run_ours(args):
                   "status": infomx.status_worst,
                   "hbm_effective": {"achieved_gbs": round(hbm_bytes * K / totmx / 1e9, 2), "peak_gbs": HBM_GBS,
                                     "frac": round(hbm_bytes * K / totmx / 1e9 / HBM_GBS, 5)},
+                  "roofline": mx_roof,
                   "kernels_ms": {k: round(v[1] / v[0], 4) for k, v in profmx.items()}},
         "mixed_f32x2": {"prec": "float-float (EXPM_MIXED_F32X2)",
                         "value": round(whole_job_value(world, K, totff), 3),
@@ -391,38 +435,63 @@ def run_ours(args):
         line["parity"] = {"fp64_rel_err": matrix.rel_err(Y64, Yo), "mixed_rel_err": matrix.rel_err(Ymx, Yo),
                           "mixed_f32x2_rel_err": matrix.rel_err(Yff, Yo),
                           "tolerance": {"fp64": 1e-12, "mixed": 1e-8}}
+    if world == 1 and not args.no_configs:
+        plan.close()
+        del d, e, V, Y, flush
+        torch.cuda.empty_cache()
+        line["configs"] = bench_configs()
+        print(json.dumps(line), flush=True)
+        return
     print(json.dumps(line), flush=True)
     plan.close()
 
 
+def bench_configs():
+    """The other configurations, each bounded so that the default run stays within minutes:
+    steps and request counts are stated in each sub-object."""
+    out = {}
+    for key, fn in (("dense_small_64", lambda: cfg_dense_small(300)),
+                    ("dense_hermitian_4096", lambda: cfg_dense(4096, 2)),
+                    ("uneven_batch_4096", lambda: cfg_batched(4096, 3)),
+                    ("served_stream", lambda: cfg_served(600, (0.5, 0.9, 1.2), 12, 200))):
+        t0 = time.perf_counter()
+        try:
+            out[key] = fn()
+        except Exception as ex:  # a failing configuration is reported, the headline line still prints
+            out[key] = {"error": f"{type(ex).__name__}: {ex}"}
+        out[key]["wall_s"] = round(time.perf_counter() - t0, 1)
+        log(f"config {key}: {out[key]['wall_s']} s")
+    return out
+
+
 def run_reference(args):
+    """The reference arm: the oracle (the paper's method written plainly: one LAPACK banded
+    solve per pole for all 16 poles, summed in long double) evaluating the full headline
+    workload in every step on the host's cores."""
     rank, world, _ = dist_env()
     if rank != 0:
         return
     import workloads
     from oracle import coeffs, matrix
     workers = min(16, os.cpu_count() or 1)
-    rows = 1 << 17
-    w = workloads.laplacian_1d(N=rows, nrhs=1, offset=1)
+    w = workloads.laplacian_1d(N=N_ROWS, nrhs=NRHS, offset=1)
     th, a = coeffs.theta(DEGREE), coeffs.residues(DEGREE)
-    scale = (N_ROWS / rows) * NRHS            # banded solves are linear in rows and columns
     for _ in range(args.warmup):
         matrix.apply_tridiag(w["d"], w["e"], w["V"], th, a, workers=workers)
     times = []
     for _ in range(args.steps):
         t0 = time.perf_counter()
         matrix.apply_tridiag(w["d"], w["e"], w["V"], th, a, workers=workers)
-        times.append((time.perf_counter() - t0) * scale)
+        times.append(time.perf_counter() - t0)
     tot = sum(times)
     value = args.steps / tot
-    sample = (f"per step: oracle on a 2^17-row slice of the same Laplacian, 1 RHS, all 16 poles on {workers} "
-              f"threads; time scaled x{scale:g} to one full evaluation (2^20 rows, 8 RHS)")
+    sample = (f"every step one full evaluation (N=2^20, 8 RHS, all 16 poles, LAPACK banded LU per pole on "
+              f"{workers} threads)")
     line = {"impl": "reference", "metric": METRIC, "value": round(value, 5), "unit": "evals/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(tot * 1e3 / args.steps, 3),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic",
-            "config": {"workload": "1D Laplacian 100*tridiag(1,-2,1), N=2^20, 8 Gaussian RHS, degree 16, FP64",
-                       "N": N_ROWS, "nrhs": NRHS, "degree": DEGREE},
+            "data": "synthetic", "config": dict(CONFIG, parallelism=f"replicas{world}"),
+            "latency_ms": {"p50": round(1e3 * statistics.median(times), 3), "p99": round(1e3 * max(times), 3)},
             "cpu_baseline": {"value": round(value, 5), "unit": "evals/s", "cores": workers, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": round(value, 5), "unit": "evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -443,78 +512,137 @@ def _time_calls(fn, steps, warmup):
     return ts
 
 
-def run_dense(args):
-    """Dense complex Hermitian n x n, V n x 256, degree 16: binary64 vs mixed path."""
+def _pcts(ts):
+    xs = sorted(ts)
+    return xs[len(xs) // 2], xs[min(len(xs) - 1, int(math.ceil(0.99 * len(xs))) - 1)]
+
+
+def cfg_dense_small(steps=300):
+    """The small plain configuration: real symmetric 64 x 64, spectrum U[-20, 0], one Gaussian
+    vector, degree 12 (12 poles, 6 conjugate pairs).  Latency of one evaluation through
+    expm_apply_dense and through a captured graph (one launch), binary64 and mixed; parity
+    against the oracle and the eigen closed form of R_n(A)v; distance to exp(A)v against
+    Prop. 2.2's bound 2^-n."""
     import torch
     import paper_2306_16778_gb300 as P
     import workloads
-    dev = torch.device("cuda", 0)
-    w = workloads.dense_hermitian(n=args.dense_n, nrhs=256)
+    from oracle import coeffs, matrix, scalar
+    dev = torch.device("cuda", torch.cuda.current_device())
+    n = 12
+    w = workloads.dense_small(offset=0)
+    th, a = coeffs.theta(n), coeffs.residues(n)
+    Yo, _ = matrix.apply_dense(w["A"], w["V"], th, a)
+    Yeig = matrix.eig_apply(w["Q"], w["mu"], w["V"], lambda x: scalar.R_n(x, n))
+    Yexp = matrix.eig_apply(w["Q"], w["mu"], w["V"], np.exp)
+    plan = P.Plan(degree=n)
+    A, V = (torch.from_numpy(x).to(dev) for x in (w["A"], w["V"]))
+    out = {"workload": "dense real symmetric 64x64, spectrum U[-20,0], 1 Gaussian vector, degree 12",
+           "evals_per_path": steps}
+    for name, prec in (("fp64", P.EXPM_FP64), ("mixed", P.EXPM_MIXED_FP32)):
+        Y = torch.empty_like(V)
+        ts = _time_calls(lambda: P.expm_apply_dense(plan, A, V, Y, prec=prec), steps, 20)
+        y = Y.cpu().numpy()
+        Yg = torch.empty_like(V)
+        gr = P.BatchGraph(plan, [A], [V], [Yg], prec=prec, scheme=0)
+        tg = _time_calls(lambda: gr.replay(), steps, 20)
+        yg = Yg.cpu().numpy()
+        gr.close()
+        p50, p99 = _pcts(ts)
+        g50, g99 = _pcts(tg)
+        out[name] = {"us_per_eval": {"p50": round(p50 * 1e6, 2), "p99": round(p99 * 1e6, 2)},
+                     "graph_us_per_eval": {"p50": round(g50 * 1e6, 2), "p99": round(g99 * 1e6, 2)},
+                     "evals_per_s": round(1.0 / min(p50, g50), 1),
+                     "rel_err_vs_oracle": matrix.rel_err(y, Yo), "graph_rel_err_vs_oracle": matrix.rel_err(yg, Yo),
+                     "rel_err_vs_eigen_Rn": matrix.rel_err(y, Yeig), "rel_err_vs_exp": matrix.rel_err(y, Yexp)}
+    out["exp_bound"] = {"sup_err_n": 2.0 ** -n, "note": "|R_n(x) - e^x| <= 2^-n on x <= 0 (Prop. 2.2); "
+                        "relative to |exp(A)v| this allows ~6e-4 here (reading c6)"}
+    out["tolerance"] = {"fp64": 1e-12, "mixed": 1e-8}
+    plan.close()
+    return out
+
+
+def cfg_dense(n=4096, steps=2, reduced=False):
+    """Dense complex Hermitian n x n, V n x 256 complex, degree 16, spectrum U[-50, 0]:
+    binary64 against the mixed modes (binary32 LU, 3xTF32 and bf16x3 tensor-core LU updates,
+    all with the binary64-accurate tensor-core residual), tensor-pipe rooflines, parity
+    against the binary64 path and the eigen closed form."""
+    import torch
+    import paper_2306_16778_gb300 as P
+    import workloads
+    from oracle import matrix, scalar
+    dev = torch.device("cuda", torch.cuda.current_device())
+    w = workloads.dense_hermitian(n=n, nrhs=256)
+    Yeig = matrix.eig_apply(w["Q"], w["mu"], w["V"], lambda x: scalar.R_n(x, 16))
     plan = P.Plan(degree=16)
     A, V = (torch.from_numpy(x).to(dev) for x in (w["A"], w["V"]))
-    out = {"workload": f"dense Hermitian n={args.dense_n}, 256 complex RHS, degree 16, spectrum U[-50,0]"}
+    out = {"workload": f"dense Hermitian n={n}, 256 complex RHS, degree 16, spectrum U[-50,0]",
+           "steps": {"fp64": 1, "mixed": steps}}
     Ys = {}
-    for name, prec in (("fp64", P.EXPM_FP64), ("mixed", P.EXPM_MIXED_FP32), ("mixed_tc", P.EXPM_MIXED_TF32X3),
-                       ("mixed_bf16x3", P.EXPM_MIXED_BF16X3)):
+    modes = (("fp64", P.EXPM_FP64), ("mixed", P.EXPM_MIXED_FP32), ("mixed_tc", P.EXPM_MIXED_TF32X3),
+             ("mixed_bf16x3", P.EXPM_MIXED_BF16X3))
+    for name, prec in modes:
         Y = torch.empty_like(V)
         info = P.expm_apply_dense(plan, A, V, Y, prec=prec)
-        # timed without the per-kernel events, then the same calls again for the breakdown
-        ts = _time_calls(lambda: P.expm_apply_dense(plan, A, V, Y, prec=prec), max(1, args.steps), 0)
+        k = 1 if prec == P.EXPM_FP64 else max(1, steps)
+        ts = _time_calls(lambda: P.expm_apply_dense(plan, A, V, Y, prec=prec), k, 0)
         P.expm_profile_enable(plan, True)
-        _time_calls(lambda: P.expm_apply_dense(plan, A, V, Y, prec=prec), max(1, args.steps), 0)
+        _time_calls(lambda: P.expm_apply_dense(plan, A, V, Y, prec=prec), 1, 0)
         prof = P.expm_profile_read(plan)
         P.expm_profile_enable(plan, False)
         Ys[name] = Y.clone()
-        out[name] = {"s_per_eval": round(statistics.median(ts), 5), "evals_per_s": round(1 / statistics.median(ts), 4),
+        med = statistics.median(ts)
+        out[name] = {"s_per_eval": round(med, 5), "evals_per_s": round(1 / med, 4),
+                     "latency_s": {"p50": round(_pcts(ts)[0], 5), "p99": round(_pcts(ts)[1], 5)},
                      "refine_sweeps": info.refine_iters_max, "resid_rel": info.resid_rel_max,
-                     "growth": info.growth_max_seen,
-                     "kernels_ms_total": {k: round(v[1], 3) for k, v in prof.items()},
-                     "kernel_launches": {k: v[0] for k, v in prof.items()}}
-    # the same through the reduction of A to real tridiagonal form (binary64 reduction and
-    # reflector products; binary64 or binary32 + refinement tridiagonal solves)
-    for name, prec, kw in (("reduced", P.EXPM_FP64, {}),
-                           ("reduced_mixed", P.EXPM_MIXED_FP32, dict(tol=1e-12, max_refine=2))):
-        Y = torch.empty_like(V)
-        P.expm_apply_dense_reduced(plan, A, V, Y, prec=prec, **kw)
-        P.expm_profile_enable(plan, True)
-        ts = _time_calls(lambda: P.expm_apply_dense_reduced(plan, A, V, Y, prec=prec, want_info=False, **kw),
-                         max(1, args.steps), 0)
-        prof = P.expm_profile_read(plan)
-        P.expm_profile_enable(plan, False)
-        Ys[name] = Y.clone()
-        out[name] = {"s_per_eval": round(statistics.median(ts), 5), "evals_per_s": round(1 / statistics.median(ts), 4),
-                     "kernels_ms_total": {k: round(v[1], 3) for k, v in prof.items()}}
-    # tensor-pipe rooflines of the two tensor-core kernels of the bf16x3 step (algorithmic
-    # bf16 flops of the split products / their CUDA-event time; the kernels run inside a
-    # long step, so the sustained peak is the denominator)
-    n, kc, nsys = args.dense_n, 256, 16
+                     "growth": info.growth_max_seen, "rel_err_vs_eigen_Rn": matrix.rel_err(Y.cpu().numpy(), Yeig),
+                     "kernels_ms": {k_: round(v[1], 3) for k_, v in prof.items()},
+                     "kernel_launches": {k_: v[0] for k_, v in prof.items()}}
+    if reduced:
+        for name, prec, kw in (("reduced", P.EXPM_FP64, {}),
+                               ("reduced_mixed", P.EXPM_MIXED_FP32, dict(tol=1e-12, max_refine=2))):
+            Y = torch.empty_like(V)
+            P.expm_apply_dense_reduced(plan, A, V, Y, prec=prec, **kw)
+            ts = _time_calls(lambda: P.expm_apply_dense_reduced(plan, A, V, Y, prec=prec, want_info=False, **kw),
+                             max(1, steps), 0)
+            Ys[name] = Y.clone()
+            out[name] = {"s_per_eval": round(statistics.median(ts), 5),
+                         "rel_err_vs_eigen_Rn": matrix.rel_err(Y.cpu().numpy(), Yeig)}
+    # tensor-pipe rooflines of the bf16x3 step's tensor-core kernels (algorithmic bf16 flops of
+    # the split products / their CUDA-event time; inside a long step: the sustained peak)
+    kc, nsys = 256, 16
     burst, sustained, src = _bf16_peak()
-    prof = out["mixed_bf16x3"]["kernels_ms_total"]
+    prof = out["mixed_bf16x3"]["kernels_ms"]
     launches = out["mixed_bf16x3"]["kernel_launches"]
-    steps = max(1, args.steps)
-    # slice products of the real product (n x 2n) (2n x 2 nsys kc): 28 in the full residual
-    # (seven slices per operand), 10 in the light update after a correction (four per operand)
     for key, kname, pairs in (("oz_gemm", "oz_gemm_kernel<OzFull>", 28), ("oz_gemm_light", "oz_gemm_kernel<OzLight>", 10)):
-        if key not in prof:
-            continue
-        fl = 2.0 * pairs * n * (2 * n) * (2 * nsys * kc) * launches[key]
-        tf = fl / (prof[key] * 1e-3) / 1e12
-        out["roofline_" + key] = {"kernel": kname, "bound": "tensor", "achieved": round(tf, 1), "peak": sustained,
-                                  "unit": "TFLOP/s", "frac": round(tf / sustained, 4),
-                                  "peak_source": f"{src} bf16 sustained", "launches": launches[key],
-                                  "algorithmic": f"{pairs} slice products x 2 x n x 2n x (2 x 16 systems x 256 columns)"}
+        if key in prof:
+            fl = 2.0 * pairs * n * (2 * n) * (2 * nsys * kc) * launches[key]
+            tf = fl / (prof[key] * 1e-3) / 1e12
+            out["roofline_" + key] = {"kernel": kname, "bound": "tensor", "achieved": round(tf, 1), "peak": sustained,
+                                      "unit": "TFLOP/s", "frac": round(tf / sustained, 4),
+                                      "peak_source": f"{src} bf16 sustained", "launches": launches[key],
+                                      "algorithmic": f"{pairs} slice products x 2 x n x 2n x (2 x 16 systems x 256 columns)"}
     if "tc_gemm_bf16x3" in prof:
-        # trailing updates of the 256-column panels: 8 pairs, real (right) x (2 right) x (12 x 256)
-        fl = sum(2.0 * 8 * r * (2 * r) * (12 * 256) for r in range(n - 256, 0, -256)) * steps
+        fl = sum(2.0 * 8 * r * (2 * r) * (12 * 256) for r in range(n - 256, 0, -256))
         tf = fl / (prof["tc_gemm_bf16x3"] * 1e-3) / 1e12
         out["roofline_tc_lu"] = {"kernel": "tc_gemm_kernel<bf16>", "bound": "tensor", "achieved": round(tf, 1),
                                  "peak": sustained, "unit": "TFLOP/s", "frac": round(tf / sustained, 4),
                                  "peak_source": f"{src} bf16 sustained",
                                  "algorithmic": "sum over panels of 8 pairs x 2 x right x 2 right x 12 x 256"}
-    for name in ("mixed", "mixed_tc", "mixed_bf16x3", "reduced", "reduced_mixed"):
+    # algorithmic complex-LU rate of the fastest mixed mode: 8 pair LUs x (8/3) n^3 real flops
+    best = min(("mixed", "mixed_tc", "mixed_bf16x3"), key=lambda m: out[m]["s_per_eval"])
+    out["best_mixed"] = {"mode": best, "speedup_vs_fp64": round(out["fp64"]["s_per_eval"] / out[best]["s_per_eval"], 2),
+                         "lu_algorithmic_tflops": round(8 * (8.0 / 3.0) * n ** 3 / out[best]["s_per_eval"] / 1e12, 2),
+                         "note": "whole-step rate of the 8 pair LUs' algorithmic flops (the LU is one part of the step)"}
+    for name in [m for m, _ in modes[1:]] + (["reduced", "reduced_mixed"] if reduced else []):
         d = (Ys[name] - Ys["fp64"]).abs().pow(2).sum().sqrt() / Ys["fp64"].abs().pow(2).sum().sqrt()
-        out[f"{name}_vs_fp64_rel"] = float(d)
-    print(json.dumps(out), flush=True)
+        out[name]["rel_err_vs_fp64"] = float(d)
+    out["tolerance"] = {"mixed_vs_fp64": 1e-10, "fp64_vs_closed_form": 1e-12}
+    plan.close()
+    return out
+
+
+def run_dense(args):
+    print(json.dumps(cfg_dense(args.dense_n, max(1, args.steps), reduced=True)), flush=True)
 
 
 def run_laplacian2d(args):
@@ -544,135 +672,204 @@ def run_laplacian2d(args):
     print(json.dumps(out), flush=True)
 
 
-def run_batched(args):
-    """Uneven batch: sizes log-uniform in [32, 768], one complex RHS, degree 12."""
+def _thread_map(fn, items, workers=None):
+    from concurrent.futures import ThreadPoolExecutor
+    workers = workers or min(16, os.cpu_count() or 1)
+    with ThreadPoolExecutor(workers) as ex:
+        return list(ex.map(fn, items))
+
+
+def cfg_batched(count=4096, steps=3):
+    """Uneven batch: `count` complex Hermitian instances, n log-uniform in [32, 768], spectra
+    U[-30, 0], one complex RHS each, degree 12 (6 pair LUs per instance).  Binary64 and
+    binary32 + refinement through expm_apply_batched, and the mixed batch captured into one
+    CUDA graph with the autotuned bucket scheme; worst-instance parity against the eigen
+    closed form and against the binary64 path."""
     import torch
     import paper_2306_16778_gb300 as P
     import workloads
-    dev = torch.device("cuda", 0)
-    w = workloads.uneven_batch(count=args.batch_count)
+    from oracle import matrix, scalar
+    dev = torch.device("cuda", torch.cuda.current_device())
+    w = workloads.uneven_batch(count=count, workers=min(16, os.cpu_count() or 1))
+    inst = w["instances"]
+    Yeig = _thread_map(lambda i: matrix.eig_apply(i["Q"], i["mu"], i["V"], lambda x: scalar.R_n(x, 12)), inst)
     plan = P.Plan(degree=12)
-    As = [torch.from_numpy(i["A"]).to(dev) for i in w["instances"]]
-    Vs = [torch.from_numpy(i["V"]).to(dev) for i in w["instances"]]
-    out = {"workload": f"{args.batch_count} complex Hermitian instances, n log-uniform [32,768], 1 RHS, degree 12",
-           "sum_n3": float(np.sum(w["sizes"].astype(float) ** 3))}
+    As = [torch.from_numpy(i["A"]).to(dev) for i in inst]
+    Vs = [torch.from_numpy(i["V"]).to(dev) for i in inst]
+    out = {"workload": f"{count} complex Hermitian instances, n log-uniform [32,768], 1 RHS, degree 12",
+           "sum_n3": float(np.sum(w["sizes"].astype(float) ** 3)), "steps": {"fp64": 1, "mixed": steps}}
+
+    def worst(Ys, ref):
+        return max(matrix.rel_err(y.cpu().numpy(), r) for y, r in zip(Ys, ref))
+
     Ys = {}
     for name, prec in (("fp64", P.EXPM_FP64), ("mixed", P.EXPM_MIXED_FP32)):
         Y = [torch.empty_like(v) for v in Vs]
-        ts = _time_calls(lambda: P.expm_apply_batched(plan, As, Vs, Y, prec=prec), max(1, args.steps), 1)
+        k = 1 if prec == P.EXPM_FP64 else steps
+        ts = _time_calls(lambda: P.expm_apply_batched(plan, As, Vs, Y, prec=prec), k, 1)
         Ys[name] = Y
         med = statistics.median(ts)
-        out[name] = {"s_per_batch": round(med, 4), "instances_per_s": round(args.batch_count / med, 2)}
-        # one more call with per-kernel CUDA events (outside the timed calls)
+        out[name] = {"s_per_batch": round(med, 4), "instances_per_s": round(count / med, 2),
+                     "worst_rel_err_vs_eigen_Rn": worst(Y, Yeig)}
         P.expm_profile_enable(plan, True)
         P.expm_apply_batched(plan, As, Vs, Y, prec=prec)
         prof = P.expm_profile_read(plan)
         P.expm_profile_enable(plan, False)
-        out[name]["kernels_ms"] = {k: round(v[1], 3) for k, v in prof.items()}
-    worst = max(float((a - b).abs().pow(2).sum().sqrt() / b.abs().pow(2).sum().sqrt())
-                for a, b in zip(Ys["mixed"], Ys["fp64"]))
-    out["mixed_vs_fp64_worst_rel"] = worst
-    # the same batch captured into one CUDA graph (bucket scheme autotuned), replayed
+        out[name]["kernels_ms"] = {k_: round(v[1], 3) for k_, v in prof.items()}
+    out["mixed"]["worst_rel_err_vs_fp64"] = max(
+        float((a - b).abs().pow(2).sum().sqrt() / b.abs().pow(2).sum().sqrt()) for a, b in zip(Ys["mixed"], Ys["fp64"]))
     Yg = [torch.empty_like(v) for v in Vs]
     t0 = time.perf_counter()
     gr = P.BatchGraph(plan, As, Vs, Yg, prec=P.EXPM_MIXED_FP32, scheme=-1)
     cap_s = time.perf_counter() - t0
     infos = gr.replay(want_info=True)
-    ts = _time_calls(lambda: gr.replay(), max(1, args.steps), 1)
+    ts = _time_calls(lambda: gr.replay(), steps, 1)
     med = statistics.median(ts)
     gi = gr.info()
-    out["mixed_graph"] = {"s_per_batch": round(med, 4), "instances_per_s": round(args.batch_count / med, 2),
+    out["mixed_graph"] = {"s_per_batch": round(med, 4), "instances_per_s": round(count / med, 2),
+                          "latency_s": {"p50": round(_pcts(ts)[0], 4), "p99": round(_pcts(ts)[1], 4)},
                           "scheme": gi["scheme"], "ms_per_scheme": [round(x, 2) for x in gi["ms_per_scheme"]],
                           "launch_groups": gi["launch_groups"], "capture_and_tune_s": round(cap_s, 2),
                           "refine_sweeps_max": max(i.refine_iters_max for i in infos),
                           "worst_status": max(i.status_worst for i in infos),
-                          "vs_fp64_worst_rel": max(float((a - b).abs().pow(2).sum().sqrt() /
-                                                         b.abs().pow(2).sum().sqrt())
-                                                   for a, b in zip(Yg, Ys["fp64"]))}
+                          "worst_rel_err_vs_eigen_Rn": worst(Yg, Yeig),
+                          "worst_rel_err_vs_fp64": max(float((a - b).abs().pow(2).sum().sqrt() /
+                                                             b.abs().pow(2).sum().sqrt())
+                                                       for a, b in zip(Yg, Ys["fp64"]))}
+    out["speedup_mixed_graph_vs_fp64"] = round(out["fp64"]["s_per_batch"] / med, 2)
+    out["tolerance"] = {"mixed_vs_closed_form": 1e-8, "fp64_vs_closed_form": 1e-12}
     gr.close()
-    print(json.dumps(out), flush=True)
+    plan.close()
+    return out
 
 
-def run_served(args):
-    """Served stream: Poisson arrivals at swept rates; p50/p99 latency and evals/s."""
+def run_batched(args):
+    print(json.dumps(cfg_batched(args.batch_count, max(1, args.steps))), flush=True)
+
+
+def cfg_served(requests=600, fracs=(0.5, 0.9, 1.2), sample=12, all_new=200, max_inflight=8):
+    """Served stream: Poisson arrivals, 70 % tridiagonal Laplacian requests (N log-uniform in
+    [2^12, 2^20], 1-4 RHS), 30 % dense Hermitian (n log-uniform in [64, 2048], 1-64 RHS,
+    spectra U[-40, 0]), degree 12 or 16, operators from a seeded pool of 64 + 64 (resident
+    factorizations reused).  Saturation (everything submitted at once) per precision, then
+    both precisions at the SAME offered rates (fractions of the binary64 saturation), p50/p99
+    of submit -> done and completed requests/s; a sample of each run's requests checked
+    against the closed form (dense) or the oracle (tridiagonal); and a run in which every
+    request names an operator never seen before (no factorization reused)."""
     import torch
     import paper_2306_16778_gb300 as P
     import workloads
-    dev = torch.device("cuda", 0)
+    from oracle import coeffs, matrix, scalar
+    dev = torch.device("cuda", torch.cuda.current_device())
     plans = {12: P.Plan(degree=12), 16: P.Plan(degree=16)}
-    reqs_all = workloads.served_stream(args.served_requests, rate=1.0)
-    out = {"workload": "served stream: 70% Laplacian N log-uniform [2^12,2^20] 1-4 RHS, "
-                       "30% dense Hermitian n log-uniform [64,2048] 1-64 RHS, degree 12/16",
-           "requests_per_rate": args.served_requests}
+    reqs = workloads.served_stream(requests, rate=1.0)
+    keys = sorted({(r["kind"], r["op"]) for r in reqs})
+    opdata = dict(zip(keys, _thread_map(lambda k: workloads.served_operator(*k), keys)))
+    bufs = []
+    for r in reqs:
+        od = opdata[(r["kind"], r["op"])]
+        n = od["d"].shape[0] if r["kind"] == "tridiag" else od["A"].shape[0]
+        bufs.append(torch.from_numpy(workloads.request_rhs(n, r["nrhs"], r["seed"], r["kind"] == "dense")).to(dev))
+    dev_ops = {}
+    for k, od in opdata.items():
+        dev_ops[k] = tuple(torch.from_numpy(x).to(dev) for x in ((od["d"], od["e"]) if k[0] == "tridiag" else (od["A"],)))
+    precs = {"fp64": (P.EXPM_FP64, P.EXPM_FP64), "mixed": (P.EXPM_MIXED_FP32, P.EXPM_MIXED_FP32)}
+
     def sub_opts(kind, ptri, pden):
-        # tridiagonal binary32 + refinement with the headline settings; dense with its defaults
         if kind == "tridiag":
             return dict(prec=ptri, **(MIXED_OPTS if ptri == P.EXPM_MIXED_FP32 else {}))
         return dict(prec=pden)
 
-    for prec_name, ptri, pden in (("fp64", P.EXPM_FP64, P.EXPM_FP64),
-                                  ("mixed", P.EXPM_MIXED_FP32, P.EXPM_MIXED_FP32)):
-        server = P.Server(hbm_budget_bytes=64 << 30, max_inflight=8)
-        ops = {}
-        for r in reqs_all:
-            key = (r["kind"], r["op"])
-            if key not in ops:
-                op = workloads.served_operator(r["kind"], r["op"])
-                if r["kind"] == "tridiag":
-                    d, e = (torch.from_numpy(x).to(dev) for x in (op["d"], op["e"]))
-                    ops[key] = (server.register_tridiag(d, e), d.shape[0])
-                else:
-                    A = torch.from_numpy(op["A"]).to(dev)
-                    ops[key] = (server.register_dense(A), A.shape[0])
-        bufs = []
-        for r in reqs_all:
-            oid, n = ops[(r["kind"], r["op"])]
-            V = torch.from_numpy(workloads.request_rhs(n, r["nrhs"], r["seed"], r["kind"] == "dense")).to(dev)
-            bufs.append((oid, V, torch.empty_like(V)))
-        # saturation: submit everything at once
-        t0 = time.perf_counter()
-        tk = [server.submit(oid, plans[r["degree"]], V, Y, **sub_opts(r["kind"], ptri, pden))
-              for r, (oid, V, Y) in zip(reqs_all, bufs)]
-        lat = []
-        pending = set(tk)
-        while pending:
+    def make_server(fresh):
+        server = P.Server(hbm_budget_bytes=64 << 30, max_inflight=max_inflight)
+        ids = {}
+        for i, r in enumerate(reqs):
+            k = (r["kind"], r["op"])
+            key = (k, i) if fresh else k
+            if key not in ids:
+                t = dev_ops[k]
+                ids[key] = server.register_tridiag(*t) if k[0] == "tridiag" else server.register_dense(t[0])
+        return server, [ids[((r["kind"], r["op"]), i) if fresh else (r["kind"], r["op"])] for i, r in enumerate(reqs)]
+
+    def run(server, oids, ptri, pden, rate, n_req):
+        outs = [torch.empty_like(V) for V in bufs[:n_req]]
+        torch.cuda.synchronize()
+        gaps = workloads.rng(77).exponential(1.0 / rate, n_req) if rate else np.zeros(n_req)
+        t_start = time.perf_counter()
+        arrival = t_start + np.cumsum(gaps)
+        lat, pending, i = [], {}, 0
+        while i < n_req or pending:
+            now = time.perf_counter()
+            while i < n_req and arrival[i] <= now:
+                r = reqs[i]
+                t = server.submit(oids[i], plans[r["degree"]], bufs[i], outs[i], **sub_opts(r["kind"], ptri, pden))
+                pending[t] = i
+                i += 1
             for t in list(pending):
                 res = server.poll(t)
                 if res is not None:
-                    pending.discard(t)
+                    assert res[0] == 0, ("request failed", res[0])
+                    del pending[t]
                     lat.append(res[2][3] - res[2][0])
-        sat = len(tk) / (time.perf_counter() - t0)
-        rates = {}
-        for frac in (0.5, 0.9):
-            rate = frac * sat
-            gaps = workloads.rng(77).exponential(1.0 / rate, len(bufs))
-            t_start = time.perf_counter()
-            arrival = t_start + np.cumsum(gaps)
-            tk = []
-            lat = []
-            pending = {}
-            i = 0
-            while i < len(bufs) or pending:
-                now = time.perf_counter()
-                while i < len(bufs) and arrival[i] <= now:
-                    r = reqs_all[i]
-                    oid, V, Y = bufs[i]
-                    t = server.submit(oid, plans[r["degree"]], V, Y, **sub_opts(r["kind"], ptri, pden))
-                    pending[t] = True
-                    i += 1
-                for t in list(pending):
-                    res = server.poll(t)
-                    if res is not None:
-                        del pending[t]
-                        lat.append(res[2][3] - res[2][0])
-            wall = time.perf_counter() - t_start
-            lat.sort()
-            rates[f"{frac:.1f}xsat"] = {"offered_rps": round(rate, 2), "evals_per_s": round(len(lat) / wall, 2),
-                                       "p50_ms": round(1e3 * lat[len(lat) // 2], 3),
-                                       "p99_ms": round(1e3 * lat[min(len(lat) - 1, int(0.99 * len(lat)))], 3)}
-        out[prec_name] = {"saturation_evals_per_s": round(sat, 2), "rates": rates}
+        wall = time.perf_counter() - t_start
+        lat.sort()
+        return {"offered_rps": round(rate, 2) if rate else None, "requests": n_req,
+                "evals_per_s": round(n_req / wall, 2), "p50_ms": round(1e3 * lat[len(lat) // 2], 3),
+                "p99_ms": round(1e3 * lat[min(len(lat) - 1, int(0.99 * len(lat)))], 3)}, outs
+
+    def check(outs, n_req):
+        idx = list(range(0, n_req, max(1, n_req // sample)))[:sample]
+
+        def one(i):
+            r = reqs[i]
+            od = opdata[(r["kind"], r["op"])]
+            V = bufs[i].cpu().numpy()
+            if r["kind"] == "dense":
+                ref = matrix.eig_apply(od["Q"], od["mu"], V, lambda x: scalar.R_n(x, r["degree"]))
+            else:
+                ref, _ = matrix.apply_tridiag(od["d"], od["e"], V, coeffs.theta(r["degree"]),
+                                              coeffs.residues(r["degree"]))
+            return matrix.rel_err(outs[i].cpu().numpy(), ref)
+        errs = _thread_map(one, idx)
+        return {"checked": len(idx), "worst_rel_err": max(errs)}
+
+    out = {"workload": "served stream: 70% Laplacian N log-uniform [2^12,2^20] 1-4 RHS, 30% dense Hermitian "
+                       "n log-uniform [64,2048] 1-64 RHS, degree 12/16, operator pool 64+64",
+           "requests_per_run": requests, "max_inflight": max_inflight,
+           "budget": f"{requests} requests per rate (rates {list(fracs)} x the binary64 saturation), "
+                     f"{sample} requests per run checked, {all_new} requests in the all-new-operator runs"}
+    sat = {}
+    for name, (ptri, pden) in precs.items():
+        server, oids = make_server(False)
+        run(server, oids, ptri, pden, 0, min(requests, 200))  # warm: factorizations built and cached
+        res, outs = run(server, oids, ptri, pden, 0, requests)
+        sat[name] = res["evals_per_s"]
+        out[name] = {"saturation": dict(res, accuracy=check(outs, requests)), "rates": {}}
         server.close()
-    print(json.dumps(out), flush=True)
+    for f in fracs:
+        rate = f * sat["fp64"]
+        for name, (ptri, pden) in precs.items():
+            server, oids = make_server(False)
+            run(server, oids, ptri, pden, 0, min(requests, 200))
+            res, outs = run(server, oids, ptri, pden, rate, requests)
+            out[name]["rates"][f"{f:g}x_fp64_sat"] = dict(res, accuracy=check(outs, requests))
+            server.close()
+    out["all_new_operators"] = {}
+    n_new = min(all_new, requests)
+    for name, (ptri, pden) in precs.items():
+        server, oids = make_server(True)
+        res, outs = run(server, oids, ptri, pden, 0.5 * sat["fp64"], n_new)
+        out["all_new_operators"][name] = dict(res, accuracy=check(outs, n_new))
+        server.close()
+    out["tolerance"] = {"fp64": 1e-12, "mixed": 1e-8}
+    for p_ in plans.values():
+        p_.close()
+    return out
+
+
+def run_served(args):
+    print(json.dumps(cfg_served(args.served_requests, fracs=(0.25, 0.5, 0.75, 0.9, 1.0, 1.2), sample=24,
+                                all_new=min(1000, args.served_requests))), flush=True)
 
 
 def main():

@@ -94,15 +94,29 @@ def batch_sizes(count: int, g, lo: int = 32, hi: int = 768) -> np.ndarray:
     return np.rint(np.exp(g.uniform(math.log(lo), math.log(hi), count))).astype(np.int64)
 
 
+def _batch_instance(args):
+    n, seed, mu_lo = args
+    g = np.random.Generator(np.random.PCG64(seed))
+    A, Q, mu, V = dense_symmetric(int(n), mu_lo, 0.0, 1, g, complex_=True)
+    return dict(A=A, Q=Q, mu=mu, V=V)
+
+
 def uneven_batch(count: int = 4096, offset: int = 3, lo: int = 32, hi: int = 768,
-                 mu_lo: float = -30.0):
-    """``count`` complex Hermitian instances, sizes log-uniform in [lo, hi], one RHS each."""
+                 mu_lo: float = -30.0, workers: int = 1):
+    """``count`` complex Hermitian instances, sizes log-uniform in [lo, hi], one RHS each.
+
+    Instance i draws from its own generator (seed BASE_SEED + 1_000_000 * offset + i), so
+    the batch is the same whether it is made sequentially or by ``workers`` threads (the
+    QR factorizations and products release the interpreter lock)."""
     g = rng(offset)
     sizes = batch_sizes(count, g, lo, hi)
-    inst = []
-    for n in sizes:
-        A, Q, mu, V = dense_symmetric(int(n), mu_lo, 0.0, 1, g, complex_=True)
-        inst.append(dict(A=A, Q=Q, mu=mu, V=V))
+    args = [(int(n), BASE_SEED + 1_000_000 * offset + i, mu_lo) for i, n in enumerate(sizes)]
+    if workers > 1 and count > 64:
+        from concurrent.futures import ThreadPoolExecutor
+        with ThreadPoolExecutor(workers) as ex:
+            inst = list(ex.map(_batch_instance, args))
+    else:
+        inst = [_batch_instance(x) for x in args]
     return dict(sizes=sizes, instances=inst, degree=12)
 
 
