@@ -398,7 +398,9 @@ expm_status expm_apply_dense(expm_plan p, int n, const void *A, int lda, int a_i
         if (!dy) dY = base + nA + nV;
         if (err != cudaSuccess) return cuda_error(err, "apply_dense: staging copy");
     }
-    expm_status s = plan_reserve(p, &p->work, &p->work_bytes, dense_workspace_bytes(g));
+    const bool small = dense_small_fits(g);  // one cluster launch (dense_small.cu)
+    expm_status s = plan_reserve(p, &p->work, &p->work_bytes,
+                                 small ? dense_small_workspace_bytes() : dense_workspace_bytes(g));
     if (s != EXPM_OK) return s;
     DenseResult res{};
     DenseIO io{};
@@ -413,7 +415,8 @@ expm_status expm_apply_dense(expm_plan p, int n, const void *A, int lda, int a_i
     io.ldy = split_v ? 2 * (int64_t)ldy : ldy;
     io.ystride = 0;
     io.y_real = complex_a ? 0 : 1;
-    cudaError_t err = dense_run(g, io, sys, p->work, st, p->prof, &res);
+    cudaError_t err = small ? dense_small_run(g, io, sys, p->work, st, p->prof, &res)
+                            : dense_run(g, io, sys, p->work, st, p->prof, &res);
     if (err != cudaSuccess) return cuda_error(err, "apply_dense: kernels");
     if (staged && !dy) {
         err = cudaMemcpyAsync(Y, dY, sizeof(double) * nY, cudaMemcpyDeviceToHost, st);
