@@ -16,6 +16,38 @@
 #define EXPM_HD __host__ __device__ __forceinline__
 #define EXPM_D __device__ __forceinline__
 
+// ------------------------------------------------------------------ packed binary32 pairs
+// Two binary32 numbers in one 64-bit register (low half first) and the two-lane
+// instructions of sm_100 and later, add/sub/mul/fma.rn.f32x2: one instruction performs
+// the same operation on both halves, each rounded as the scalar *_rn operation would be.
+EXPM_D uint64_t pk2(float lo, float hi) {
+    uint64_t r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+EXPM_D void upk2(uint64_t v, float &lo, float &hi) { asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v)); }
+EXPM_D uint64_t padd2(uint64_t a, uint64_t b) {
+    uint64_t d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+EXPM_D uint64_t psub2(uint64_t a, uint64_t b) {
+    uint64_t d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+EXPM_D uint64_t pmul2(uint64_t a, uint64_t b) {
+    uint64_t d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+EXPM_D uint64_t ffma2(uint64_t a, uint64_t b, uint64_t c) {  // a * b + c
+    uint64_t d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+EXPM_D uint64_t pneg2(uint64_t a) { return a ^ 0x8000000080000000ull; }  // both signs flipped
+
 // ------------------------------------------------------------------ f32x2 type
 struct f32x2 {
     float hi, lo;
@@ -75,29 +107,45 @@ EXPM_D f32x2 to_f32x2(double x) {
 }
 EXPM_D double to_double(f32x2 x) { return (double)x.hi + (double)x.lo; }
 
-// binary64 -> float pair with integer operations only (no FP64-pipe work): hi takes
-// the leading 24 significand bits, lo the remaining 29 bits rounded to 24; the pair
-// is then renormalised.  Values outside [2^-74, 2^128) take the binary64 route.
+// An unsigned integer m < 2^29 to binary32, rounded to nearest, on the FP32 pipe: the
+// high 6 and low 23 bits become exact floats by the 2^23 bias trick (the integer in the
+// significand of 2^23, then 2^23 subtracted), and one FMA rounds mh 2^23 + ml once.
+// (An integer-to-float conversion instruction runs on this part's FP64 unit.)
+EXPM_D float u29_to_float_rn(unsigned m) {
+    const float two23 = 8388608.0f;
+    const float fh = __fsub_rn(__uint_as_float(0x4b000000u | (m >> 23)), two23);
+    const float fl = __fsub_rn(__uint_as_float(0x4b000000u | (m & 0x7fffffu)), two23);
+    return __fmaf_rn(fh, two23, fl);
+}
+
+// the rare range of split_bits, kept out of line so that the compiler cannot turn the
+// branch into a select that runs these FP64 conversions for every value
+static __device__ __noinline__ f32x2 split_slow(double x) { return to_f32x2(x); }
+
+// binary64 -> float pair with integer and binary32 operations only (no FP64-pipe work):
+// hi takes the leading 24 significand bits, lo the remaining 29 bits rounded to 24; the
+// pair is then renormalised.  Values outside [2^-74, 2^128) take the binary64 route.
 EXPM_D f32x2 split_bits(double x) {
     const unsigned long long u = (unsigned long long)__double_as_longlong(x);
     const int ex = (int)((u >> 52) & 0x7ff);
-    if (ex < 1023 + 52 - 126 || ex > 1023 + 127) return to_f32x2(x);
+    if (__builtin_expect(ex < 1023 + 52 - 126 || ex > 1023 + 127, 0)) return split_slow(x);
     const unsigned sign = (unsigned)(u >> 63) << 31;
     const float hi = __uint_as_float(sign | ((unsigned)(ex - 1023 + 127) << 23) | (unsigned)((u >> 29) & 0x7fffffu));
     const float scalef = __uint_as_float((unsigned)(ex - 1023 - 52 + 127) << 23);
-    float lo = __fmul_rn(__uint2float_rn((unsigned)(u & 0x1fffffffu)), scalef);
+    float lo = __fmul_rn(u29_to_float_rn((unsigned)(u & 0x1fffffffu)), scalef);
     if (sign) lo = -lo;
     return fast_two_sum(hi, lo);
 }
 
-// float -> binary64 by bit widening (normal floats; zero and the rest fall back)
+// float -> binary64 by bit widening
+// (subnormal, infinite and NaN inputs out of line, as for split_bits; zero stays inline)
+static __device__ __noinline__ double widen_slow(float f) { return (double)f; }
 EXPM_D double widen_bits(float f) {
     const unsigned u = __float_as_uint(f);
-    const unsigned ex = (u >> 23) & 0xff;
-    if (ex == 0 || ex == 0xff) return (double)f;
-    const unsigned long long b = ((unsigned long long)(u >> 31) << 63) |
-                                 ((unsigned long long)(ex - 127 + 1023) << 52) |
-                                 ((unsigned long long)(u & 0x7fffffu) << 29);
+    const unsigned ex = (u >> 23) & 0xff, man = u & 0x7fffffu;
+    if (__builtin_expect(ex == 0xff || (ex == 0 && man != 0), 0)) return widen_slow(f);
+    const unsigned long long e64 = ex == 0 ? 0ull : (unsigned long long)(ex - 127 + 1023);  // +-0 stays +-0
+    const unsigned long long b = ((unsigned long long)(u >> 31) << 63) | (e64 << 52) | ((unsigned long long)man << 29);
     return __longlong_as_double((long long)b);
 }
 
@@ -127,9 +175,9 @@ template <> struct RealOps<float> {
     static EXPM_D float zero() { return 0.f; }
     static EXPM_D float rcp(float x) { return __frcp_rn(x); }
 };
-template <> struct RealOps<f32x2> {
-    static EXPM_D f32x2 from(double x) { return to_f32x2(x); }
-    static EXPM_D double todbl(f32x2 x) { return to_double(x); }
+template <> struct RealOps<f32x2> {  // conversions by integer operations (FP64 unit only to add)
+    static EXPM_D f32x2 from(double x) { return split_bits(x); }
+    static EXPM_D double todbl(f32x2 x) { return widen_bits(x.hi) + widen_bits(x.lo); }
     static EXPM_D f32x2 zero() { return {0.f, 0.f}; }
     static EXPM_D f32x2 rcp(f32x2 x) { return recip(x); }
 };

@@ -73,22 +73,11 @@ template <class W> EXPM_D cx<W> cinvW(cx<W> w) {
 }
 template <class W> EXPM_D W cabs2(cx<W> a) { return a.re * a.re + a.im * a.im; }
 
-// Packed binary32 pairs (low = re, high = im) in one 64-bit register, and the two-lane FMA
-// fma.rn.f32x2 (sm_100 and later): d = a * b + c in each half, rounded to nearest.
-EXPM_D uint64_t pk2(float lo, float hi) {
-    uint64_t r;
-    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
-    return r;
-}
-EXPM_D cx<float> upk2(uint64_t v) {
+// Packed (re, im) pairs of the mixed kernel's registers (pk2 / ffma2 of arith.cuh)
+EXPM_D cx<float> upk2c(uint64_t v) {
     cx<float> r;
-    asm("mov.b64 {%0, %1}, %2;" : "=f"(r.re), "=f"(r.im) : "l"(v));
+    upk2(v, r.re, r.im);
     return r;
-}
-EXPM_D uint64_t ffma2(uint64_t a, uint64_t b, uint64_t c) {
-    uint64_t d;
-    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
-    return d;
 }
 
 // A_ij of the input (real symmetric or complex Hermitian)
@@ -390,13 +379,13 @@ __global__ void __launch_bounds__(DS_THREADS, 1) dense_small_mixed_kernel(DsArgs
             }
         }
         __syncthreads();
-        const cx<float> piv = upk2(rowbuf[b][j]);
+        const cx<float> piv = upk2c(rowbuf[b][j]);
         const float q = __frcp_rn(piv.re * piv.re + piv.im * piv.im);
         const cx<float> inv = {piv.re * q, -piv.im * q};
         uint64_t ua[2], ub[2];
 #pragma unroll
         for (int c = 0; c < 2; ++c) {
-            const cx<float> u = upk2(rowbuf[b][tx + 32 * c]);
+            const cx<float> u = upk2c(rowbuf[b][tx + 32 * c]);
             if (tx + 32 * c >= j) umax_f = fmaxf(umax_f, cabs2(u));
             const cx<float> uh = (tx + 32 * c == j) ? inv : cmulW(u, inv);
             ua[c] = pk2(-uh.re, -uh.im);
@@ -404,7 +393,7 @@ __global__ void __launch_bounds__(DS_THREADS, 1) dense_small_mixed_kernel(DsArgs
         }
 #pragma unroll
         for (int r = 0; r < DS_N / 8; ++r) {
-            const cx<float> l = upk2(colbuf[b][ty + 8 * r]);
+            const cx<float> l = upk2c(colbuf[b][ty + 8 * r]);
             const uint64_t lr = pk2(l.re, l.re), li = pk2(l.im, l.im);
 #pragma unroll
             for (int c = 0; c < 2; ++c) mp[r][c] = ffma2(li, ub[c], ffma2(lr, ua[c], mp[r][c]));
@@ -415,7 +404,7 @@ __global__ void __launch_bounds__(DS_THREADS, 1) dense_small_mixed_kernel(DsArgs
                 if (r == rj) {
 #pragma unroll
                     for (int c = 0; c < 2; ++c) {
-                        const cx<float> na = upk2(ua[c]);
+                        const cx<float> na = upk2c(ua[c]);
                         mp[r][c] = pk2(-na.re, -na.im);
                     }
                 }
@@ -425,7 +414,7 @@ __global__ void __launch_bounds__(DS_THREADS, 1) dense_small_mixed_kernel(DsArgs
 #pragma unroll
     for (int r = 0; r < DS_N / 8; ++r)
 #pragma unroll
-        for (int c = 0; c < 2; ++c) MT[(tx + 32 * c) * DS_LD + ty + 8 * r] = upk2(mp[r][c]);
+        for (int c = 0; c < 2; ++c) MT[(tx + 32 * c) * DS_LD + ty + 8 * r] = upk2c(mp[r][c]);
     double umax = (double)umax_f, unused = 0.0;
     block_max_sum(umax, unused, red);
     umax = sqrt(umax);

@@ -139,8 +139,11 @@ __device__ __forceinline__ void oz_digits(double x, int ebias, uint16_t out[OZ_S
     d[0] = (int)V;
 #pragma unroll
     for (int p = 0; p < OZ_S; ++p) {
-        // d_p 2^(-8p): exact in binary32 and in bf16 (the low 16 bits of the float are zero)
-        const float f = __int2float_rn(d[p]) * __int_as_float((127 - 8 * p) << 23);
+        // d_p 2^(-8p): exact in binary32 and in bf16 (the low 16 bits of the float are zero).
+        // |d_p| <= 2^8, so d_p becomes a float exactly by the 1.5 2^23 bias trick on the FP32
+        // pipe (an integer-to-float conversion instruction would run on the FP64 unit)
+        const float dp = __fsub_rn(__int_as_float(0x4b400000 + d[p]), 12582912.0f);
+        const float f = dp * __int_as_float((127 - 8 * p) << 23);
         out[p] = (uint16_t)(__float_as_uint(f) >> 16);
     }
 }

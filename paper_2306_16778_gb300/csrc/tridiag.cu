@@ -294,11 +294,11 @@ static cudaError_t tri_solve_t(const TriGeom &g, const double *V, double *Y, con
     });
     if (err != cudaSuccess) return err;
     if (g.P > 1) {
-        const size_t smem = (size_t)4 * (g.P - 1) * sizeof(cx<R>);
+        const size_t smem = 4 * cr_len<R>(g.P - 1) * sizeof(cx<R>);
         // the attribute is a ceiling: set it to the largest reduced system (TRI_PMAX) so
         // that concurrent callers (server workers) never lower it under another's launch
         err = cudaFuncSetAttribute(tri_reduced_cr<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   (int)(4 * (size_t)(TRI_PMAX - 1) * sizeof(cx<R>)));
+                                   (int)(4 * cr_len<R>(TRI_PMAX - 1) * sizeof(cx<R>)));
         if (err != cudaSuccess) return err;
         err = prof.timed(ff ? "tri_reduced_cr<f32x2>" : "tri_reduced_cr<f64>", st, [&] {
             tri_reduced_cr<R><<<g.S * g.Rc, 512, smem, st>>>(g, dP, eP, Vuse, nullptr, ps, spk, yend, sig, nullptr);

@@ -170,6 +170,53 @@ __global__ void __launch_bounds__(128) tri_block_dots(TriGeom g, const R *__rest
 // Reduced system for the separators of one (system, column):
 //   A_b sigma_{b-1} + B_b sigma_b + C_b sigma_{b+1} = D_b,   b = 0 .. P-2
 // solved by cyclic reduction (odd-even elimination) in shared memory.
+// Shared-memory layout of the reduced system's arrays: entry i at cr_ix(i), one padding
+// entry after every 128 bytes, so that the strided accesses of the deeper reduction
+// levels (i = 2^k t + const) spread over the banks; cr_len(n) entries per array.
+template <class R> __host__ __device__ constexpr int cr_shift() { return sizeof(cx<R>) == 8 ? 4 : 3; }
+template <class R> EXPM_D int cr_ix(int i) { return i + (i >> cr_shift<R>()); }
+template <class R> __host__ __device__ inline size_t cr_len(int64_t n) { return (size_t)(n + (n >> cr_shift<R>()) + 1); }
+
+// Cyclic reduction of the tridiagonal system  A_i x_{i-1} + Bc_i x_i + C_i x_{i+1} = D_i
+// (i < n) held in shared memory (entry i at cr_ix(i)); every thread of the CTA takes part
+// and the solution overwrites D.  Forward: odd levels eliminated into their neighbours
+// level by level; back: substitution from the top level down.
+template <class R>
+EXPM_D void cr_solve_smem(cx<R> *A, cx<R> *Bc, cx<R> *C, cx<R> *D, int n) {
+    for (int stride = 1; 2 * stride - 1 < n; stride *= 2) {
+        for (int i = 2 * stride - 1 + 2 * stride * threadIdx.x; i < n; i += 2 * stride * blockDim.x) {
+            const int lo = i - stride, hi = i + stride;
+            const cx<R> k1 = A[cr_ix<R>(i)] * cinv(Bc[cr_ix<R>(lo)]);
+            cx<R> nb = Bc[cr_ix<R>(i)] - k1 * C[cr_ix<R>(lo)];
+            cx<R> nd = D[cr_ix<R>(i)] - k1 * D[cr_ix<R>(lo)];
+            cx<R> na = -(k1 * A[cr_ix<R>(lo)]);
+            cx<R> nc = cxz<R>();
+            if (hi < n) {
+                const cx<R> k2 = C[cr_ix<R>(i)] * cinv(Bc[cr_ix<R>(hi)]);
+                nb = nb - k2 * A[cr_ix<R>(hi)];
+                nd = nd - k2 * D[cr_ix<R>(hi)];
+                nc = -(k2 * C[cr_ix<R>(hi)]);
+            }
+            A[cr_ix<R>(i)] = na;
+            Bc[cr_ix<R>(i)] = nb;
+            C[cr_ix<R>(i)] = nc;
+            D[cr_ix<R>(i)] = nd;
+        }
+        __syncthreads();
+    }
+    int top = 1;
+    while (top * 2 <= n) top *= 2;
+    for (int st = top; st >= 1; st /= 2) {
+        for (int i = st - 1 + 2 * st * threadIdx.x; i < n; i += 2 * st * blockDim.x) {
+            cx<R> rhs = D[cr_ix<R>(i)];
+            if (i - st >= 0) rhs = rhs - A[cr_ix<R>(i)] * D[cr_ix<R>(i - st)];
+            if (i + st < n) rhs = rhs - C[cr_ix<R>(i)] * D[cr_ix<R>(i + st)];
+            D[cr_ix<R>(i)] = rhs * cinv(Bc[cr_ix<R>(i)]);  // D now holds the solution at index i
+        }
+        __syncthreads();
+    }
+}
+
 template <class R>
 __global__ void __launch_bounds__(1024) tri_reduced_cr(TriGeom g, const R *__restrict__ dP,
                                                        const R *__restrict__ eP, const R *__restrict__ VP,
@@ -180,10 +227,11 @@ __global__ void __launch_bounds__(1024) tri_reduced_cr(TriGeom g, const R *__res
     if (skip != nullptr && *skip) return;  // refinement already converged (uniform over the launch)
     extern __shared__ unsigned char smem_raw[];
     const int n = g.P - 1;
+    const int np = (int)cr_len<R>(n);
     cx<R> *A = reinterpret_cast<cx<R> *>(smem_raw);
-    cx<R> *Bc = A + n;
-    cx<R> *C = Bc + n;
-    cx<R> *D = C + n;
+    cx<R> *Bc = A + np;
+    cx<R> *C = Bc + np;
+    cx<R> *D = C + np;
     const int s = blockIdx.x / g.Rc;
     const int j = blockIdx.x % g.Rc;
     const cx<R> theta = cx_from<R>(ps.th_re[s], ps.th_im[s]);
@@ -208,46 +256,15 @@ __global__ void __launch_bounds__(1024) tri_reduced_cr(TriGeom g, const R *__res
         cx<R> Db = sepRhs != nullptr ? sepRhs[((int64_t)s * g.P + b) * g.Rc + j]
                                      : cx<R>{VP[r * g.Rc + j], RealOps<R>::zero()};
         Db = Db - scale(el, yL) - scale(er, y0n);
-        A[b] = Ab;
-        Bc[b] = Bb;
-        C[b] = Cb;
-        D[b] = Db;
+        A[cr_ix<R>(b)] = Ab;
+        Bc[cr_ix<R>(b)] = Bb;
+        C[cr_ix<R>(b)] = Cb;
+        D[cr_ix<R>(b)] = Db;
     }
     __syncthreads();
-    for (int stride = 1; 2 * stride - 1 < n; stride *= 2) {
-        for (int i = 2 * stride - 1 + 2 * stride * threadIdx.x; i < n; i += 2 * stride * blockDim.x) {
-            const int lo = i - stride, hi = i + stride;
-            const cx<R> k1 = A[i] * cinv(Bc[lo]);
-            cx<R> nb = Bc[i] - k1 * C[lo];
-            cx<R> nd = D[i] - k1 * D[lo];
-            cx<R> na = -(k1 * A[lo]);
-            cx<R> nc = cxz<R>();
-            if (hi < n) {
-                const cx<R> k2 = C[i] * cinv(Bc[hi]);
-                nb = nb - k2 * A[hi];
-                nd = nd - k2 * D[hi];
-                nc = -(k2 * C[hi]);
-            }
-            A[i] = na;
-            Bc[i] = nb;
-            C[i] = nc;
-            D[i] = nd;
-        }
-        __syncthreads();
-    }
-    int top = 1;
-    while (top * 2 <= n) top *= 2;
-    for (int st = top; st >= 1; st /= 2) {
-        for (int i = st - 1 + 2 * st * threadIdx.x; i < n; i += 2 * st * blockDim.x) {
-            cx<R> rhs = D[i];
-            if (i - st >= 0) rhs = rhs - A[i] * D[i - st];
-            if (i + st < n) rhs = rhs - C[i] * D[i + st];
-            D[i] = rhs * cinv(Bc[i]);  // D now holds the solution at index i
-        }
-        __syncthreads();
-    }
+    cr_solve_smem<R>(A, Bc, C, D, n);
     cx<R> *SG = sigma + (int64_t)s * g.P * g.Rc;
-    for (int b = threadIdx.x; b < n; b += blockDim.x) SG[(int64_t)b * g.Rc + j] = D[b];
+    for (int b = threadIdx.x; b < n; b += blockDim.x) SG[(int64_t)b * g.Rc + j] = D[cr_ix<R>(b)];
 }
 
 // ------------------------------------------------------------------ K4: float pairs of Y to binary64

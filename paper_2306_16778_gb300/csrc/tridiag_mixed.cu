@@ -32,7 +32,8 @@
 //                         corner entries of M~_b^{-1} (factor part: T, t, c, poles only)
 //   mx_ends               pass 0 end values of M~_b^{-1} v_b: a top-down sweep gives
 //                         the last row, a bottom-up (UL) sweep the first
-//   tri_reduced_cr<float> reduced separator system of a pass
+//   mx_cr_coef            the reduced separator system's coefficients (factor part)
+//   mx_cr                 reduced separator system of a pass (cyclic reduction)
 //   mx_main               pass 0, one thread per (block, column, system): the block
 //                         solve for x_0, then, walking the rows bottom-up, the
 //                         float-float residual r_1 (stored), Re(W x_0) summed over the
@@ -82,14 +83,16 @@ struct MxArgs {
     const float *VPf, *VPl;              // V as float pairs
     const cx<float> *pg, *pu;            // pivots g (top-down) and g^ (bottom-up), [row][LG]
     const cx<float> *spk;                // corner entries of M~_b^{-1}, [system][block][4]
-    cx<float> *yend;                     // block end values of the pass's right-hand side, [system][block][column][2]
+    const struct MxCrc *crc;             // reduced-system coefficients, [system][separator]
+    cx<float> *yend;                     // block end values of the pass's right-hand side, [system][column][block][2]
     cx<float> *sig;                      // separator values of the pass, [system][block][column]
     cx<float> *xb;                       // first / last row of the pass's block solutions, [system][block][column][2]
     cx<float> *sepR, *sepLo;             // separator residuals, [system][block][column]
     cx<float> *R, *Rlo;                  // interior residuals, [row][column][lane]
     float2 *ckpt;                        // forward checkpoints z, [chunk][thread]
     double *Y;                           // float pairs during the passes, binary64 at the end
-    double *part3, *partS;               // per-CTA partial norms of mx_main/mx_pass and mx_sep_resid
+    float *part3;                        // per-CTA partial norms of mx_main / mx_pass
+    double *partS;                       // per-CTA partial norms of mx_sep_resid
     MixState *state;
     const unsigned *beta_bits;
 };
@@ -97,23 +100,40 @@ struct MxArgs {
 // ------------------------------------------------------------------ prep
 __global__ void mx_prep(TriGeom g, const double *__restrict__ d, const double *__restrict__ e, float *dPf,
                         float *dPl, float *ePf, float *ePl, unsigned *beta_bits) {
+    // d' = t d - c and e' = t e as float pairs, formed in float-float arithmetic from the
+    // pairs of d, e, t and c (binary32 and integer operations only: this part's FP64 unit
+    // would bind), and the row sums |d'| + |e'_i| + |e'_{i-1}| bounded in binary32 rounded
+    // upwards
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const f32x2 t2 = split_bits(g.t), c2 = split_bits(g.cshift);
+    const bool plain = g.t == 1.0 && g.cshift == 0.0;  // t T - c I = T: the splits as they are
+    auto bound = [](f32x2 v) { return __fadd_ru(fabsf(v.hi), fabsf(v.lo)); };
     float bmax = 0.f;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < g.N; i += stride) {
-        const double dv = g.t * d[i] - g.cshift;
-        const double ev = i + 1 < g.N ? g.t * e[i] : 0.0;
-        const double evp = i > 0 ? g.t * e[i - 1] : 0.0;
-        const f32x2 ds = split_bits(dv), es = split_bits(ev);
+        f32x2 ds = split_bits(d[i]);
+        f32x2 es = i + 1 < g.N ? split_bits(e[i]) : f32x2{0.f, 0.f};
+        f32x2 esp = i > 0 ? split_bits(e[i - 1]) : f32x2{0.f, 0.f};
+        if (!plain) {
+            ds = dd_fma(t2, ds, -c2);
+            es = t2 * es;
+            esp = t2 * esp;
+        }
         dPf[i] = ds.hi;
         dPl[i] = ds.lo;
         ePf[i] = es.hi;
         ePl[i] = es.lo;
-        bmax = fmaxf(bmax, __double2float_ru(fabs(dv) + fabs(ev) + fabs(evp)));
+        bmax = fmaxf(bmax, __fadd_ru(__fadd_ru(bound(ds), bound(es)), bound(esp)));
     }
+    // one atomic per CTA (one per warp serialises thousands of them on one address)
+    __shared__ float wmax[32];
     for (int off = 16; off > 0; off >>= 1) bmax = fmaxf(bmax, __shfl_xor_sync(0xffffffffu, bmax, off));
-    if ((threadIdx.x & 31) == 0) atomicMax(beta_bits, __float_as_uint(bmax));  // non-negative: bit order = value order
+    if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = bmax;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) bmax = fmaxf(bmax, wmax[w]);
+        atomicMax(beta_bits, __float_as_uint(bmax));  // non-negative: bit order = value order
+    }
 }
-
 __global__ void mx_prep_v(int64_t n, const double *__restrict__ V, float *VPf, float *VPl) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
@@ -124,15 +144,36 @@ __global__ void mx_prep_v(int64_t n, const double *__restrict__ V, float *VPf, f
 }
 
 // ------------------------------------------------------------------ residual arithmetic
-// s + c  -=  (ah + al) x : the binary32 product ah x split exactly by an FMA, the
-// rounding error of the running sum s collected in c.
-EXPM_D void csum_sub(float &s, float &c, float ah, float al, float x) {
-    const float p = __fmul_rn(ah, x);
-    float pe = __fmaf_rn(ah, x, -p);
-    pe = __fmaf_rn(al, x, pe);
-    const f32x2 t = two_sum(s, -p);
-    s = t.hi;
-    c = __fadd_rn(c, __fsub_rn(t.lo, pe));
+// The residual of a row pairs its two components term by term, each term a real
+// coefficient (a float pair) times a binary32 pair of x entries:
+//   (a, a)(xs.re, xs.im), (-Im theta, Im theta)(xs.im, xs.re), (e_l, e_l)(xl.re, xl.im),
+//   (e_r, e_r)(xr.re, xr.im),   a = d_q + Re theta,
+// so both components run through one packed (two-lane) instruction stream.
+// s + c  -=  (ah + al) x  on pairs: the binary32 product ah x split exactly by an FMA,
+// the rounding error of the running sum s (TwoSum of s and -p) collected in c.
+EXPM_D void pcsum_sub(uint64_t &s, uint64_t &c, uint64_t ah, uint64_t al, uint64_t x) {
+    const uint64_t p = pmul2(ah, x);
+    const uint64_t pe = ffma2(al, x, ffma2(ah, x, pneg2(p)));
+    const uint64_t t = psub2(s, p);
+    const uint64_t bb = psub2(t, s);
+    const uint64_t err = psub2(psub2(s, psub2(t, bb)), padd2(p, bb));
+    s = t;
+    c = padd2(c, psub2(err, pe));
+}
+// the four terms of a row, then the pair (s, c) renormalised by TwoSum
+EXPM_D void mx_resid_terms(uint64_t s, uint64_t c, f32x2 dq, f32x2 el, f32x2 er, f32x2 thr, f32x2 thi, cx<float> xl,
+                           cx<float> xs, cx<float> xr, cx<float> &hi, cx<float> &lo) {
+    const f32x2 t = two_sum(dq.hi, thr.hi);  // a = d_q + Re theta as an (unnormalised) pair
+    const float alo = __fadd_rn(t.lo, __fadd_rn(dq.lo, thr.lo));
+    pcsum_sub(s, c, pk2(t.hi, t.hi), pk2(alo, alo), pk2(xs.re, xs.im));
+    pcsum_sub(s, c, pk2(-thi.hi, thi.hi), pk2(-thi.lo, thi.lo), pk2(xs.im, xs.re));
+    pcsum_sub(s, c, pk2(el.hi, el.hi), pk2(el.lo, el.lo), pk2(xl.re, xl.im));
+    pcsum_sub(s, c, pk2(er.hi, er.hi), pk2(er.lo, er.lo), pk2(xr.re, xr.im));
+    const uint64_t h = padd2(s, c);
+    const uint64_t bb = psub2(h, s);
+    const uint64_t l = padd2(psub2(s, psub2(h, bb)), psub2(c, bb));
+    upk2(h, hi.re, hi.im);
+    upk2(l, lo.re, lo.im);
 }
 
 // Pass 0:  r = v - [ (d_q + theta) x_q + e_{q-1} x_{q-1} + e_q x_{q+1} ]  for one row, with
@@ -140,42 +181,13 @@ EXPM_D void csum_sub(float &s, float &c, float ah, float al, float x) {
 // (hi, lo) per component.
 EXPM_D void mx_resid_first(f32x2 v, f32x2 dq, f32x2 el, f32x2 er, f32x2 thr, f32x2 thi, cx<float> xl,
                            cx<float> xs, cx<float> xr, cx<float> &hi, cx<float> &lo) {
-    const f32x2 t = two_sum(dq.hi, thr.hi);  // a = d_q + Re theta as an (unnormalised) pair
-    const float alo = __fadd_rn(t.lo, __fadd_rn(dq.lo, thr.lo));
-    float sr = v.hi, cr = v.lo;
-    csum_sub(sr, cr, t.hi, alo, xs.re);
-    csum_sub(sr, cr, -thi.hi, -thi.lo, xs.im);
-    csum_sub(sr, cr, el.hi, el.lo, xl.re);
-    csum_sub(sr, cr, er.hi, er.lo, xr.re);
-    const float p = __fmul_rn(t.hi, xs.im);  // imaginary part: v is real
-    float pe = __fmaf_rn(t.hi, xs.im, -p);
-    pe = __fmaf_rn(alo, xs.im, pe);
-    float si = -p, ci = -pe;
-    csum_sub(si, ci, thi.hi, thi.lo, xs.re);
-    csum_sub(si, ci, el.hi, el.lo, xl.im);
-    csum_sub(si, ci, er.hi, er.lo, xr.im);
-    const f32x2 a = two_sum(sr, cr), b = two_sum(si, ci);
-    hi = {a.hi, b.hi};
-    lo = {a.lo, b.lo};
+    mx_resid_terms(pk2(v.hi, 0.f), pk2(v.lo, 0.f), dq, el, er, thr, thi, xl, xs, xr, hi, lo);
 }
 
 // Later stored residuals:  r_{k+1} = r_k - M d_k  with r_k = rh + rl, float-float accurate.
 EXPM_D void mx_resid_comp(cx<float> rh, cx<float> rl, f32x2 dq, f32x2 el, f32x2 er, f32x2 thr, f32x2 thi,
                           cx<float> xl, cx<float> xs, cx<float> xr, cx<float> &hi, cx<float> &lo) {
-    const f32x2 t = two_sum(dq.hi, thr.hi);
-    const float alo = __fadd_rn(t.lo, __fadd_rn(dq.lo, thr.lo));
-    float sr = rh.re, cr = rl.re, si = rh.im, ci = rl.im;
-    csum_sub(sr, cr, t.hi, alo, xs.re);
-    csum_sub(sr, cr, -thi.hi, -thi.lo, xs.im);
-    csum_sub(sr, cr, el.hi, el.lo, xl.re);
-    csum_sub(sr, cr, er.hi, er.lo, xr.re);
-    csum_sub(si, ci, t.hi, alo, xs.im);
-    csum_sub(si, ci, thi.hi, thi.lo, xs.re);
-    csum_sub(si, ci, el.hi, el.lo, xl.im);
-    csum_sub(si, ci, er.hi, er.lo, xr.im);
-    const f32x2 a = two_sum(sr, cr), b = two_sum(si, ci);
-    hi = {a.hi, b.hi};
-    lo = {a.lo, b.lo};
+    mx_resid_terms(pk2(rh.re, rh.im), pk2(rl.re, rl.im), dq, el, er, thr, thi, xl, xs, xr, hi, lo);
 }
 
 // The verification residual r_{K+1} = r_K - M d_K in binary32: its terms are already
@@ -247,17 +259,20 @@ EXPM_D void y_store_pair(double *Y, int64_t idx, f32x2s v, bool final_) {  // Y[
 EXPM_D void y_add(double *Y, int64_t idx, float v, bool final_) {
     f32x2 *p = reinterpret_cast<f32x2 *>(Y) + idx;
     const f32x2 y = *p;
-    if (final_) {
-        Y[idx] = (widen_bits(y.hi) + widen_bits(y.lo)) + widen_bits(v);
+    if (final_) {  // the three terms added in float-float, one binary64 addition for the pair
+        const f32x2 s = two_sum(y.hi, v);
+        const f32x2 r = fast_two_sum(s.hi, __fadd_rn(s.lo, y.lo));
+        Y[idx] = widen_bits(r.hi) + widen_bits(r.lo);
     } else {
         const f32x2 s = two_sum(y.hi, v);
         *p = fast_two_sum(s.hi, __fadd_rn(s.lo, y.lo));
     }
 }
 
-// Sum per system lane over the CTA into part[blockIdx][lane][2] (fixed order).
+// Sum per system lane over the CTA into part[blockIdx][lane][2] (binary32, fixed order:
+// these feed only the stopping test's norms).
 template <int LG>
-EXPM_D void cta_norms(float rn2, float xn2, double *part) {
+EXPM_D void cta_norms(float rn2, float xn2, float *part) {
     __shared__ float red[MX_CTA / 32][LG][2];
 #pragma unroll
     for (int off = 16; off >= LG; off >>= 1) {
@@ -272,8 +287,8 @@ EXPM_D void cta_norms(float rn2, float xn2, double *part) {
     __syncthreads();
     if (threadIdx.x < 2 * LG) {
         const int l = threadIdx.x >> 1, c = threadIdx.x & 1;
-        double acc = 0.0;
-        for (int w = 0; w < MX_CTA / 32; ++w) acc += (double)red[w][l][c];
+        float acc = 0.f;
+        for (int w = 0; w < MX_CTA / 32; ++w) acc += red[w][l][c];
         part[((int64_t)blockIdx.x * LG + l) * 2 + c] = acc;
     }
 }
@@ -573,37 +588,90 @@ EXPM_D cx<float> zstep(cx<float> gi, float el, cx<float> f, cx<float> zp) {
 
 // ------------------------------------------------------------------ pass 0 end values
 // y_b = M~_b^{-1} v_b: the top-down sweep ends at y_b[last], the bottom-up (UL) sweep,
-// h_i = g^_i (v_i - e'_i h_{i+1}), at y_b[first]; nothing is stored per row.
-template <int LG, bool ST>
-__global__ void __launch_bounds__(MX_CTA) mx_ends(TriGeom g, MxArgs a) {
-    extern __shared__ __align__(16) float mx_smem[];
-    MxLane t;
-    const bool ok = mx_lane<LG>(g, t);
-    MxRows<ST> rw;
-    mx_stage<LG, ST>(g, a, true, 2, mx_smem, ok ? t.first : 0, ok ? t.j : 0, ok ? t.s : 0, rw);
-    if (!ok || !t.active) return;
-    const int len = t.len;
-    cx<float> z = {0.f, 0.f};
-    int i = 0;
-    for (; i + MX_CK <= len; i += MX_CK) {
+// h_i = g^_i (v_i - e'_i h_{i+1}), at y_b[first]; nothing is stored per row.  One thread
+// per (block, system, group of MX_EC columns): a row's pivot and e' serve all the
+// group's columns, whose entries of V are contiguous, and the columns' recurrences are
+// independent chains.  Rows are read straight from global memory MX_CK at a time, all
+// loads of a chunk issued before its first use.
+constexpr int MX_EC = 2;
+template <int LG, bool V4>
+__global__ void __launch_bounds__(128) mx_ends(TriGeom g, MxArgs a) {
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int Rc = g.Rc, nq = (Rc + MX_EC - 1) / MX_EC;
+    const int q = (int)(tid % nq);
+    const int sl = (int)((tid / nq) % LG);
+    const int b = (int)(tid / ((int64_t)nq * LG));
+    if (b >= g.P || sl >= g.S) return;
+    const int64_t first = (int64_t)b * g.B;
+    const int len = (b < g.P - 1) ? g.m : (int)(g.N - first);
+    const int j0 = q * MX_EC, nc = Rc - j0 < MX_EC ? Rc - j0 : MX_EC;
+    const cx<float> *G = a.pg + first * LG + sl, *U = a.pu + first * LG + sl;
+    const float *ep = a.ePf + first;
+    const float *vp = a.VPf + first * Rc + j0;
+    auto load_v = [&](int i, float (&v)[MX_EC]) {
+        if (V4) {
+            const float2 w = *reinterpret_cast<const float2 *>(vp + (int64_t)i * Rc);
+            v[0] = w.x;
+            v[1] = w.y;
+        } else {
+#pragma unroll
+            for (int c = 0; c < MX_EC; ++c) v[c] = c < nc ? vp[(int64_t)i * Rc + c] : 0.f;
+        }
+    };
+    cx<float> z[MX_EC];
+#pragma unroll
+    for (int c = 0; c < MX_EC; ++c) z[c] = {0.f, 0.f};
+    for (int i0 = 0; i0 < len; i0 += MX_CK) {
+        cx<float> p[MX_CK];
+        float el[MX_CK], v[MX_CK][MX_EC];
 #pragma unroll
         for (int r = 0; r < MX_CK; ++r) {
-            const float el = (i + r) > 0 ? rw.eh[i + r - 1] : 0.f;
-            z = zstep(rw.g[(i + r) * LG], el, cx<float>{rw.v_hi(i + r), 0.f}, z);
+            const int i = i0 + r;
+            if (i < len) {
+                p[r] = G[(int64_t)i * LG];
+                el[r] = i > 0 ? ep[i - 1] : 0.f;
+                load_v(i, v[r]);
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < MX_CK; ++r) {
+            if (i0 + r < len) {
+#pragma unroll
+                for (int c = 0; c < MX_EC; ++c) z[c] = zstep(p[r], el[r], cx<float>{v[r][c], 0.f}, z[c]);
+            }
         }
     }
-    for (; i < len; ++i) z = zstep(rw.g[i * LG], i > 0 ? rw.eh[i - 1] : 0.f, cx<float>{rw.v_hi(i), 0.f}, z);
-    cx<float> h = {0.f, 0.f};
-    i = len - 1;
-    h = zstep(rw.u[i * LG], 0.f, cx<float>{rw.v_hi(i), 0.f}, h);  // the last row has no coupling inside the block
-    for (i = len - 2; i - MX_CK + 1 >= 0; i -= MX_CK) {
+    cx<float> h[MX_EC];
 #pragma unroll
-        for (int r = 0; r < MX_CK; ++r) h = zstep(rw.u[(i - r) * LG], rw.eh[i - r], cx<float>{rw.v_hi(i - r), 0.f}, h);
+    for (int c = 0; c < MX_EC; ++c) h[c] = {0.f, 0.f};
+    for (int i0 = len - 1; i0 >= 0; i0 -= MX_CK) {
+        cx<float> p[MX_CK];
+        float er[MX_CK], v[MX_CK][MX_EC];
+#pragma unroll
+        for (int r = 0; r < MX_CK; ++r) {
+            const int i = i0 - r;
+            if (i >= 0) {
+                p[r] = U[(int64_t)i * LG];
+                er[r] = i < len - 1 ? ep[i] : 0.f;  // the last row has no coupling inside the block
+                load_v(i, v[r]);
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < MX_CK; ++r) {
+            if (i0 - r >= 0) {
+#pragma unroll
+                for (int c = 0; c < MX_EC; ++c) h[c] = zstep(p[r], er[r], cx<float>{v[r][c], 0.f}, h[c]);
+            }
+        }
     }
-    for (; i >= 0; --i) h = zstep(rw.u[i * LG], rw.eh[i], cx<float>{rw.v_hi(i), 0.f}, h);
-    cx<float> *YE = a.yend + (((int64_t)t.s * g.P + t.b) * g.Rc + t.j) * 2;
-    YE[0] = h;
-    YE[1] = z;
+#pragma unroll
+    for (int c = 0; c < MX_EC; ++c) {
+        if (c < nc) {
+            cx<float> *YE = a.yend + (((int64_t)sl * Rc + j0 + c) * g.P + b) * 2;
+            YE[0] = h[c];
+            YE[1] = z[c];
+        }
+    }
 }
 
 // ------------------------------------------------------------------ block solves
@@ -846,7 +914,7 @@ __global__ void __launch_bounds__(MX_CTA, 4) mx_main(TriGeom g, MxArgs a, TriPol
             XB[0] = xfirst;
             XB[1] = xlast;
             if (STORE) {
-                cx<float> *YE = a.yend + (((int64_t)t.s * g.P + t.b) * Rc + t.j) * 2;
+                cx<float> *YE = a.yend + (((int64_t)t.s * Rc + t.j) * g.P + t.b) * 2;
                 YE[0] = h;
                 YE[1] = yw;
             }
@@ -975,7 +1043,7 @@ __global__ void __launch_bounds__(MX_CTA, 4) mx_pass(TriGeom g, MxArgs a, TriPol
             XB[0] = xfirst;
             XB[1] = xlast;
             if (STORE) {
-                cx<float> *YE = a.yend + (((int64_t)t.s * g.P + t.b) * Rc + t.j) * 2;
+                cx<float> *YE = a.yend + (((int64_t)t.s * Rc + t.j) * g.P + t.b) * 2;
                 YE[0] = h;
                 YE[1] = yw;
             }
@@ -1043,42 +1111,154 @@ __global__ void __launch_bounds__(MX_CTA) mx_sep_resid(TriGeom g, MxArgs a, TriP
     }
 }
 
+// ------------------------------------------------------------------ reduced system
+// Row b of the reduced separator system (b < P-1) couples sigma_{b-1}, sigma_b and
+// sigma_{b+1} through the corner entries of the neighbouring block inverses
+// (tridiag.cu's Schur complement):
+//   A_b = -e'_{p-1} e'_{p-B} u_b[last],   C_b = -e'_p e'_{p+B-1} w_{b+1}[first],
+//   B_b = d'_p + theta - e'_{p-1}^2 w_b[last] - e'_p^2 u_{b+1}[first],
+//   D_b = rhs_p - e'_{p-1} y_b[last] - e'_p y_{b+1}[first]            (p = bB + m).
+// A, B, C depend on neither the column nor the pass: mx_cr_coef forms them once per
+// factorization, stored contiguously per system with e'_{p-1}, e'_p, so that the pass's
+// CR reads them coalesced instead of gathering rows B apart.
+struct __align__(16) MxCrc {
+    cx<float> A, B, C;
+    float el, er;
+};
+
+__global__ void __launch_bounds__(128) mx_cr_coef(TriGeom g, const float *__restrict__ dPf,
+                                                  const float *__restrict__ ePf, TriPoles ps,
+                                                  const cx<float> *__restrict__ spk, MxCrc *crc) {
+    const int n = g.P - 1;
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (int64_t)n * g.S) return;
+    const int s = (int)(t / n), b = (int)(t % n);
+    const int64_t r = (int64_t)b * g.B + g.m;  // separator row
+    const float el = ePf[r - 1], er = ePf[r];
+    const cx<float> *SP = spk + (int64_t)s * g.P * 4;
+    const cx<float> uL = SP[4 * b + 1], wL = SP[4 * b + 3];
+    const cx<float> u0n = SP[4 * (b + 1) + 0], w0n = SP[4 * (b + 1) + 2];
+    const cx<float> th = {__double2float_rn(ps.th_re[s]), __double2float_rn(ps.th_im[s])};
+    MxCrc c;
+    c.A = b >= 1 ? -scale(el * ePf[r - g.B], uL) : cxz<float>();
+    c.C = b + 1 <= n - 1 ? -scale(er * ePf[r + g.B - 1], w0n) : cxz<float>();
+    c.B = cx<float>{dPf[r] + th.re, th.im} - scale(el * el, wL) - scale(er * er, u0n);
+    c.el = el;
+    c.er = er;
+    crc[t] = c;
+}
+
+// The pass's reduced system, one CTA of 512 threads per (system, column), solved by cyclic
+// reduction in shared memory; the right-hand side is V's separator entry (pass 0) or the
+// separator residual r_k (later passes).
+__global__ void __launch_bounds__(512) mx_cr(TriGeom g, const MxCrc *__restrict__ crc,
+                                             const float *__restrict__ VPf, const cx<float> *__restrict__ sepRhs,
+                                             const cx<float> *__restrict__ yend, cx<float> *__restrict__ sigma,
+                                             const int *skip) {
+    if (skip != nullptr && *skip) return;  // refinement already converged (uniform over the launch)
+    extern __shared__ __align__(16) unsigned char mx_cr_smem[];
+    const int n = g.P - 1;
+    const int np = (int)cr_len<float>(n);
+    cx<float> *A = reinterpret_cast<cx<float> *>(mx_cr_smem);
+    cx<float> *Bc = A + np;
+    cx<float> *C = Bc + np;
+    cx<float> *D = C + np;
+    const int s = blockIdx.x / g.Rc;
+    const int j = blockIdx.x % g.Rc;
+    const MxCrc *CF = crc + (int64_t)s * n;
+    const cx<float> *YE = yend + ((int64_t)s * g.Rc + j) * g.P * 2;
+    // four rows per thread and round, all their loads issued before any is used
+    constexpr int U = 4;
+    for (int b0 = threadIdx.x; b0 < n; b0 += U * blockDim.x) {
+        MxCrc c[U];
+        cx<float> yL[U], y0n[U], rhs[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int b = b0 + u * blockDim.x;
+            if (b < n) {
+                c[u] = CF[b];
+                yL[u] = YE[2 * b + 1];
+                y0n[u] = YE[2 * (b + 1)];
+                const int64_t r = (int64_t)b * g.B + g.m;
+                rhs[u] = sepRhs != nullptr ? sepRhs[((int64_t)s * g.P + b) * g.Rc + j] : cx<float>{VPf[r * g.Rc + j], 0.f};
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int b = b0 + u * blockDim.x;
+            if (b < n) {
+                const int bp = cr_ix<float>(b);
+                A[bp] = c[u].A;
+                Bc[bp] = c[u].B;
+                C[bp] = c[u].C;
+                D[bp] = rhs[u] - scale(c[u].el, yL[u]) - scale(c[u].er, y0n[u]);
+            }
+        }
+    }
+    __syncthreads();
+    cr_solve_smem<float>(A, Bc, C, D, n);
+    cx<float> *SG = sigma + (int64_t)s * g.P * g.Rc;
+    for (int b = threadIdx.x; b < n; b += blockDim.x) SG[(int64_t)b * g.Rc + j] = D[cr_ix<float>(b)];
+}
+
 // ------------------------------------------------------------------ stopping test
-// `tps` threads per system (a multiple of 32), system s = threadIdx.x / tps.  After pass
-// `pass`: iters = pass; with a residual, the relative residual
-// max_s ||r_s|| / ((beta + |theta_s|) ||x_s||) and the stopping decision.  The partial
-// sums are added in a fixed order (strided per thread, then a tree), so the decision does
-// not depend on scheduling.
-__global__ void mx_check(MxArgs a, TriPoles ps, int S, int LG, int tps, int n3, int nS, int pass, int has_resid,
-                         int first, double tol) {
-    __shared__ double red[2][1024];
+// One CTA of MX_CHECK_T threads.  After pass `pass`: iters = pass; with a residual, the
+// relative residual max_s ||r_s|| / ((beta + |theta_s|) ||x_s||) and the stopping
+// decision.  The partial sums are added in a fixed order, so the decision does not
+// depend on scheduling: the solve kernels' partials [cta][lane][2] (binary32) are read coalesced,
+// thread t taking entries t, t + T, ... (all of one (lane, component), since 2 LG
+// divides T) into four interleaved sums, then a tree over the threads of each
+// (lane, component); the separator partials [system][cta][2] by `tps` threads per system
+// (a power of two), system s = t / tps, strided, then a tree.
+constexpr int MX_CHECK_T = 1024;
+__global__ void __launch_bounds__(MX_CHECK_T) mx_check(MxArgs a, TriPoles ps, int S, int LG, int tps, int n3, int nS,
+                                                       int pass, int has_resid, int first, double tol) {
+    __shared__ double red[2][MX_CHECK_T];
+    __shared__ float redf[MX_CHECK_T];
+    __shared__ double bins[2 * 32];  // (lane, component) sums of the solve kernels' partials
     __shared__ double rel[TRI_MAXSYS];
     MixState *st = a.state;
     if (st->done) return;
-    const int s = threadIdx.x / tps, l = threadIdx.x % tps;
+    const int t = threadIdx.x;
     if (has_resid) {
+        // (binary32 here: a CTA runs on one SM, whose FP64 rate would bind)
+        const int64_t n = (int64_t)n3 * LG * 2;
+        float acc[4] = {0.f, 0.f, 0.f, 0.f};
+        int64_t e = t;
+        for (; e + 3 * MX_CHECK_T < n; e += 4 * MX_CHECK_T) {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) acc[k] += a.part3[e + k * MX_CHECK_T];
+        }
+        for (int k = 0; e < n; e += MX_CHECK_T, ++k) acc[k] += a.part3[e];  // fewer than 4 left
+        redf[t] = (acc[0] + acc[1]) + (acc[2] + acc[3]);
+        __syncthreads();
+        for (int h = MX_CHECK_T / 2; h >= 2 * LG; h >>= 1) {
+            if (t < h) redf[t] += redf[t + h];
+            __syncthreads();
+        }
+        if (t < 2 * LG) bins[t] = (double)redf[t];
+        __syncthreads();
+        const int s = t / tps, l = t % tps;
         double r2 = 0.0, x2 = 0.0;
-        for (int i = l; i < n3; i += tps) {
-            r2 += a.part3[((int64_t)i * LG + s) * 2];
-            x2 += a.part3[((int64_t)i * LG + s) * 2 + 1];
+        if (s < S) {
+            for (int i = l; i < nS; i += tps) {
+                r2 += a.partS[((int64_t)s * nS + i) * 2];
+                x2 += a.partS[((int64_t)s * nS + i) * 2 + 1];
+            }
         }
-        for (int i = l; i < nS; i += tps) {
-            r2 += a.partS[((int64_t)s * nS + i) * 2];
-            x2 += a.partS[((int64_t)s * nS + i) * 2 + 1];
-        }
-        red[0][threadIdx.x] = r2;
-        red[1][threadIdx.x] = x2;
+        red[0][t] = r2;
+        red[1][t] = x2;
         __syncthreads();
         for (int h = tps / 2; h > 0; h >>= 1) {
             if (l < h) {
-                red[0][threadIdx.x] += red[0][threadIdx.x + h];
-                red[1][threadIdx.x] += red[1][threadIdx.x + h];
+                red[0][t] += red[0][t + h];
+                red[1][t] += red[1][t + h];
             }
             __syncthreads();
         }
-        if (l == 0) {
-            r2 = red[0][threadIdx.x];
-            x2 = red[1][threadIdx.x];
+        if (s < S && l == 0) {
+            r2 = red[0][t] + bins[2 * s];
+            x2 = red[1][t] + bins[2 * s + 1];
             if (first) st->xnorm2[s] = x2;
             const double xn = sqrt(first ? x2 : st->xnorm2[s]);
             const double beta = (double)__uint_as_float(*a.beta_bits);
@@ -1099,7 +1279,7 @@ __global__ void mx_check(MxArgs a, TriPoles ps, int S, int LG, int tps, int n3, 
 }
 
 struct MixLayout {
-    size_t dPf, dPl, ePf, ePl, beta, pg, pu, spk, factor_total;
+    size_t dPf, dPl, ePf, ePl, beta, pg, pu, spk, crc, factor_total;
     size_t VPf, VPl, yend, sig, xb, sepR, sepLo, R, Rlo, ckpt, part3, partS, state, solve_total;
     int nchk, n3, nSx;
 };
@@ -1118,6 +1298,7 @@ static MixLayout mx_layout(const TriGeom &g, int max_refine) {
     L.pg = off; off += al(N * LG * 8);
     L.pu = off; off += al(N * LG * 8);
     L.spk = off; off += al(S * P * 4 * 8);
+    L.crc = off; off += al(S * std::max<size_t>(P - 1, 1) * sizeof(MxCrc));
     L.factor_total = off;
     L.nchk = (g.B + MX_CK - 1) / MX_CK;
     L.n3 = (int)((P * Rc * LG + MX_CTA - 1) / MX_CTA);
@@ -1187,11 +1368,11 @@ static cudaError_t launch_pass(const TriGeom &g, const MxArgs &a, const TriPoles
                              : launch_pass_t<LG, false>(g, a, ps, mode, grid, tile, st);
 }
 template <int LG>
-static cudaError_t launch_ends(const TriGeom &g, const MxArgs &a, unsigned grid, size_t smem, cudaStream_t st) {
-    cudaError_t err = smem > 0 ? mx_attr(mx_ends<LG, true>) : cudaSuccess;
-    if (err != cudaSuccess) return err;
-    if (smem > 0) mx_ends<LG, true><<<grid, MX_CTA, smem, st>>>(g, a);
-    else mx_ends<LG, false><<<grid, MX_CTA, 0, st>>>(g, a);
+static cudaError_t launch_ends(const TriGeom &g, const MxArgs &a, cudaStream_t st) {
+    const int64_t n = (int64_t)g.P * LG * ((g.Rc + MX_EC - 1) / MX_EC);
+    const unsigned grid = (unsigned)((n + 127) / 128);
+    if (g.Rc % 2 == 0) mx_ends<LG, true><<<grid, 128, 0, st>>>(g, a);  // rows of V 8-byte aligned
+    else mx_ends<LG, false><<<grid, 128, 0, st>>>(g, a);
     return cudaGetLastError();
 }
 template <int LG>
@@ -1274,7 +1455,14 @@ cudaError_t tri_mixed_factor(const TriGeom &g, const double *d, const double *e,
     if (err != cudaSuccess) return err;
     cx<float> *pg = (cx<float> *)(p + L.pg), *pu = (cx<float> *)(p + L.pu);
     cx<float> *spk = (cx<float> *)(p + L.spk);
-    return prof.timed("tri_mixed_pivots", st, [&] { MX_DISPATCH(launch_pivots, g, dPf, ePf, ps, pg, pu, spk, st); });
+    err = prof.timed("tri_mixed_pivots", st, [&] { MX_DISPATCH(launch_pivots, g, dPf, ePf, ps, pg, pu, spk, st); });
+    if (err != cudaSuccess || g.P <= 1) return err;
+    MxCrc *crc = (MxCrc *)(p + L.crc);
+    const int64_t nc = (int64_t)(g.P - 1) * g.S;
+    return prof.timed("tri_mixed_cr_coef", st, [&] {
+        mx_cr_coef<<<(unsigned)((nc + 127) / 128), 128, 0, st>>>(g, dPf, ePf, ps, spk, crc);
+        return cudaGetLastError();
+    });
 }
 
 cudaError_t tri_mixed_solve(const TriGeom &g, const double *V, double *Y, const TriPoles &ps, const void *fwork,
@@ -1291,6 +1479,7 @@ cudaError_t tri_mixed_solve(const TriGeom &g, const double *V, double *Y, const 
     a.pg = (const cx<float> *)(p + L.pg);
     a.pu = (const cx<float> *)(p + L.pu);
     a.spk = (const cx<float> *)(p + L.spk);
+    a.crc = (const MxCrc *)(p + L.crc);
     float *VPf = (float *)(q + L.VPf), *VPl = (float *)(q + L.VPl);
     a.VPf = VPf;
     a.VPl = VPl;
@@ -1302,7 +1491,7 @@ cudaError_t tri_mixed_solve(const TriGeom &g, const double *V, double *Y, const 
     a.R = mo.max_refine >= 1 ? (cx<float> *)(q + L.R) : nullptr;
     a.Rlo = mo.max_refine >= 2 ? (cx<float> *)(q + L.Rlo) : nullptr;
     a.ckpt = (float2 *)(q + L.ckpt);
-    a.part3 = (double *)(q + L.part3);
+    a.part3 = (float *)(q + L.part3);
     a.partS = (double *)(q + L.partS);
     a.state = (MixState *)(q + L.state);
     a.Y = Y;
@@ -1318,14 +1507,14 @@ cudaError_t tri_mixed_solve(const TriGeom &g, const double *V, double *Y, const 
     const unsigned grid = (unsigned)L.n3;
     const size_t smem_v = mx_smem_bytes(g, true, 2);
     if (g.P > 1) {
-        err = prof.timed("tri_mixed_ends", st, [&] { MX_DISPATCH(launch_ends, g, a, grid, smem_v, st); });
+        err = prof.timed("tri_mixed_ends", st, [&] { MX_DISPATCH(launch_ends, g, a, st); });
         if (err != cudaSuccess) return err;
         // a ceiling for the largest reduced system, never lowered under a concurrent launch
-        err = cudaFuncSetAttribute(tri_reduced_cr<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   (int)(4 * (size_t)(MX_PMAX - 1) * sizeof(cx<float>)));
+        err = cudaFuncSetAttribute(mx_cr, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)(4 * cr_len<float>(MX_PMAX - 1) * sizeof(cx<float>)));
         if (err != cudaSuccess) return err;
     }
-    const size_t smem = g.P > 1 ? (size_t)4 * (g.P - 1) * sizeof(cx<float>) : 0;
+    const size_t smem = g.P > 1 ? 4 * cr_len<float>(g.P - 1) * sizeof(cx<float>) : 0;
     const unsigned sgrid = (unsigned)L.nSx;
     const int npass = 1 + mo.max_refine;
     for (int k = 0; k < npass; ++k) {
@@ -1340,10 +1529,9 @@ cudaError_t tri_mixed_solve(const TriGeom &g, const double *V, double *Y, const 
         if (k >= 1 && !last) mode |= MX_COMP | MX_LO_IN;
         if (!last && k + 1 < npass - 1) mode |= MX_LO_OUT;
         if (g.P > 1) {
-            err = prof.timed("tri_reduced_cr<f32>", st, [&] {
-                tri_reduced_cr<float><<<g.S * g.Rc, 512, smem, st>>>(g, a.dPf, a.ePf, VPf, k == 0 ? nullptr : a.sepR,
-                                                                      ps, a.spk, a.yend, a.sig,
-                                                                      k == 0 ? nullptr : &a.state->done);
+            err = prof.timed("tri_mixed_cr", st, [&] {
+                mx_cr<<<g.S * g.Rc, 512, smem, st>>>(g, a.crc, VPf, k == 0 ? nullptr : a.sepR, a.yend, a.sig,
+                                                     k == 0 ? nullptr : &a.state->done);
                 return cudaGetLastError();
             });
             if (err != cudaSuccess) return err;
@@ -1365,9 +1553,9 @@ cudaError_t tri_mixed_solve(const TriGeom &g, const double *V, double *Y, const 
         }
         err = prof.timed("tri_mixed_check", st, [&] {
             int tps = 128;
-            while (tps > 32 && tps * g.S > 1024) tps /= 2;
-            mx_check<<<1, tps * g.S, 0, st>>>(a, ps, g.S, g.LG, tps, L.n3, g.P > 1 ? L.nSx : 0, k, resid ? 1 : 0,
-                                              k == 0 ? 1 : 0, mo.tol);
+            while (tps > 32 && tps * g.S > MX_CHECK_T) tps /= 2;
+            mx_check<<<1, MX_CHECK_T, 0, st>>>(a, ps, g.S, g.LG, tps, L.n3, g.P > 1 ? L.nSx : 0, k, resid ? 1 : 0,
+                                               k == 0 ? 1 : 0, mo.tol);
             return cudaGetLastError();
         });
         if (err != cudaSuccess) return err;
