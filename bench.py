@@ -97,10 +97,11 @@ MIXED_OPTS = dict(tol=1e-10, max_refine=1)
 # TRAFFIC_SRC_SHA (otherwise reported as null)
 TRAFFIC_K3 = 2.8495e9
 TRAFFIC_SRC_SHA = "b5a5c00d7042b497"
-# dram bytes (read + write) per launch of mx_main<8> at N = 2^20 (one ncu capture of the
-# headline command), valid while tridiag_mixed.cu hashes to TRAFFIC_MX_SHA
-TRAFFIC_MX = None
-TRAFFIC_MX_SHA = ""
+# dram bytes (read + write) per launch of mx_main<8> at N = 2^20: one ncu capture at
+# N = 2^19 (395.8 MB: 114.1 MB read + 281.7 MB write) scaled by 2, the traffic being
+# proportional to N; valid while tridiag_mixed.cu hashes to TRAFFIC_MX_SHA
+TRAFFIC_MX = 7.917e8
+TRAFFIC_MX_SHA = "afae6e6686f3e037"
 
 
 def log(*a):
@@ -125,9 +126,10 @@ def parse():
     ap.add_argument("--mixed-only", action="store_true",
                     help="time only the binary32 + refinement path (profiling runs)")
     ap.add_argument("--workload", default="laplacian",
-                    choices=["laplacian", "dense", "batched", "served", "laplacian2d"],
+                    choices=["laplacian", "dense", "batched", "served", "laplacian2d", "dense_small"],
                     help="laplacian: the headline line; the others print their own lines "
-                         "(dense 4096 Hermitian x 256 RHS; 4096-instance uneven batch; served stream)")
+                         "(dense 4096 Hermitian x 256 RHS; 4096-instance uneven batch; served stream; "
+                         "dense 64 x 64 degree 12, --steps evaluations per path)")
     ap.add_argument("--dense-n", type=int, default=4096)
     ap.add_argument("--batch-count", type=int, default=4096)
     ap.add_argument("--served-requests", type=int, default=2000)
@@ -887,6 +889,9 @@ def main():
         return
     if args.workload == "served":
         run_served(args)
+        return
+    if args.workload == "dense_small":
+        print(json.dumps({"workload": "dense_small", **cfg_dense_small(args.steps)}), flush=True)
         return
     if args.impl == "reference":
         run_reference(args)
