@@ -658,7 +658,8 @@ def run_laplacian2d(args):
     plan = P.Plan(degree=DEGREE)
     out = {"workload": f"2D Laplacian 100 (1,-2,1) along x and y, {d} x {d} grid, {NRHS} RHS, degree {DEGREE}"}
     Ys = {}
-    for name, prec, kw in (("fp64", P.EXPM_FP64, {}), ("mixed", P.EXPM_MIXED_FP32, MIXED_OPTS)):
+    for name, prec, kw in (("fp64", P.EXPM_FP64, {}), ("mixed", P.EXPM_MIXED_FP32, MIXED_OPTS),
+                           ("mixed_f32x2", P.EXPM_MIXED_F32X2, {})):
         Y = torch.empty_like(V)
         P.expm_apply_laplacian2d(plan, d, d, 100.0, -200.0, 100.0, -200.0, V, Y, prec=prec, **kw)
         P.expm_profile_enable(plan, True)
@@ -671,6 +672,14 @@ def run_laplacian2d(args):
         out[name] = {"ms_per_eval": round(med * 1e3, 4), "evals_per_s": round(1 / med, 2),
                      "kernels_ms": {k: round(v[1] / v[0], 4) for k, v in prof.items()}}
     out["mixed_vs_fp64_rel"] = float((Ys["mixed"] - Ys["fp64"]).norm() / Ys["fp64"].norm())
+    from oracle import matrix, scalar
+    ref = matrix.laplacian2d_apply(d, d, 100.0, -200.0, 100.0, -200.0, V.cpu().numpy(),
+                                   lambda m: scalar.R_n(m, DEGREE))
+    for name in Ys:
+        out[name]["rel_err_vs_closed_form"] = matrix.rel_err(Ys[name].cpu().numpy(), ref)
+    out["tolerance"] = {"fp64": 1e-12, "mixed": 1e-8, "mixed_f32x2": 1e-8}
+    out["transforms"] = ("fp64: binary64 products with S; mixed, mixed_f32x2: binary64-accurate slice products "
+                         "on the bf16 tensor cores")
     print(json.dumps(out), flush=True)
 
 

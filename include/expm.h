@@ -311,12 +311,17 @@ expm_status expm_apply_dense_reduced(expm_plan plan, int n, const void *A, int l
  * unknown (ix, iy) at row iy * dx + ix.  T_y is diagonalised by the orthonormal DST-I S,
  * so A = (S (x) I)[(+)_j (T_x + mu_j I)](S (x) I) with mu_j = by + 2 ay cos((j+1) pi/(dy+1)),
  * and (Remark 3.1) Y = (S (x) I) e^c R_n(tB - cI) (S (x) I) V with B block-diagonal
- * tridiagonal: the pole-batched tridiagonal path on dx * dy rows between two binary64
- * products with S along y.
+ * tridiagonal: the pole-batched tridiagonal path on dx * dy rows between two products
+ * with S along y.  With EXPM_FP64 the products are binary64; with the mixed precisions
+ * (and an even number dx r (1 + v_is_complex) of real columns) they are the
+ * binary64-accurate slice products on the bf16 tensor cores used by the dense
+ * refinement (error a few 2^-48 of the row and column scales).
  *   V, Y          device memory, (dx dy) x r row-major, real or complex (v_is_complex);
  *                 1 <= r <= 512, dx * dy <= 2^28
  *   opts, info    as expm_apply_tridiag (its precisions select the tridiagonal solves)
- * Asynchronous on opts->stream (except an EXPM_MIXED_FP32 report, as there).
+ * Returns EXPM_ETIMEOUT if a bounded wait inside a tensor-core product gave up (Y is then
+ * not valid).  Asynchronous on opts->stream with EXPM_FP64; with the tensor-core products
+ * the call synchronises the stream once at the end to read their status.
  */
 expm_status expm_apply_laplacian2d(expm_plan plan, int dx, int dy, double ax, double bx, double ay, double by,
                                    const void *V, int r, int v_is_complex, void *Y, const expm_opts *opts,

@@ -9,10 +9,15 @@
 //     W = (S (x) I) V,   Z = e^c R_n(tB - cI) W,   Y = (S (x) I) Z,
 // with B = (+)_j (T_x + mu_j I) one real symmetric tridiagonal matrix of dx * dy rows whose
 // off-diagonal is zero between the blocks -- the pole-batched tridiagonal path as it is.
-// The transform along y is a dense product with S (binary64, dy x dy times dy x (dx r)).
+// The transform along y is a dense product with S (dy x dy times dy x (dx r)): in binary64
+// for EXPM_FP64; for the mixed precisions the binary64-accurate slice product on the bf16
+// tensor cores of oz_gemm.cu (S as the "matrix", V viewed as dy x (dx r / 2) complex
+// columns of one system, R = 0 - (-1) S V), whose error is a few 2^-48 of the row and
+// column scales -- far below those paths' tolerances.
 #include <cmath>
 
 #include "../../include/expm.h"
+#include "oz_gemm.cuh"
 #include "plan.cuh"
 
 namespace expm {
@@ -116,22 +121,46 @@ extern "C" expm_status expm_apply_laplacian2d(expm_plan p, int dx, int dy, doubl
     cudaStream_t st = (cudaStream_t)opts.stream;
     const int64_t N = (int64_t)dx * dy;
     const int64_t ncols = (int64_t)dx * r * (v_is_complex ? 2 : 1);  // real columns of V viewed as dy x ncols
+    // the tensor-core transform: mixed precisions, an even number of real columns (pairs
+    // viewed as complex), within the slice product's limits
+    const int64_t kc = ncols / 2;
+    const bool tc = opts.prec != EXPM_FP64 && ncols % 2 == 0 && kc <= (1 << 29) && oz_resid_supported(dy, (int)kc, 1);
     auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
     const size_t oS = 0, oD = oS + al((size_t)dy * dy * 8), oE = oD + al((size_t)N * 8), oW = oE + al((size_t)N * 8),
-                 oZ = oW + al((size_t)dy * ncols * 8), total = oZ + al((size_t)dy * ncols * 8);
+                 oZ = oW + al((size_t)dy * ncols * 8), oT = oZ + al((size_t)dy * ncols * 8),
+                 total = oT + (tc ? al(oz_resid_bytes(dy, (int)kc, 1, 0)) : 0);
     expm_status s = plan_reserve(p, &p->stage, &p->stage_bytes, total);
     if (s != EXPM_OK) return s;
     unsigned char *b = (unsigned char *)p->stage;
     double *S = (double *)(b + oS), *d = (double *)(b + oD), *e = (double *)(b + oE), *W = (double *)(b + oW),
            *Z = (double *)(b + oZ);
+    void *ws = b + oT;
     dst_matrix<<<dy, 256, 0, st>>>(dy, S);
     blocks_tridiag<<<(unsigned)std::min<int64_t>((N + 255) / 256, 152 * 8), 256, 0, st>>>(dx, dy, ax, bx, ay, by, d, e);
     cudaError_t err = cudaGetLastError();
-    if (err == cudaSuccess) err = apply_s(dy, ncols, S, (const double *)V, W, st, p->prof);  // W = (S x I) V
+    if (err == cudaSuccess && tc) err = oz_split_a(dy, S, dy, 0, ws, st);  // slices of S, used by both transforms
+    // C = (S x I) B
+    auto transform = [&](const double *B, double *C) -> cudaError_t {
+        if (!tc) return apply_s(dy, ncols, S, B, C, st, p->prof);
+        return p->prof.timed("dst_y<tc>", st, [&] {
+            const int64_t nk = (int64_t)dy * kc;
+            cudaError_t x = cudaMemsetAsync(C, 0, (size_t)dy * ncols * 8, st);
+            if (x == cudaSuccess) x = oz_split_x(dy, (int)kc, 1, 0, (const cx<double> *)B, nk, ws, st);
+            if (x == cudaSuccess) x = oz_product(dy, (int)kc, 1, 0, -1.0, nk, (cx<double> *)C, ws, st, nullptr);
+            return x;
+        });
+    };
+    if (err == cudaSuccess) err = transform((const double *)V, W);  // W = (S x I) V
     if (err != cudaSuccess) return cuda_error(err, "apply_laplacian2d: transform");
     s = expm_apply_tridiag(p, N, d, e, 0, W, r, v_is_complex, Z, &opts, info);
     if (s != EXPM_OK && s != EXPM_ENOCONV) return s;
-    err = apply_s(dy, ncols, S, Z, (double *)Y, st, p->prof);  // Y = (S x I) Z
+    err = transform(Z, (double *)Y);  // Y = (S x I) Z
     if (err != cudaSuccess) return cuda_error(err, "apply_laplacian2d: transform back");
+    if (tc) {  // a bounded wait of the tensor-core product that gave up (one synchronisation)
+        int to = 0;
+        err = oz_read_timeout(dy, (int)kc, 1, 0, ws, st, &to);
+        if (err != cudaSuccess) return cuda_error(err, "apply_laplacian2d: transform status");
+        if (to) return set_error(EXPM_ETIMEOUT, "apply_laplacian2d: tensor-core transform wait gave up");
+    }
     return s;
 }

@@ -1,5 +1,6 @@
 """GPU parity of expm_apply_laplacian2d (separable 2D finite-difference Laplacian, Sec. 5):
-DST-I along y as a binary64 product, the pole-batched tridiagonal path on the
+DST-I along y as a product with S (binary64, or the binary64-accurate tensor-core slice
+product in the mixed precisions), the pole-batched tridiagonal path on the
 block-diagonal operator along x, DST-I back.  Against the oracle: per-pole dense solves on
 the assembled matrix (small grids) and the 2D DST-I closed form (large grids).
 Tolerances: 1e-12 (binary64 solves), 1e-8 (binary32 + refinement)."""
@@ -49,6 +50,29 @@ def test_small_grids_match_dense_oracle(plans, dx, dy, r, complex_v):
     A = matrix.laplacian2d_matrix(dx, dy, AX, BX, AY, BY)
     Yo, _ = matrix.apply_dense(A, V, coeffs.theta(12), coeffs.residues(12))
     assert np.linalg.norm(Y - Yo) <= 1e-12 * np.linalg.norm(Yo) + _floor(V, 12), matrix.rel_err(Y, Yo)
+
+
+@pytest.mark.parametrize("dx,dy,r,complex_v", [(7, 5, 2, False), (13, 9, 3, True), (9, 7, 1, False), (1, 1, 2, False)])
+def test_small_grids_tensor_core_transform(plans, dx, dy, r, complex_v):
+    """The mixed precisions take the sine transforms through the binary64-accurate slice
+    product on the tensor cores (an odd number of real columns falls back to the binary64
+    product): float-float solves, against the dense oracle at 1e-11."""
+    g = workloads.rng(970 + dx + dy)
+    V = g.standard_normal((dx * dy, r)) + (1j * g.standard_normal((dx * dy, r)) if complex_v else 0.0)
+    Y, _ = _run(plans[12], dx, dy, V, prec=P.EXPM_MIXED_F32X2)
+    A = matrix.laplacian2d_matrix(dx, dy, AX, BX, AY, BY)
+    Yo, _ = matrix.apply_dense(A, V, coeffs.theta(12), coeffs.residues(12))
+    assert np.linalg.norm(Y - Yo) <= 1e-11 * np.linalg.norm(Yo) + _floor(V, 12, 2.0 ** -46), matrix.rel_err(Y, Yo)
+
+
+@pytest.mark.parametrize("dx,dy,r", [(100, 200, 3), (257, 130, 2)])
+def test_medium_grids_tensor_core_transform(plans, dx, dy, r):
+    """Ragged tiles of the slice product (dy not a multiple of 128, dx r not of 96)."""
+    g = workloads.rng(980 + dx)
+    V = g.standard_normal((dx * dy, r))
+    Y, _ = _run(plans[16], dx, dy, V, prec=P.EXPM_MIXED_F32X2)
+    ref = matrix.laplacian2d_apply(dx, dy, AX, BX, AY, BY, V, lambda m: scalar.R_n(m, 16))
+    assert np.linalg.norm(Y - ref) <= 1e-11 * np.linalg.norm(ref) + _floor(V, 16, 2.0 ** -46), matrix.rel_err(Y, ref)
 
 
 @pytest.mark.parametrize("dx,dy", [(100, 80), (257, 130)])
