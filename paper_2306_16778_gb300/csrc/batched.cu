@@ -291,6 +291,10 @@ std::vector<GraphChunk> plan_chunks(const BatchSpec &b, int scheme) {
 struct expm_batch_graph_s {
     int device = 0;
     int scheme = 0;
+    // one instance small enough for the one-launch kernel (dense_small.cu): the graph is
+    // that launch on the caller's buffers, its status block at the start of mem
+    bool small = false;
+    expm::DenseGeom sg{};
     double ms_per_scheme[3] = {-1.0, -1.0, -1.0};
     expm::BatchSpec spec{};
     std::vector<expm::GraphChunk> chunks;
@@ -311,6 +315,18 @@ cudaError_t enqueue_batched(expm_batch_graph_s *G, cudaStream_t st) {
     Profiler off;
     const BatchSpec &b = G->spec;
     unsigned char *m = (unsigned char *)G->mem;
+    if (G->small) {
+        DenseIO io{};
+        io.A = (const double *)b.A[0];
+        io.lda = G->sg.n;
+        io.V = (const double *)b.V[0];
+        io.ldv = G->sg.kc;
+        io.v_cplx = b.v_cplx;
+        io.Y = (double *)b.Y[0];
+        io.ldy = G->sg.kc;
+        io.y_real = b.yw == 1 ? 1 : 0;
+        return dense_small_launch(G->sg, io, b.sys, (double *)m, st, off);
+    }
     for (const GraphChunk &c : G->chunks) {
         const int nb = c.nb, kb = c.kb, ni = c.g.ninst;
         const size_t bytesA = sizeof(double) * (size_t)ni * nb * nb * b.aw;
@@ -355,14 +371,21 @@ void destroy_graph(expm_batch_graph_s *G) {
     delete G;
 }
 
-// Builds, warms up and captures the graph for one bucket scheme.
-expm_status build_graph(const BatchSpec &b, int scheme, int device, expm_batch_graph_s **out) {
+// Builds, warms up and captures the graph for one bucket scheme (or, with `small`, the
+// one-launch kernel for the single instance of geometry sg).
+expm_status build_graph(const BatchSpec &b, int scheme, int device, expm_batch_graph_s **out,
+                        const DenseGeom *sg = nullptr) {
     auto G = new expm_batch_graph_s();
     G->device = device;
     G->scheme = scheme;
     G->spec = b;
-    G->chunks = plan_chunks(b, scheme);
-    size_t work = 0, stage = 0, ptrs = 0, res = 0;
+    if (sg) {
+        G->small = true;
+        G->sg = *sg;
+    } else {
+        G->chunks = plan_chunks(b, scheme);
+    }
+    size_t work = 0, stage = 0, ptrs = 0, res = G->small ? 256 : 0;
     for (GraphChunk &c : G->chunks) {
         const int ni = c.g.ninst;
         work = std::max(work, dense_workspace_bytes(c.g));
@@ -500,6 +523,26 @@ extern "C" expm_status expm_batched_capture(expm_plan p, int count, const int *n
     }
     // the pointer arrays are read again at capture time only: keep nothing of the caller's
     // host arrays (the graph captured their values)
+    if (count == 1) {  // one small instance: the graph is the one-launch kernel
+        DenseGeom g{};
+        g.n = n[0];
+        g.kc = k[0];
+        g.ninst = 1;
+        g.complex_a = complex_a;
+        g.npairs = b.S;
+        g.nsys = b.nsys;
+        g.mixed = opts.prec != EXPM_FP64;
+        g.t = opts.t;
+        g.tol = opts.tol;
+        g.max_refine = opts.max_refine;
+        if (dense_small_fits(g)) {
+            expm_batch_graph_s *G = nullptr;
+            expm_status s = build_graph(b, 0, p->device, &G, &g);
+            if (s != EXPM_OK) return s;
+            *out = G;
+            return EXPM_OK;
+        }
+    }
     if (scheme >= 0) {
         expm_batch_graph_s *G = nullptr;
         expm_status s = build_graph(b, scheme, p->device, &G);
@@ -549,6 +592,13 @@ extern "C" expm_status expm_batched_replay(expm_batch_graph G, void *stream, exp
     if (err != cudaSuccess) return cuda_error(err, "batched_replay: results");
     const expm_opts &o = G->spec.opts;
     expm_status worst = EXPM_OK;
+    if (G->small) {  // growth, residual, sweeps of the one-launch kernel
+        double r3[3];
+        std::memcpy(r3, h.data(), sizeof(r3));
+        if (r3[0] > o.growth_max) worst = EXPM_EGROWTH;
+        else if (G->sg.mixed && !(r3[1] <= o.tol)) worst = EXPM_ENOCONV;
+        per_instance[0] = expm_info{(int)r3[2], r3[0], r3[1], worst};
+    }
     for (const GraphChunk &c : G->chunks) {
         const unsigned char *r = h.data() + (c.res_off - G->res_base);
         int iters;
@@ -572,7 +622,7 @@ extern "C" expm_status expm_batched_graph_info(expm_batch_graph G, int *scheme, 
                                                size_t *device_bytes, double ms_per_scheme[3]) {
     if (!G) return set_error(EXPM_EINVAL, "batched_graph_info: NULL graph");
     if (scheme) *scheme = G->scheme;
-    if (launch_groups) *launch_groups = (int)G->chunks.size();
+    if (launch_groups) *launch_groups = G->small ? 1 : (int)G->chunks.size();
     if (device_bytes) *device_bytes = G->mem_bytes;
     if (ms_per_scheme)
         for (int i = 0; i < 3; ++i) ms_per_scheme[i] = G->ms_per_scheme[i];

@@ -88,10 +88,14 @@ bool dense_narrow_fits(int n, int kc);
 // panels (kept in the factor part: factor parts with and without them differ)
 bool dense_uses_inv(const DenseGeom &g);
 // small problems in one cluster launch (dense_small.cu): one instance, n <= 64, kc <= 4,
-// at most 16 solved systems; binary64, or binary32 LU with binary64-residual refinement
-// for every mixed precision.  Synchronises st to read the growth / residual / sweeps.
+// at most 16 solved systems; binary64, or the binary32 inverse with binary64-residual
+// refinement for every mixed precision.  dense_small_launch only enqueues (growth,
+// residual and sweeps land in out[0..2], device memory; usable under stream capture);
+// dense_small_run also synchronises st to read them.
 bool dense_small_fits(const DenseGeom &g);
 size_t dense_small_workspace_bytes();
+cudaError_t dense_small_launch(const DenseGeom &g, const DenseIO &io, const DenseSystems &sys, double *out,
+                               cudaStream_t st, Profiler &prof);
 cudaError_t dense_small_run(const DenseGeom &g, const DenseIO &io, const DenseSystems &sys, void *work,
                             cudaStream_t st, Profiler &prof, DenseResult *res);
 // devctl form: factor + growth + solve fully enqueued on st (nothing read back); results to out

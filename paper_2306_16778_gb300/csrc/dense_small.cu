@@ -21,6 +21,7 @@
 //     the sum is deterministic, writes Y and the worst growth / residual / sweep count.
 #include <cooperative_groups.h>
 
+#include <atomic>
 #include <cmath>
 #include <cstdint>
 
@@ -558,9 +559,15 @@ constexpr size_t DS_SMEM_MIXED = sizeof(cx<float>) * DS_N * DS_LD + sizeof(cx<do
                                  sizeof(cx<double>) * DS_N * DS_K + sizeof(cx<double>) * DS_Q * DS_N * DS_K +
                                  sizeof(cx<float>) * DS_N * DS_K;
 
+// Kernel attributes (dynamic shared memory, cluster size) are per device: set once for
+// each kernel variant and device, so that a launch inside stream capture makes no other
+// API call.
+constexpr int DS_VARIANTS = 5, DS_MAXDEV = 64;
+std::atomic<unsigned char> ds_attr_set[DS_VARIANTS][DS_MAXDEV];
+
 template <class K>
-cudaError_t launch_small(K kernel, size_t smem, const DsArgs &a, const DenseSystems &sys, int nsys, cudaStream_t st,
-                         Profiler &prof, const char *name) {
+cudaError_t launch_small(K kernel, int variant, size_t smem, const DsArgs &a, const DenseSystems &sys, int nsys,
+                         cudaStream_t st, Profiler &prof, const char *name) {
     cudaLaunchConfig_t cfg{};
     cfg.gridDim = dim3((unsigned)nsys);
     cfg.blockDim = dim3(DS_THREADS);
@@ -573,10 +580,15 @@ cudaError_t launch_small(K kernel, size_t smem, const DsArgs &a, const DenseSyst
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    // the attributes apply to the current device: set on every call (the values never change)
-    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= DS_MAXDEV || !ds_attr_set[variant][dev].load(std::memory_order_acquire)) {
+        e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        if (e != cudaSuccess) return e;
+        if (dev >= 0 && dev < DS_MAXDEV) ds_attr_set[variant][dev].store(1, std::memory_order_release);
+    }
     return prof.timed(name, st, [&] { return cudaLaunchKernelEx(&cfg, kernel, a, sys); });
 }
 
@@ -588,8 +600,8 @@ bool dense_small_fits(const DenseGeom &g) {
 
 size_t dense_small_workspace_bytes() { return 256; }
 
-cudaError_t dense_small_run(const DenseGeom &g, const DenseIO &io, const DenseSystems &sys, void *work,
-                            cudaStream_t st, Profiler &prof, DenseResult *res) {
+cudaError_t dense_small_launch(const DenseGeom &g, const DenseIO &io, const DenseSystems &sys, double *out,
+                               cudaStream_t st, Profiler &prof) {
     DsArgs a{};
     a.n = g.n;
     a.kc = g.kc;
@@ -607,18 +619,21 @@ cudaError_t dense_small_run(const DenseGeom &g, const DenseIO &io, const DenseSy
     a.ldv = io.ldv;
     a.Y = io.Y;
     a.ldy = io.ldy;
-    a.out = (double *)work;
-    cudaError_t err;
+    a.out = out;
     if (!g.mixed)
-        err = launch_small(dense_small_f64_kernel, DS_SMEM_F64, a, sys, g.nsys, st, prof, "dense_small<f64>");
-    else if (g.kc == 1)
-        err = launch_small(dense_small_mixed_kernel<1>, DS_SMEM_MIXED, a, sys, g.nsys, st, prof, "dense_small<f32>");
-    else if (g.kc == 2)
-        err = launch_small(dense_small_mixed_kernel<2>, DS_SMEM_MIXED, a, sys, g.nsys, st, prof, "dense_small<f32>");
-    else if (g.kc == 3)
-        err = launch_small(dense_small_mixed_kernel<3>, DS_SMEM_MIXED, a, sys, g.nsys, st, prof, "dense_small<f32>");
-    else
-        err = launch_small(dense_small_mixed_kernel<4>, DS_SMEM_MIXED, a, sys, g.nsys, st, prof, "dense_small<f32>");
+        return launch_small(dense_small_f64_kernel, 0, DS_SMEM_F64, a, sys, g.nsys, st, prof, "dense_small<f64>");
+    if (g.kc == 1)
+        return launch_small(dense_small_mixed_kernel<1>, 1, DS_SMEM_MIXED, a, sys, g.nsys, st, prof, "dense_small<f32>");
+    if (g.kc == 2)
+        return launch_small(dense_small_mixed_kernel<2>, 2, DS_SMEM_MIXED, a, sys, g.nsys, st, prof, "dense_small<f32>");
+    if (g.kc == 3)
+        return launch_small(dense_small_mixed_kernel<3>, 3, DS_SMEM_MIXED, a, sys, g.nsys, st, prof, "dense_small<f32>");
+    return launch_small(dense_small_mixed_kernel<4>, 4, DS_SMEM_MIXED, a, sys, g.nsys, st, prof, "dense_small<f32>");
+}
+
+cudaError_t dense_small_run(const DenseGeom &g, const DenseIO &io, const DenseSystems &sys, void *work,
+                            cudaStream_t st, Profiler &prof, DenseResult *res) {
+    cudaError_t err = dense_small_launch(g, io, sys, (double *)work, st, prof);
     if (err != cudaSuccess) return err;
     double h[3];
     err = cudaMemcpyAsync(h, work, sizeof(h), cudaMemcpyDeviceToHost, st);

@@ -96,3 +96,42 @@ def test_small_statuses(plans):
     assert info.status_worst == 3 and info.growth_max_seen >= 0.5  # EXPM_EGROWTH, Y still written
     Yo, _ = matrix.apply_dense(A, V, coeffs.theta(12), coeffs.residues(12))
     assert matrix.rel_err(Y, Yo) <= 1e-12
+
+
+@pytest.mark.parametrize("prec", [P.EXPM_FP64, P.EXPM_MIXED_FP32])
+@pytest.mark.parametrize("n,k,cplx", [(64, 1, False), (37, 3, True)])
+def test_small_captured_graph(plans, prec, n, k, cplx):
+    """A batch graph of one small instance is the one-launch kernel on the caller's buffers:
+    replays agree with the oracle, report the sweeps and growth, and follow new data in
+    the same buffers."""
+    g = workloads.rng(1280 + n)
+    A, Q, mu, V = workloads.dense_symmetric(n, -20.0, 0.0, k, g, cplx)
+    dA, dV = (torch.from_numpy(x).to(DEV) for x in (A, V))
+    dY = torch.empty_like(dV)
+    gr = P.BatchGraph(plans[12], [dA], [dV], [dY], prec=prec, scheme=-1)
+    assert gr.info()["launch_groups"] == 1
+    for rep in range(2):
+        infos = gr.replay(want_info=True)
+        torch.cuda.synchronize()
+        Yo, _ = matrix.apply_dense(A, V, coeffs.theta(12), coeffs.residues(12))
+        assert matrix.rel_err(dY.cpu().numpy(), Yo) <= TOL[prec]
+        assert infos[0].status_worst == 0 and 0.0 < infos[0].growth_max_seen < 1e3
+        if prec != P.EXPM_FP64:
+            assert infos[0].refine_iters_max >= 1 and infos[0].resid_rel_max <= 1e-14
+        Vr = workloads.rng(1290 + rep).standard_normal(V.shape)
+        V = Vr + 1j * workloads.rng(1295 + rep).standard_normal(V.shape) if cplx else Vr
+        dV.copy_(torch.from_numpy(V))   # the graph reads the same buffer
+    gr.close()
+
+
+def test_small_captured_graph_growth_status(plans):
+    g = workloads.rng(1300)
+    A, Q, mu, V = workloads.dense_symmetric(16, -10.0, 0.0, 1, g, True)
+    dA, dV = (torch.from_numpy(x).to(DEV) for x in (A, V))
+    dY = torch.empty_like(dV)
+    gr = P.BatchGraph(plans[12], [dA], [dV], [dY], prec=P.EXPM_FP64, scheme=0, growth_max=0.5)
+    infos = gr.replay(want_info=True, check=False)
+    assert infos[0].status_worst == 3        # EXPM_EGROWTH, Y still written
+    Yo, _ = matrix.apply_dense(A, V, coeffs.theta(12), coeffs.residues(12))
+    assert matrix.rel_err(dY.cpu().numpy(), Yo) <= 1e-12
+    gr.close()
