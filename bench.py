@@ -748,8 +748,23 @@ def cfg_batched(count=4096, steps=3):
                                                              b.abs().pow(2).sum().sqrt())
                                                        for a, b in zip(Yg, Ys["fp64"]))}
     out["speedup_mixed_graph_vs_fp64"] = round(out["fp64"]["s_per_batch"] / med, 2)
-    out["tolerance"] = {"mixed_vs_closed_form": 1e-8, "fp64_vs_closed_form": 1e-12}
     gr.close()
+    # the same graph with the trailing updates of buckets above order 256 on the tensor cores
+    Yt = [torch.empty_like(v) for v in Vs]
+    gt = P.BatchGraph(plan, As, Vs, Yt, prec=P.EXPM_MIXED_BF16X3, scheme=gi["scheme"])
+    infos = gt.replay(want_info=True, check=False)
+    tt = _time_calls(lambda: gt.replay(), steps, 1)
+    medt = statistics.median(tt)
+    out["mixed_tc_graph"] = {"prec": "EXPM_MIXED_BF16X3 (tensor-core trailing updates for padded orders > 256)",
+                             "scheme": gi["scheme"], "s_per_batch": round(medt, 4),
+                             "instances_per_s": round(count / medt, 2),
+                             "latency_s": {"p50": round(_pcts(tt)[0], 4), "p99": round(_pcts(tt)[1], 4)},
+                             "refine_sweeps_max": max(i.refine_iters_max for i in infos),
+                             "worst_status": max(i.status_worst for i in infos),
+                             "worst_rel_err_vs_eigen_Rn": worst(Yt, Yeig)}
+    out["speedup_mixed_tc_graph_vs_fp64"] = round(out["fp64"]["s_per_batch"] / medt, 2)
+    gt.close()
+    out["tolerance"] = {"mixed_vs_closed_form": 1e-8, "fp64_vs_closed_form": 1e-12}
     plan.close()
     return out
 

@@ -338,7 +338,10 @@ expm_status expm_apply_laplacian2d(expm_plan plan, int dx, int dy, double ax, do
  *   V[i], Y[i]       n[i] x k[i], row-major, leading dimension k[i], device memory;
  *                    V complex iff v_is_complex (complex V needs complex A); Y complex
  *                    iff A or V is complex
- *   opts             as expm_apply_dense (precision, refinement, growth limit, stream)
+ *   opts             as expm_apply_dense (precision, refinement, growth limit, stream);
+ *                    EXPM_MIXED_TF32X3 / EXPM_MIXED_BF16X3 run the LU's trailing updates
+ *                    on the tensor cores for buckets of padded order above 256 (binary32
+ *                    LU on the FP32 pipe below), refined as EXPM_MIXED_FP32
  *   per_instance     optional host array of `count` expm_info, filled per instance
  * Method: instances are grouped by size into buckets and zero-padded to the bucket's
  * order (exact: the padded part of tA - cI + theta I is the diagonal (theta - c) I);
@@ -346,7 +349,8 @@ expm_status expm_apply_laplacian2d(expm_plan plan, int dx, int dy, double ax, do
  * (unpivoted LU, triangular solves, refinement, residue sum).  The call
  * synchronises opts->stream.  Returns EXPM_EGROWTH / EXPM_ENOCONV if any instance
  * failed the growth or refinement test (all Y_i are written; per_instance says
- * which), EXPM_ENOTSUP for complex V with real A.
+ * which), EXPM_ENOTSUP for complex V with real A, EXPM_ETIMEOUT if a bounded wait in a
+ * tensor-core update gave up.
  */
 expm_status expm_apply_batched(expm_plan plan, int count, const int *n, const void *const *A, int a_is_complex,
                                const void *const *V, const int *k, int v_is_complex, void *const *Y,
@@ -376,7 +380,9 @@ expm_status expm_apply_batched(expm_plan plan, int count, const int *n, const vo
  * cannot be allocated, EXPM_ECUDA when the capture fails.
  *   expm_batched_replay      enqueues the graph on stream; with per_instance (host
  *                 array of count entries) the call waits and reports each instance as
- *                 expm_apply_batched does, returning EXPM_EGROWTH / EXPM_ENOCONV likewise.
+ *                 expm_apply_batched does, returning EXPM_EGROWTH / EXPM_ENOCONV /
+ *                 EXPM_ETIMEOUT likewise.  A single instance small enough for the
+ *                 one-launch kernel of expm_apply_dense is captured as that launch.
  *   expm_batched_graph_info  chosen scheme, number of launch groups (bucket chunks),
  *                 device bytes, and the timed ms per scheme (-1 where not timed).
  */

@@ -82,6 +82,18 @@ int bucket_order(int n, int scheme = 0) {
 
 using namespace expm;
 
+// Tensor-core trailing updates (EXPM_MIXED_TF32X3 / EXPM_MIXED_BF16X3) for buckets whose
+// padded order exceeds one outer panel of the tensor-core LU; smaller buckets factor on
+// the FP32 pipe (their updates are too small to fill a 128-row tile per step).
+static int batch_tc(int prec, int nb) {
+    if (nb <= 256) return 0;
+    return prec == EXPM_MIXED_TF32X3 ? 1 : prec == EXPM_MIXED_BF16X3 ? 2 : 0;
+}
+static bool batch_prec_ok(int prec) {
+    return prec == EXPM_FP64 || prec == EXPM_MIXED_FP32 || prec == EXPM_MIXED_F32X2 || prec == EXPM_MIXED_TF32X3 ||
+           prec == EXPM_MIXED_BF16X3;
+}
+
 extern "C" expm_status expm_apply_batched(expm_plan p, int count, const int *n, const void *const *A, int a_is_complex,
                                           const void *const *V, const int *k, int v_is_complex, void *const *Y,
                                           const expm_opts *opts_in, expm_info *per_instance) {
@@ -91,8 +103,7 @@ extern "C" expm_status expm_apply_batched(expm_plan p, int count, const int *n, 
     if (count == 0) return EXPM_OK;
     expm_opts opts;
     if (opts_in) opts = *opts_in; else expm_opts_default(&opts);
-    if (opts.prec != EXPM_FP64 && opts.prec != EXPM_MIXED_FP32 && opts.prec != EXPM_MIXED_F32X2)
-        return set_error(EXPM_EINVAL, "apply_batched: precision must be EXPM_FP64, EXPM_MIXED_FP32 or EXPM_MIXED_F32X2");
+    if (!batch_prec_ok(opts.prec)) return set_error(EXPM_EINVAL, "apply_batched: unknown precision");
     if (opts.flags != 0) return set_error(EXPM_EINVAL, "apply_batched: opts.flags must be 0");
     if (!std::isfinite(opts.t) || !std::isfinite(opts.shift_c) || !(opts.tol > 0) || opts.max_refine < 0)
         return set_error(EXPM_EINVAL, "apply_batched: bad t, shift_c, tol or max_refine");
@@ -150,6 +161,7 @@ extern "C" expm_status expm_apply_batched(expm_plan p, int count, const int *n, 
         g.t = opts.t;
         g.tol = opts.tol;
         g.max_refine = opts.max_refine;
+        g.tc = batch_tc(opts.prec, nb);
         g.ninst = 1;
         const size_t per_inst = dense_workspace_bytes(g) + sizeof(double) * ((size_t)nb * nb * aw + 2 * (size_t)nb * kb * 2);
         size_t chunk = std::max<size_t>(1, ((size_t)8 << 30) / per_inst);
@@ -201,6 +213,7 @@ extern "C" expm_status expm_apply_batched(expm_plan p, int count, const int *n, 
             if ((err = cudaGetLastError()) != cudaSuccess) return cuda_error(err, "apply_batched: scatter");
             // the pointer table and staging buffers are reused by the next chunk
             if ((err = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_error(err, "apply_batched: sync");
+            if (res.tc_timeout) return set_error(EXPM_ETIMEOUT, "apply_batched: a tensor-core wait gave up");
             for (int z = 0; z < g.ninst; ++z) {
                 const int i = order[c0 + z];
                 expm_status si = EXPM_OK;
@@ -266,6 +279,7 @@ std::vector<GraphChunk> plan_chunks(const BatchSpec &b, int scheme) {
         g.t = b.opts.t;
         g.tol = b.opts.tol;
         g.max_refine = b.opts.max_refine;
+        g.tc = batch_tc(b.opts.prec, nb);
         g.devctl = 1;
         g.ninst = 1;
         const size_t per_inst = dense_workspace_bytes(g) + sizeof(double) * ((size_t)nb * nb * b.aw + 2 * (size_t)nb * kb * 2);
@@ -355,6 +369,14 @@ cudaError_t enqueue_batched(expm_batch_graph_s *G, cudaStream_t st) {
         DenseDevOut out{(int *)r, (double *)(r + 256), (double *)(r + 256 + al256(sizeof(double) * ni))};
         err = dense_run_devctl(c.g, io, b.sys, m + G->work_off, st, off, out);
         if (err != cudaSuccess) return err;
+        if (c.g.tc) {  // the tensor-core updates' time-out flag, next to the sweep count
+            err = cudaMemcpyAsync(r + sizeof(int), m + G->work_off + dense_tc_flag_offset(c.g), sizeof(int),
+                                  cudaMemcpyDeviceToDevice, st);
+            if (err != cudaSuccess) return err;
+        } else {
+            err = cudaMemsetAsync(r + sizeof(int), 0, sizeof(int), st);
+            if (err != cudaSuccess) return err;
+        }
         scatter_unpad<<<dim3((unsigned)std::min<int64_t>(((int64_t)nb * kb * b.yw + 255) / 256, 1024), 1, ni), 256, 0,
                         st>>>(dptr, nb, kb, b.yw, Ypad);
         if ((err = cudaGetLastError()) != cudaSuccess) return err;
@@ -476,8 +498,7 @@ extern "C" expm_status expm_batched_capture(expm_plan p, int count, const int *n
     if (scheme < -1 || scheme > 2) return set_error(EXPM_EINVAL, "batched_capture: scheme must be -1 (tune), 0, 1 or 2");
     expm_opts opts;
     if (opts_in) opts = *opts_in; else expm_opts_default(&opts);
-    if (opts.prec != EXPM_FP64 && opts.prec != EXPM_MIXED_FP32 && opts.prec != EXPM_MIXED_F32X2)
-        return set_error(EXPM_EINVAL, "batched_capture: precision must be EXPM_FP64, EXPM_MIXED_FP32 or EXPM_MIXED_F32X2");
+    if (!batch_prec_ok(opts.prec)) return set_error(EXPM_EINVAL, "batched_capture: unknown precision");
     if (opts.flags != 0) return set_error(EXPM_EINVAL, "batched_capture: opts.flags must be 0");
     if (!std::isfinite(opts.t) || !std::isfinite(opts.shift_c) || !(opts.tol > 0) || opts.max_refine < 0 ||
         opts.max_refine > 64)
@@ -601,8 +622,10 @@ extern "C" expm_status expm_batched_replay(expm_batch_graph G, void *stream, exp
     }
     for (const GraphChunk &c : G->chunks) {
         const unsigned char *r = h.data() + (c.res_off - G->res_base);
-        int iters;
+        int iters, tc_timeout;
         std::memcpy(&iters, r, sizeof(int));
+        std::memcpy(&tc_timeout, r + sizeof(int), sizeof(int));
+        if (tc_timeout) return set_error(EXPM_ETIMEOUT, "batched_replay: a tensor-core wait gave up");
         const double *resid = (const double *)(r + 256);
         const double *growth = (const double *)(r + 256 + al256(sizeof(double) * c.g.ninst));
         for (int z = 0; z < c.g.ninst; ++z) {

@@ -1270,6 +1270,8 @@ static cudaError_t dense_solve_devctl(const DenseGeom &g, const DenseIO &io, con
     });
 }
 
+size_t dense_tc_flag_offset(const DenseGeom &g) { return dense_layout(g).tcflag; }
+
 cudaError_t dense_run_devctl(const DenseGeom &g, const DenseIO &io, const DenseSystems &sys, void *work,
                              cudaStream_t st, Profiler &prof, const DenseDevOut &out) {
     const DenseLayout L = dense_layout(g);

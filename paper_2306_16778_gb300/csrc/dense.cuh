@@ -98,6 +98,8 @@ cudaError_t dense_small_launch(const DenseGeom &g, const DenseIO &io, const Dens
                                cudaStream_t st, Profiler &prof);
 cudaError_t dense_small_run(const DenseGeom &g, const DenseIO &io, const DenseSystems &sys, void *work,
                             cudaStream_t st, Profiler &prof, DenseResult *res);
+// offset in the workspace of the tensor-core updates' time-out flag (an int; g.tc != 0)
+size_t dense_tc_flag_offset(const DenseGeom &g);
 // devctl form: factor + growth + solve fully enqueued on st (nothing read back); results to out
 cudaError_t dense_run_devctl(const DenseGeom &g, const DenseIO &io, const DenseSystems &sys, void *work,
                              cudaStream_t st, Profiler &prof, const DenseDevOut &out);

@@ -150,3 +150,28 @@ def test_graph_rejections():
     with pytest.raises(P.ExpmError) as ei:                      # unknown scheme
         P.BatchGraph(plan, [A], [V], [torch.empty_like(V)], scheme=3)
     assert ei.value.status == 1
+
+
+@pytest.mark.parametrize("prec", [P.EXPM_MIXED_TF32X3, P.EXPM_MIXED_BF16X3])
+def test_tensor_core_buckets(prec):
+    """Buckets of padded order above 256 take the LU's trailing updates to the tensor cores
+    (the smaller ones stay on the FP32 pipe), through the direct call and the captured
+    graph: every instance within the mixed tolerance of the oracle, all statuses clean."""
+    inst, As, Vs = _batch(520, 6, 200, 700, kmax=2)
+    sizes = [A.shape[0] for A, _, _, _ in inst]
+    assert any(n > 256 for n in sizes) and any(n <= 256 for n in sizes)
+    plan = P.Plan(degree=12)
+    th, a = coeffs.theta(12), coeffs.residues(12)
+    Ya = [torch.empty_like(v) for v in Vs]
+    ia = P.expm_apply_batched(plan, As, Vs, Ya, prec=prec)
+    assert all(i.status_worst == 0 for i in ia)
+    Yg = [torch.empty_like(v) for v in Vs]
+    gr = P.BatchGraph(plan, As, Vs, Yg, prec=prec, scheme=0)
+    ig = gr.replay(want_info=True)
+    torch.cuda.synchronize()
+    assert all(i.status_worst == 0 for i in ig)
+    for (A, _, _, V), y1, y2 in zip(inst, Ya, Yg):
+        Yo, _ = matrix.apply_dense(A, V, th, a)
+        assert _close(y1.cpu().numpy(), Yo, V, 12, 1e-8)
+        assert _close(y2.cpu().numpy(), Yo, V, 12, 1e-8)
+    gr.close()
