@@ -22,10 +22,15 @@
 // pipe's rate).  The batch entry is the third coordinate of both tensor maps (grid z).
 // Every mbarrier wait is bounded: on time-out the kernel records an error flag, stops
 // issuing work, drains what it issued, frees its tensor memory and returns.
+// That one-tile-per-CTA kernel runs its epilogue after the K loop, with the tensor pipe
+// idle; the default launch is the persistent form further down (two accumulators, the
+// epilogue of one tile under the MMAs of the next).
 #include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 
@@ -239,6 +244,233 @@ __global__ void __launch_bounds__(128, 1)
     }
 }
 
+// ---------------------------------------------------------------------------------------
+// Persistent form: one CTA per SM walks the tiles t = blockIdx.x, + gridDim.x, ... (N tile
+// fastest, then M, then the batch entry) with two 128 x 256 accumulators in tensor memory
+// (all 512 columns), so that the epilogue of one tile runs while the MMAs of the next one
+// fill the other accumulator.  Warp roles (192 threads):
+//   warp 0      TMA producer: the K ring, continuous across tiles (stage = global k-block
+//               counter mod TC_STAGES)
+//   warp 1      MMA issuer: waits until the epilogue has released the tile's accumulator
+//               (acc_empty), issues the tile's MMAs, commits acc_full
+//   warps 2-5   epilogue: warp w reads TMEM lanes 32 (w % 4) .. (rows of the tile), per
+//               32-column chunk tcgen05.ld, a transpose through its own shared-memory
+//               buffer and C -= chunk with coalesced row segments; then arrives on
+//               acc_empty.  Before waiting for a tile they pull its C rows into L2.
+// Every wait is bounded; on time-out the kernel raises the abort flag, every role leaves
+// its loop, the MMA thread's last commit (drain) is awaited before the accumulators are
+// freed, and copies issued but not consumed are awaited before the CTA exits.
+constexpr int TCP_THREADS = 192;
+constexpr int TCP_EPI_BYTES = 4 * 32 * 33 * 4;  // per epilogue warp a 32 x 33 fp32 transpose buffer
+constexpr int TCP_SMEM = TC_STAGES * (TC_A_BYTES + TC_B_BYTES) + TCP_EPI_BYTES + 1024 + 256;
+
+template <bool BF16>
+__global__ void __launch_bounds__(TCP_THREADS, 1)
+    tc_gemm_persistent(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, int M, int N,
+                       int K, int batch, float *__restrict__ C, int ldc, int64_t cstride, int *__restrict__ err_flag) {
+    constexpr int TC_BK = BF16 ? 64 : 32;
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char *base = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    unsigned char *sA = base;
+    unsigned char *sB = base + TC_STAGES * TC_A_BYTES;
+    float *epi = reinterpret_cast<float *>(sB + TC_STAGES * TC_B_BYTES);
+    uint64_t *full = reinterpret_cast<uint64_t *>(reinterpret_cast<unsigned char *>(epi) + TCP_EPI_BYTES);
+    uint64_t *empty = full + TC_STAGES;
+    uint64_t *acc_full = empty + TC_STAGES;   // [2]
+    uint64_t *acc_empty = acc_full + 2;       // [2]
+    uint64_t *drain = acc_empty + 2;
+    uint32_t *tmem_slot = (uint32_t *)(drain + 1);
+    __shared__ int abort_flag;
+    __shared__ long long consumed, produced;  // global k-blocks taken by the MMA issuer / issued by TMA
+
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    const int nk = (K + TC_BK - 1) / TC_BK;
+    const int tn = (N + TC_BN - 1) / TC_BN, tm = (M + TC_BM - 1) / TC_BM;
+    const long long ntiles = (long long)tn * tm * batch;
+    auto decode = [&](long long t, int &m0, int &n0, int &bz) {
+        bz = (int)(t / ((long long)tn * tm));
+        const int r = (int)(t % ((long long)tn * tm));
+        m0 = (r / tn) * TC_BM;
+        n0 = (r % tn) * TC_BN;
+    };
+
+    if (threadIdx.x == 0) {
+        abort_flag = 0;
+        consumed = 0;
+        produced = 0;
+        for (int st = 0; st < TC_STAGES; ++st) {
+            mbar_init(&full[st], 1);
+            mbar_init(&empty[st], 1);
+        }
+        for (int a = 0; a < 2; ++a) {
+            mbar_init(&acc_full[a], 1);
+            mbar_init(&acc_empty[a], 4);  // the four epilogue warps
+        }
+        mbar_init(drain, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {  // both accumulators: 512 TMEM columns (one CTA per SM)
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(smem_u32(tmem_slot))
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            long long g = 0;
+            for (long long t = blockIdx.x; t < ntiles && !*(volatile int *)&abort_flag; t += gridDim.x) {
+                int m0, n0, bz;
+                decode(t, m0, n0, bz);
+                for (int kb = 0; kb < nk; ++kb, ++g) {
+                    const int st = (int)(g % TC_STAGES);
+                    const uint32_t ph = (uint32_t)(g / TC_STAGES) & 1u;
+                    if (!mbar_wait(&empty[st], ph ^ 1u) || *(volatile int *)&abort_flag) {
+                        atomicExch(&abort_flag, 1);
+                        break;
+                    }
+                    mbar_expect_tx(&full[st], TC_A_BYTES + TC_B_BYTES);
+                    tma_load_3d(&mapA, &full[st], sA + st * TC_A_BYTES, kb * TC_BK, m0, bz);
+                    tma_load_3d(&mapB, &full[st], sB + st * TC_B_BYTES, kb * TC_BK, n0, bz);
+                    produced = g + 1;
+                }
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            constexpr uint32_t idesc = idesc_tc(BF16, TC_BM, TC_BN);
+            long long g = 0;
+            int i = 0;
+            for (long long t = blockIdx.x; t < ntiles && !*(volatile int *)&abort_flag; t += gridDim.x, ++i) {
+                const int a = i & 1;
+                // the epilogue has read this accumulator's previous tile (first use: passes)
+                if (!mbar_wait(&acc_empty[a], (uint32_t)((i >> 1) & 1) ^ 1u)) {
+                    atomicExch(&abort_flag, 1);
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t dst = tmem + (uint32_t)(a * TC_BN);
+                bool ok = true;
+                for (int kb = 0; kb < nk; ++kb, ++g) {
+                    const int st = (int)(g % TC_STAGES);
+                    const uint32_t ph = (uint32_t)(g / TC_STAGES) & 1u;
+                    if (!mbar_wait(&full[st], ph) || *(volatile int *)&abort_flag) {
+                        atomicExch(&abort_flag, 1);
+                        ok = false;
+                        break;
+                    }
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    const uint32_t a0 = smem_u32(sA + st * TC_A_BYTES), b0 = smem_u32(sB + st * TC_B_BYTES);
+#pragma unroll
+                    for (int kk = 0; kk < 4; ++kk) {
+                        const uint64_t ad = smem_desc_sw128(a0 + kk * 32), bd = smem_desc_sw128(b0 + kk * 32);
+                        const uint32_t accu = (kb > 0 || kk > 0) ? 1u : 0u;
+                        if (BF16)
+                            asm volatile(
+                                "{\n\t.reg .pred p;\n\t"
+                                "setp.ne.u32 p, %4, 0;\n\t"
+                                "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(dst),
+                                "l"(ad), "l"(bd), "r"(idesc), "r"(accu)
+                                : "memory");
+                        else
+                            asm volatile(
+                                "{\n\t.reg .pred p;\n\t"
+                                "setp.ne.u32 p, %4, 0;\n\t"
+                                "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(dst),
+                                "l"(ad), "l"(bd), "r"(idesc), "r"(accu)
+                                : "memory");
+                    }
+                    tcu::mma_commit(&empty[st]);  // the stage is free once these MMAs have read it
+                    consumed = g + 1;
+                }
+                if (!ok) break;
+                tcu::mma_commit(&acc_full[a]);  // the tile's accumulator is complete
+            }
+            tcu::mma_commit(drain);  // everything issued has completed
+        }
+    } else {
+        // epilogue warps 2..5: TMEM lane quadrant q = warp % 4 = tile rows 32 q .. 32 q + 31
+        const int q = warp & 3;
+        float *stage = epi + (warp - 2) * 32 * 33;
+        const uint32_t lane_base = (uint32_t)(q * 32) << 16;
+        int i = 0;
+        for (long long t = blockIdx.x; t < ntiles; t += gridDim.x, ++i) {
+            int m0, n0, bz;
+            decode(t, m0, n0, bz);
+            float *Cb = C + (int64_t)bz * cstride;
+            // this warp's 32 rows of the C tile (1 KB each) into L2 while the MMAs run
+            for (int e = lane; e < 32 * (TC_BN * 4 / 128); e += 32) {
+                const int row = m0 + q * 32 + e / (TC_BN * 4 / 128), col = n0 + (e % (TC_BN * 4 / 128)) * 32;
+                if (row < M && col < N) asm volatile("prefetch.global.L2 [%0];" ::"l"(Cb + (int64_t)row * ldc + col));
+            }
+            const int a = i & 1;
+            if (!mbar_wait(&acc_full[a], (uint32_t)((i >> 1) & 1)) || *(volatile int *)&abort_flag) {
+                atomicExch(&abort_flag, 1);
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll 1
+            for (int c0 = 0; c0 < TC_BN; c0 += 32) {
+                uint32_t v[32];
+                asm volatile(
+                    "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, "
+                    "%13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, "
+                    "[%32];"
+                    : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+                      "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
+                      "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]),
+                      "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]),
+                      "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+                    : "r"(tmem + lane_base + (uint32_t)(a * TC_BN + c0)));
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                if (c0 + 32 >= TC_BN) {  // the accumulator is read: release it to the MMA issuer
+                    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                    __syncwarp();
+                    if (lane == 0) tcu::mbar_arrive(&acc_empty[a]);
+                }
+#pragma unroll
+                for (int j = 0; j < 32; ++j) stage[lane * 33 + j] = __uint_as_float(v[j]);
+                __syncwarp();
+                const int col = n0 + c0 + lane;
+                float cv[32];
+#pragma unroll
+                for (int r = 0; r < 32; ++r) {
+                    const int row = m0 + q * 32 + r;
+                    cv[r] = (row < M && col < N) ? Cb[(int64_t)row * ldc + col] : 0.f;
+                }
+#pragma unroll
+                for (int r = 0; r < 32; ++r) {
+                    const int row = m0 + q * 32 + r;
+                    if (row < M && col < N) Cb[(int64_t)row * ldc + col] = cv[r] - stage[r * 33 + lane];
+                }
+                __syncwarp();
+            }
+        }
+    }
+    __syncwarp();
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    const int aborted = *(volatile int *)&abort_flag;
+    if (threadIdx.x == 0) {
+        // every MMA issued has completed before the accumulators are freed
+        const bool drained = mbar_wait(drain, 0u);
+        if (aborted || !drained) {
+            atomicExch(err_flag, 1);
+            // copies issued but not consumed must land before this CTA's shared memory goes
+            for (long long g = consumed; g < produced; ++g)
+                mbar_wait(&full[g % TC_STAGES], (uint32_t)(g / TC_STAGES) & 1u);
+        }
+    }
+    __syncthreads();
+    if (warp == 1) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem) : "memory");
+    }
+}
+
 using tcu::EncodeFn;
 using tcu::encode_fn;
 
@@ -259,6 +491,16 @@ bool make_map(CUtensorMap *map, const void *ptr, int rows, int cols, int ld, int
                CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// The persistent two-accumulator kernel is the default; EXPM_TC_PERSISTENT=0 in the
+// environment selects the one-tile-per-CTA kernel (kept for comparison).
+static bool tc_persistent_enabled() {
+    static const bool on = [] {
+        const char *v = std::getenv("EXPM_TC_PERSISTENT");
+        return !(v && v[0] == '0');
+    }();
+    return on;
+}
+
 template <bool BF16>
 cudaError_t tc_gemm_sub(int M, int N, int K, const void *A, int lda, int64_t sA, const void *B, int ldb, int64_t sB,
                         float *C, int ldc, int64_t sC, int batch, int *err_flag, cudaStream_t st) {
@@ -275,8 +517,20 @@ cudaError_t tc_gemm_sub(int M, int N, int K, const void *A, int lda, int64_t sA,
     static cudaError_t attr = cudaSuccess;
     std::call_once(once, [] {
         attr = cudaFuncSetAttribute(tc_gemm_kernel<BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
+        if (attr == cudaSuccess)
+            attr = cudaFuncSetAttribute(tc_gemm_persistent<BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, TCP_SMEM);
     });
     if (attr != cudaSuccess) return attr;
+    const long long ntiles = (long long)((N + TC_BN - 1) / TC_BN) * ((M + TC_BM - 1) / TC_BM) * batch;
+    if (tc_persistent_enabled()) {
+        int dev = 0, sms = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) return e;
+        const unsigned grid = (unsigned)std::min<long long>(ntiles, sms);
+        tc_gemm_persistent<BF16><<<grid, TCP_THREADS, TCP_SMEM, st>>>(ma, mb, M, N, K, batch, C, ldc, sC, err_flag);
+        return cudaGetLastError();
+    }
     dim3 grid((N + TC_BN - 1) / TC_BN, (M + TC_BM - 1) / TC_BM, batch);
     tc_gemm_kernel<BF16><<<grid, 128, TC_SMEM, st>>>(ma, mb, M, N, K, C, ldc, sC, err_flag);
     return cudaGetLastError();
