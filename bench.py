@@ -626,7 +626,7 @@ def cfg_dense(n=4096, steps=2, reduced=False):
     if "tc_gemm_bf16x3" in prof:
         fl = sum(2.0 * 8 * r * (2 * r) * (12 * 256) for r in range(n - 256, 0, -256))
         tf = fl / (prof["tc_gemm_bf16x3"] * 1e-3) / 1e12
-        out["roofline_tc_lu"] = {"kernel": "tc_gemm_kernel<bf16>", "bound": "tensor", "achieved": round(tf, 1),
+        out["roofline_tc_lu"] = {"kernel": "tc_gemm_persistent<bf16>", "bound": "tensor", "achieved": round(tf, 1),
                                  "peak": sustained, "unit": "TFLOP/s", "frac": round(tf / sustained, 4),
                                  "peak_source": f"{src} bf16 sustained",
                                  "algorithmic": "sum over panels of 8 pairs x 2 x right x 2 right x 12 x 256"}
