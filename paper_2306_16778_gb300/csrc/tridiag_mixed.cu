@@ -65,9 +65,15 @@ namespace {
 constexpr int MX_CTA = 128;
 constexpr int MX_CK = 8;            // rows per forward-recurrence checkpoint
 constexpr int MX_PMAX = 6144;       // blocks: the binary32 reduced system (32 B per separator) in shared memory
-constexpr int MX_THREADS_SM = 384;  // resident (block, column, system) threads per SM (3 CTAs of the solve kernels)
+#ifndef EXPM_MX_CTAS_SM
+#define EXPM_MX_CTAS_SM 3
+#endif
+#ifndef EXPM_MX_SMEM_KB
+#define EXPM_MX_SMEM_KB 72
+#endif
+constexpr int MX_THREADS_SM = 128 * EXPM_MX_CTAS_SM;  // resident (block, column, system) threads per SM
 constexpr int MX_WAVES = EXPM_MX_WAVES;
-constexpr int MX_SMEM_MAX = 72 * 1024;  // shared-memory tile per CTA (3 CTAs of the solve kernels per SM)
+constexpr int MX_SMEM_MAX = EXPM_MX_SMEM_KB * 1024;  // shared-memory tile per CTA of the solve kernels
 
 enum : int { MX_STORE = 1, MX_LO_OUT = 2, MX_FINAL = 4, MX_COMP = 8, MX_LO_IN = 16, MX_RESID = 32 };
 
