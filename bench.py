@@ -741,6 +741,8 @@ def cfg_batched(count=4096, steps=3):
                           "latency_s": {"p50": round(_pcts(ts)[0], 4), "p99": round(_pcts(ts)[1], 4)},
                           "scheme": gi["scheme"], "ms_per_scheme": [round(x, 2) for x in gi["ms_per_scheme"]],
                           "launch_groups": gi["launch_groups"], "capture_and_tune_s": round(cap_s, 2),
+                          "bucket_tiles": [[b_["order"], b_["ninst"], b_["tile"], round(b_["ms_tile"][0], 3),
+                                            round(b_["ms_tile"][1], 3)] for b_ in gr.buckets()],
                           "refine_sweeps_max": max(i.refine_iters_max for i in infos),
                           "worst_status": max(i.status_worst for i in infos),
                           "worst_rel_err_vs_eigen_Rn": worst(Yg, Yeig),

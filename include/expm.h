@@ -372,7 +372,11 @@ expm_status expm_apply_batched(expm_plan plan, int count, const int *n, const vo
  *   scheme        padded orders of the size buckets: 0 (multiples of 32 up to 128, then
  *                 steps of about a quarter; the expm_apply_batched default), 1 (all
  *                 multiples of 32), 2 (powers of two and midpoints), or -1: capture all
- *                 three, time two launches of each and keep the fastest (autotuning)
+ *                 three, time two launches of each and keep the fastest (autotuning);
+ *                 with -1 every bucket factorised on the FP32 pipe (EXPM_MIXED_FP32,
+ *                 and the mixed tensor-core precisions below order 257) first times its
+ *                 factorization with 128 x 64 and 64 x 64 trailing-update tiles and
+ *                 keeps the faster shape
  *   out           the graph; it owns its device memory (workspace, staging copies of
  *                 the padded instances, pointer tables, per-instance results)
  * The call runs the evaluation once outside the capture (so Y holds a result on return)
@@ -385,6 +389,12 @@ expm_status expm_apply_batched(expm_plan plan, int count, const int *n, const vo
  *                 one-launch kernel of expm_apply_dense is captured as that launch.
  *   expm_batched_graph_info  chosen scheme, number of launch groups (bucket chunks),
  *                 device bytes, and the timed ms per scheme (-1 where not timed).
+ *   expm_batched_graph_buckets  per launch group i < max of the chosen graph: padded
+ *                 order[i], instances ninst[i], trailing-update tile[i] (0: 128 x 64,
+ *                 1: 64 x 64) and the timed factorization ms with each (ms_tile0[i],
+ *                 ms_tile1[i]; -1 where not timed).  Any output pointer may be NULL
+ *                 (host arrays of max entries).  Returns the number of launch groups
+ *                 (0 for a captured one-launch small instance), -1 for a NULL graph.
  */
 typedef struct expm_batch_graph_s *expm_batch_graph;
 expm_status expm_batched_capture(expm_plan plan, int count, const int *n, const void *const *A, int a_is_complex,
@@ -393,6 +403,8 @@ expm_status expm_batched_capture(expm_plan plan, int count, const int *n, const 
 expm_status expm_batched_replay(expm_batch_graph graph, void *stream, expm_info *per_instance);
 expm_status expm_batched_graph_info(expm_batch_graph graph, int *scheme, int *launch_groups, size_t *device_bytes,
                                     double ms_per_scheme[3]);
+int expm_batched_graph_buckets(expm_batch_graph graph, int max, int *order, int *ninst, int *tile, double *ms_tile0,
+                              double *ms_tile1);
 expm_status expm_batched_graph_destroy(expm_batch_graph graph);
 
 /*

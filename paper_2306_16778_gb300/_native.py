@@ -98,6 +98,9 @@ def _load() -> ctypes.CDLL:
     L.expm_batched_graph_info.argtypes = [vp, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(ctypes.c_size_t),
                                           ctypes.POINTER(ctypes.c_double)]
     L.expm_batched_graph_info.restype = i
+    ip, dp = ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)
+    L.expm_batched_graph_buckets.argtypes = [vp, i, ip, ip, ip, dp, dp]
+    L.expm_batched_graph_buckets.restype = i
     L.expm_batched_graph_destroy.argtypes = [vp]
     L.expm_batched_graph_destroy.restype = i
     u64 = ctypes.c_uint64
@@ -409,6 +412,18 @@ class BatchGraph:
                "expm_batched_graph_info")
         return {"scheme": sc.value, "launch_groups": groups.value, "device_bytes": nbytes.value,
                 "ms_per_scheme": list(ms)}
+
+    def buckets(self) -> list:
+        """Per launch group of the graph: padded order, instances, the trailing-update tile
+        shape in use (0: 128 x 64, 1: 64 x 64) and the factorization ms timed with each."""
+        cnt = lib.expm_batched_graph_buckets(self._h, 0, None, None, None, None, None)
+        if cnt < 0:
+            raise RuntimeError("expm_batched_graph_buckets: no graph")
+        cint, cdbl = ctypes.c_int * max(cnt, 1), ctypes.c_double * max(cnt, 1)
+        order, ninst, tile, m0, m1 = cint(), cint(), cint(), cdbl(), cdbl()
+        lib.expm_batched_graph_buckets(self._h, cnt, order, ninst, tile, m0, m1)
+        return [{"order": order[j], "ninst": ninst[j], "tile": tile[j], "ms_tile": (m0[j], m1[j])}
+                for j in range(cnt)]
 
     def close(self) -> None:
         if getattr(self, "_h", None):

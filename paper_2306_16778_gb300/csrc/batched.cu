@@ -243,6 +243,7 @@ namespace {
 struct GraphChunk {
     DenseGeom g;
     int nb, kb;
+    double tile_ms[2] = {-1.0, -1.0};  // factorization time with each trailing-update tile shape (tuned)
     std::vector<int> inst;  // original instance indices, in batch order
     size_t ptr_off, res_off;  // offsets of the pointer table and of the results in the graph memory
 };
@@ -323,6 +324,72 @@ namespace {
 
 static inline size_t al256(size_t x) { return (x + 255) & ~size_t(255); }
 
+// The padded staging buffers of chunk c as the dense kernels' input/output.
+DenseIO chunk_io(const expm_batch_graph_s *G, const GraphChunk &c) {
+    const BatchSpec &b = G->spec;
+    unsigned char *m = (unsigned char *)G->mem;
+    const int nb = c.nb, kb = c.kb, ni = c.g.ninst;
+    const size_t bytesA = sizeof(double) * (size_t)ni * nb * nb * b.aw;
+    const size_t bytesV = sizeof(double) * (size_t)ni * nb * kb * b.vw;
+    DenseIO io{};
+    io.A = (double *)(m + G->stage_off);
+    io.lda = nb;
+    io.astride = (int64_t)nb * nb;
+    io.V = (double *)(m + G->stage_off + bytesA);
+    io.ldv = kb;
+    io.vstride = (int64_t)nb * kb;
+    io.v_cplx = b.v_cplx;
+    io.Y = (double *)(m + G->stage_off + bytesA + bytesV);
+    io.ldy = kb;
+    io.ystride = (int64_t)nb * kb;
+    io.y_real = b.yw == 1 ? 1 : 0;
+    return io;
+}
+void enqueue_gather(const expm_batch_graph_s *G, const GraphChunk &c, const DenseIO &io, cudaStream_t st) {
+    const BatchSpec &b = G->spec;
+    const InstPtr *dptr = (const InstPtr *)((unsigned char *)G->mem + c.ptr_off);
+    const unsigned gx = (unsigned)std::min<int64_t>(((int64_t)c.nb * c.nb * b.aw + 255) / 256, 1024);
+    gather_pad<<<dim3(gx, 1, c.g.ninst), 256, 0, st>>>(dptr, c.nb, c.kb, b.aw, b.vw, const_cast<double *>(io.A),
+                                                     const_cast<double *>(io.V));
+}
+
+// Per-bucket tuning of the binary32 trailing updates' tile shape: each chunk's gather and
+// factorization run with 128 x 64 and with 64 x 64 output tiles (the second run of each
+// timed), and the faster shape is kept for the capture.
+cudaError_t tune_tiles(expm_batch_graph_s *G, cudaStream_t st) {
+    Profiler off;
+    cudaEvent_t e0, e1;
+    cudaError_t err = cudaEventCreate(&e0);
+    if (err != cudaSuccess) return err;
+    if ((err = cudaEventCreate(&e1)) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return err;
+    }
+    const DenseSystems &sys = G->spec.sys;
+    for (GraphChunk &c : G->chunks) {
+        if (!c.g.mixed || c.g.tc) continue;  // binary64 has one shape; tensor-core buckets use no SIMT tile
+        const DenseIO io = chunk_io(G, c);
+        for (int tile = 0; tile < 2 && err == cudaSuccess; ++tile) {
+            c.g.tile = tile;
+            for (int rep = 0; rep < 2 && err == cudaSuccess; ++rep) {
+                if (rep == 1) err = cudaEventRecord(e0, st);
+                enqueue_gather(G, c, io, st);
+                if (err == cudaSuccess) err = cudaGetLastError();
+                if (err == cudaSuccess) err = dense_factor(c.g, io, sys, (unsigned char *)G->mem + G->work_off, st, off);
+                if (err == cudaSuccess && rep == 1) err = cudaEventRecord(e1, st);
+            }
+            float ms = 0.f;
+            if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+            if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
+            c.tile_ms[tile] = ms;
+        }
+        c.g.tile = (c.tile_ms[1] >= 0.0 && c.tile_ms[1] < c.tile_ms[0]) ? 1 : 0;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return err;
+}
+
 // Enqueues the whole evaluation of graph object G on st (used for the warm-up run and
 // inside the capture).
 cudaError_t enqueue_batched(expm_batch_graph_s *G, cudaStream_t st) {
@@ -343,28 +410,11 @@ cudaError_t enqueue_batched(expm_batch_graph_s *G, cudaStream_t st) {
     }
     for (const GraphChunk &c : G->chunks) {
         const int nb = c.nb, kb = c.kb, ni = c.g.ninst;
-        const size_t bytesA = sizeof(double) * (size_t)ni * nb * nb * b.aw;
-        const size_t bytesV = sizeof(double) * (size_t)ni * nb * kb * b.vw;
-        double *Apad = (double *)(m + G->stage_off);
-        double *Vpad = (double *)(m + G->stage_off + bytesA);
-        double *Ypad = (double *)(m + G->stage_off + bytesA + bytesV);
+        const DenseIO io = chunk_io(G, c);
         const InstPtr *dptr = (const InstPtr *)(m + c.ptr_off);
-        const unsigned gx = (unsigned)std::min<int64_t>(((int64_t)nb * nb * b.aw + 255) / 256, 1024);
-        gather_pad<<<dim3(gx, 1, ni), 256, 0, st>>>(dptr, nb, kb, b.aw, b.vw, Apad, Vpad);
+        enqueue_gather(G, c, io, st);
         cudaError_t err = cudaGetLastError();
         if (err != cudaSuccess) return err;
-        DenseIO io{};
-        io.A = Apad;
-        io.lda = nb;
-        io.astride = (int64_t)nb * nb;
-        io.V = Vpad;
-        io.ldv = kb;
-        io.vstride = (int64_t)nb * kb;
-        io.v_cplx = b.v_cplx;
-        io.Y = Ypad;
-        io.ldy = kb;
-        io.ystride = (int64_t)nb * kb;
-        io.y_real = b.yw == 1 ? 1 : 0;
         unsigned char *r = m + c.res_off;
         DenseDevOut out{(int *)r, (double *)(r + 256), (double *)(r + 256 + al256(sizeof(double) * ni))};
         err = dense_run_devctl(c.g, io, b.sys, m + G->work_off, st, off, out);
@@ -378,7 +428,7 @@ cudaError_t enqueue_batched(expm_batch_graph_s *G, cudaStream_t st) {
             if (err != cudaSuccess) return err;
         }
         scatter_unpad<<<dim3((unsigned)std::min<int64_t>(((int64_t)nb * kb * b.yw + 255) / 256, 1024), 1, ni), 256, 0,
-                        st>>>(dptr, nb, kb, b.yw, Ypad);
+                        st>>>(dptr, nb, kb, b.yw, io.Y);
         if ((err = cudaGetLastError()) != cudaSuccess) return err;
     }
     return cudaSuccess;
@@ -394,9 +444,10 @@ void destroy_graph(expm_batch_graph_s *G) {
 }
 
 // Builds, warms up and captures the graph for one bucket scheme (or, with `small`, the
-// one-launch kernel for the single instance of geometry sg).
+// one-launch kernel for the single instance of geometry sg); with `tune`, each bucket's
+// trailing-update tile shape is chosen by timing first.
 expm_status build_graph(const BatchSpec &b, int scheme, int device, expm_batch_graph_s **out,
-                        const DenseGeom *sg = nullptr) {
+                        const DenseGeom *sg = nullptr, bool tune = false) {
     auto G = new expm_batch_graph_s();
     G->device = device;
     G->scheme = scheme;
@@ -446,6 +497,7 @@ expm_status build_graph(const BatchSpec &b, int scheme, int device, expm_batch_g
     }
     cudaStream_t st = nullptr;
     if (err == cudaSuccess) err = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    if (err == cudaSuccess && tune && !G->small) err = tune_tiles(G, st);
     // one plain run first: sets kernel attributes and checks every launch outside capture
     if (err == cudaSuccess) err = enqueue_batched(G, st);
     if (err == cudaSuccess) err = cudaStreamSynchronize(st);
@@ -579,7 +631,7 @@ extern "C" expm_status expm_batched_capture(expm_plan p, int count, const int *n
     double ms[3] = {-1.0, -1.0, -1.0};
     for (int sc = 0; sc < 3; ++sc) {
         expm_batch_graph_s *G = nullptr;
-        expm_status s = build_graph(b, sc, p->device, &G);
+        expm_status s = build_graph(b, sc, p->device, &G, nullptr, true);
         if (s != EXPM_OK) {
             if (best) destroy_graph(best);
             return s;
@@ -650,6 +702,21 @@ extern "C" expm_status expm_batched_graph_info(expm_batch_graph G, int *scheme, 
     if (ms_per_scheme)
         for (int i = 0; i < 3; ++i) ms_per_scheme[i] = G->ms_per_scheme[i];
     return EXPM_OK;
+}
+
+extern "C" int expm_batched_graph_buckets(expm_batch_graph G, int max, int *order, int *ninst, int *tile,
+                                          double *ms_tile0, double *ms_tile1) {
+    if (!G) return -1;
+    const int nc = (int)G->chunks.size();
+    for (int i = 0; i < nc && i < max; ++i) {
+        const expm::GraphChunk &c = G->chunks[i];
+        if (order) order[i] = c.nb;
+        if (ninst) ninst[i] = c.g.ninst;
+        if (tile) tile[i] = c.g.tile;
+        if (ms_tile0) ms_tile0[i] = c.tile_ms[0];
+        if (ms_tile1) ms_tile1[i] = c.tile_ms[1];
+    }
+    return nc;
 }
 
 extern "C" expm_status expm_batched_graph_destroy(expm_batch_graph G) {

@@ -499,7 +499,7 @@ static cudaError_t lu_panels_tc(int n, int batch, cx<float> *F, cudaStream_t st,
 // tc (binary32 only) the trailing updates run on the tensor cores.
 template <class T>
 static cudaError_t lu_blocked(int n, int batch, cx<T> *F, cudaStream_t st, Profiler &prof,
-                              const TcScratch *tc = nullptr) {
+                              const TcScratch *tc = nullptr, int tile = 0) {
     // bf16x3 only: with 3xTF32 (twice the truncated accumulation steps per unit of K, 22
     // split bits instead of 24) the K = 256 updates cost a second refinement sweep
     // (measured), so 3xTF32 keeps the rank-64 updates
@@ -566,7 +566,7 @@ static cudaError_t lu_blocked(int n, int batch, cx<T> *F, cudaStream_t st, Profi
             // A22 -= L21 U12
             cgemm_launch<T, cx<T>, false, false>(rest, rest, nb, cx<T>{T(-1), T(0)}, T(1), diag + (int64_t)nb * n, n,
                                                  bs, diag + nb, n, bs, diag + (int64_t)nb * n + nb, n, bs, 1, batch,
-                                                 st);
+                                                 st, tile);
             return cudaGetLastError();
         }));
     }
@@ -875,7 +875,7 @@ static cudaError_t factor_pairs(const DenseGeom &g, const DenseIO &io, const Den
             g.n, io.A, (int)io.lda, io.astride, g.complex_a, g.npairs, g.t, pairs, F, amax);
         return cudaGetLastError();
     }));
-    EXPM_TRY(lu_blocked<T>(g.n, batch, F, st, prof, tc));
+    EXPM_TRY(lu_blocked<T>(g.n, batch, F, st, prof, tc, g.tile));
     max_abs_upper<T><<<dim3((g.n + 7) / 8, 1, batch), 256, 0, st>>>(g.n, F, g.n, (int64_t)g.n * g.n, umax);
     return cudaGetLastError();
 }

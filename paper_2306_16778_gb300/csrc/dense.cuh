@@ -32,6 +32,7 @@ struct DenseGeom {
     int complex_a;  // A complex Hermitian (else real symmetric)
     int mixed;      // binary32 factorization + binary64 refinement
     int tc;         // mixed only: LU trailing updates on the tensor cores (1: 3xTF32, 2: bf16x3)
+    int tile = 0;   // binary32 SIMT trailing updates: 0 = 128 x 64 output tiles, 1 = 64 x 64
     double t;       // time factor
     double tol;     // refinement tolerance
     int max_refine;

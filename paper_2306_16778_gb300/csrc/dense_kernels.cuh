@@ -353,9 +353,10 @@ __global__ void __launch_bounds__(256, 2) cgemm_f32w(int m, int n, int K, cx<flo
 template <class T, class AE, bool CONJ_A, bool CONJ_B>
 inline void cgemm_launch(int m, int n, int K, cx<T> alpha, T beta, const AE *A, int lda, int64_t sA,
                          const cx<T> *B, int ldb, int64_t sB, cx<T> *C, int ldc, int64_t sC, int adiv, int batch,
-                         cudaStream_t st) {
+                         cudaStream_t st, int tile = 0) {
+    // tile 0: 128 x 64 output tiles for binary32 (wider than 32 columns), tile 1: 64 x 64
     if constexpr (std::is_same<T, float>::value && std::is_same<AE, cx<float>>::value && !CONJ_B) {
-        if (n > 32) {
+        if (n > 32 && tile == 0) {
             dim3 g((n + 63) / 64, (m + 127) / 128, batch);
             cgemm_f32w<CONJ_A><<<g, 256, 0, st>>>(m, n, K, alpha, beta, A, lda, sA, B, ldb, sB, C, ldc, sC, adiv);
             return;

@@ -130,6 +130,15 @@ def test_graph_autotune():
     assert info["scheme"] in (0, 1, 2)
     assert all(ms > 0 for ms in info["ms_per_scheme"])
     assert info["ms_per_scheme"][info["scheme"]] == min(info["ms_per_scheme"])
+    # every bucket (all factorised on the FP32 pipe here) timed both trailing-update tile
+    # shapes and kept the faster; the groups cover every instance once
+    bk = gr.buckets()
+    assert len(bk) == info["launch_groups"] and sum(b["ninst"] for b in bk) == len(inst)
+    sizes = sorted(A.shape[0] for A, _, _, _ in inst)
+    assert max(b["order"] for b in bk) >= sizes[-1]
+    for b in bk:
+        m0, m1 = b["ms_tile"]
+        assert m0 > 0 and m1 > 0 and b["tile"] == (1 if m1 < m0 else 0)
     infos = gr.replay(want_info=True)
     assert all(i.status_worst == 0 for i in infos)
     th, a = coeffs.theta(12), coeffs.residues(12)
@@ -167,6 +176,8 @@ def test_tensor_core_buckets(prec):
     assert all(i.status_worst == 0 for i in ia)
     Yg = [torch.empty_like(v) for v in Vs]
     gr = P.BatchGraph(plan, As, Vs, Yg, prec=prec, scheme=0)
+    # no tuning without autotuning: every group keeps the default shape, untimed
+    assert all(b["tile"] == 0 and b["ms_tile"] == (-1.0, -1.0) for b in gr.buckets())
     ig = gr.replay(want_info=True)
     torch.cuda.synchronize()
     assert all(i.status_worst == 0 for i in ig)

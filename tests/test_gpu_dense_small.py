@@ -109,7 +109,7 @@ def test_small_captured_graph(plans, prec, n, k, cplx):
     dA, dV = (torch.from_numpy(x).to(DEV) for x in (A, V))
     dY = torch.empty_like(dV)
     gr = P.BatchGraph(plans[12], [dA], [dV], [dY], prec=prec, scheme=-1)
-    assert gr.info()["launch_groups"] == 1
+    assert gr.info()["launch_groups"] == 1 and gr.buckets() == []
     for rep in range(2):
         infos = gr.replay(want_info=True)
         torch.cuda.synchronize()
