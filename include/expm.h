@@ -180,7 +180,13 @@ expm_status expm_plan_destroy(expm_plan plan);
  * number has a positive-definite Hermitian part when Im lambda != 0, so no pivot
  * is needed), the separators solve a reduced tridiagonal system by cyclic
  * reduction, and the blocks are then solved and summed with their weights.
- * Returns EXPM_ENOTSUP for complex e (not implemented), EXPM_EINVAL for bad sizes.
+ * Complex e (a general Hermitian T): D = diag(phi), phi_0 = 1, phi_{i+1} = phi_i
+ * conj(e_i)/|e_i|, is unitary and D^H T D is real symmetric with off-diagonal |e|;
+ * since every resolvent satisfies (tT - cI + theta I)^{-1} = D (tD^H T D - cI +
+ * theta I)^{-1} D^H, the call forms phi (a parallel prefix product), solves the real
+ * problem on D^H V and multiplies row i of the result by phi_i.  Extra device scratch:
+ * 24 N + 16 N r bytes; Y is complex.
+ * Returns EXPM_EINVAL for bad sizes.
  */
 expm_status expm_apply_tridiag(expm_plan plan, int64_t N, const double *d, const void *e,
                                int e_is_complex, const void *V, int r, int v_is_complex,
@@ -202,7 +208,8 @@ expm_status expm_apply_tridiag(expm_plan plan, int64_t N, const double *d, const
  *   Size limit: a problem whose scratch exceeds EXPM_NOALLOC_SCRATCH_BYTES is
  *   rejected with EXPM_EINVAL and a message giving the bytes needed (about
  *   N * (400 + 136 r) bytes for degree 16 and r >= 2 real right-hand sides, so N up
- *   to about 22,000 for r = 8).
+ *   to about 22,000 for r = 8; complex e counts its right-hand sides as complex and
+ *   adds 24 N + 16 N r bytes for |e|, the phases and D^H V).
  *   Set-up: the first call on each device looks up the array's device address
  *   (cudaGetSymbolAddress) with that device current and caches it.  With CUDA's lazy
  *   module loading (the default) that first lookup is also when the library's module,
@@ -427,9 +434,12 @@ expm_status expm_batched_graph_destroy(expm_batch_graph graph);
  *   expm_server_create     hbm_budget_bytes: bound on solve scratch + cached factors
  *                          (operator copies are not counted); 1 <= max_inflight <= 64.
  *                          Uses the CUDA device current at creation.
- *   expm_server_register_op  desc: EXPM_OP_TRIDIAG (d, e as in expm_apply_tridiag;
- *                          real e only) or EXPM_OP_DENSE (A, lda, a_is_complex); the
- *                          data may be host or device memory and is copied.
+ *   expm_server_register_op  desc: EXPM_OP_TRIDIAG (d, e, e_is_complex as in
+ *                          expm_apply_tridiag; for complex e the phases phi and |e|
+ *                          are formed once here and each request solves on D^H V,
+ *                          with 16 n k more bytes of solve scratch) or EXPM_OP_DENSE
+ *                          (A, lda, a_is_complex); the data may be host or device
+ *                          memory and is copied.
  *   expm_server_submit     V and Y device memory (EXPM_EINVAL otherwise), valid until
  *                          poll reports the request finished, as is the plan; 1 <= k <= 64;
  *                          opts as for the matching apply call
@@ -449,7 +459,7 @@ typedef struct expm_op_desc {
     int64_t n;         /* rows (tridiagonal N or dense order n)        */
     const double *d;   /* tridiagonal: diagonal (n doubles)            */
     const void *e;     /* tridiagonal: off-diagonal (n-1 entries)      */
-    int e_is_complex;  /* tridiagonal: must be 0                       */
+    int e_is_complex;  /* tridiagonal: e complex (Hermitian T; Y complex) */
     const void *A;     /* dense: n x n, row-major                      */
     int lda;           /* dense: leading dimension (elements)          */
     int a_is_complex;  /* dense: complex Hermitian if nonzero          */

@@ -241,12 +241,15 @@ expm_status expm_apply_tridiag(expm_plan p, int64_t N, const double *d, const vo
         return set_error(EXPM_EINVAL, "apply_tridiag: need 0 <= max_refine <= 64 and tol >= 0");
     if (!std::isfinite(opts.t) || !std::isfinite(opts.shift_c))
         return set_error(EXPM_EINVAL, "apply_tridiag: t and shift_c must be finite");
-    if (e_is_complex) return set_error(EXPM_ENOTSUP, "apply_tridiag: complex off-diagonal not implemented");
     if (info) *info = expm_info{0, 0.0, 0.0, EXPM_OK};
 
     DeviceGuard guard(p->device);
     const bool ff = opts.prec == EXPM_MIXED_F32X2;
-    const int Rc = r * (v_is_complex ? 2 : 1);  // complex V with real T: real and imaginary parts are columns
+    const bool herm = e_is_complex != 0;  // complex T: solved as D^H T D (real) on D^H V
+    const int Rin = r * (v_is_complex ? 2 : 1);  // real doubles per row of V
+    // the kernels' real columns: complex V with real T has its real and imaginary parts as
+    // columns; complex T always gives a complex V' = D^H V and a complex Y
+    const int Rc = herm ? 2 * r : Rin;
     const int S = p->degree / 2;
     TriPoles ps{};
     const double ec = std::exp(opts.shift_c);
@@ -263,7 +266,10 @@ expm_status expm_apply_tridiag(expm_plan p, int64_t N, const double *d, const vo
     const MixOpts mo{opts.max_refine, (opts.flags & EXPM_FLAG_SKIP_FINAL_RESIDUAL) ? 0 : 1, opts.tol};
     const size_t mix_factor = mixed ? tri_mixed_factor_bytes(g) : 0;
 
-    const size_t need = mixed ? mix_factor + tri_mixed_solve_bytes(g, mo.max_refine) : tri_workspace_bytes(g, ff);
+    const size_t base_need =
+        mixed ? mix_factor + tri_mixed_solve_bytes(g, mo.max_refine) : tri_workspace_bytes(g, ff);
+    const size_t herm_off = (base_need + 255) & ~(size_t)255;
+    const size_t need = herm ? herm_off + herm_scratch_bytes(N, r) : base_need;
     expm_status s = plan_reserve(p, &p->work, &p->work_bytes, need);
     if (s != EXPM_OK) return s;
 
@@ -271,19 +277,20 @@ expm_status expm_apply_tridiag(expm_plan p, int64_t N, const double *d, const vo
                dy = is_device_ptr(Y);
     const double *dD = d, *dE = (const double *)e, *dV = (const double *)V;
     double *dY = (double *)Y;
-    const size_t nV = (size_t)N * Rc;
+    const size_t nV = (size_t)N * Rin, nY = (size_t)N * Rc;
+    const size_t ew = e_is_complex ? 2 : 1;  // doubles per off-diagonal entry
     const bool staged = !(dd && de && dv && dy);
     cudaEvent_t v_ready = nullptr;  // set when V is copied on the second stream
     if (staged) {
-        const size_t bytes = sizeof(double) * ((size_t)N + (size_t)N + 2 * nV) + 1024;
+        const size_t bytes = sizeof(double) * ((size_t)N + ew * (size_t)N + nV + nY) + 1024;
         s = plan_reserve(p, &p->stage, &p->stage_bytes, bytes);
         if (s != EXPM_OK) return s;
         double *base = (double *)p->stage;
-        double *sD = base, *sE = base + N, *sV = sE + N, *sY = sV + nV;
+        double *sD = base, *sE = base + N, *sV = sE + ew * N, *sY = sV + nV;
         cudaError_t err = cudaSuccess;
         if (!dd) { err = cudaMemcpyAsync(sD, d, sizeof(double) * N, cudaMemcpyHostToDevice, st); dD = sD; }
         if (err == cudaSuccess && !de && N > 1) {
-            err = cudaMemcpyAsync(sE, e, sizeof(double) * (N - 1), cudaMemcpyHostToDevice, st);
+            err = cudaMemcpyAsync(sE, e, sizeof(double) * ew * (N - 1), cudaMemcpyHostToDevice, st);
             dE = sE;
         }
         if (err == cudaSuccess && !dv) {
@@ -305,6 +312,17 @@ expm_status expm_apply_tridiag(expm_plan p, int64_t N, const double *d, const vo
         if (err != cudaSuccess) return cuda_error(err, "apply_tridiag: staging copy");
     }
     cudaError_t err;
+    HermWork hw{};
+    if (herm) {  // |e|, phi and D^H V; the kernels below then see a real symmetric T
+        hw = herm_carve((unsigned char *)p->work + herm_off, N, r);
+        if (v_ready) err = cudaStreamWaitEvent(st, v_ready, 0);
+        else err = cudaSuccess;
+        v_ready = nullptr;
+        if (err == cudaSuccess) err = herm_prepare(N, dE, dV, r, v_is_complex, hw, p->sm_count, st);
+        if (err != cudaSuccess) return cuda_error(err, "apply_tridiag: Hermitian phases");
+        dE = hw.eabs;
+        dV = hw.Vp;
+    }
     if (mixed) {
         void *swork = (unsigned char *)p->work + mix_factor;
         err = tri_mixed_factor(g, dD, dE, ps, p->work, st, p->prof);
@@ -323,8 +341,12 @@ expm_status expm_apply_tridiag(expm_plan p, int64_t N, const double *d, const vo
         err = tri_run(g, ff, dD, dE, dV, dY, ps, p->work, st, p->prof, v_ready);
         if (err != cudaSuccess) return cuda_error(err, "apply_tridiag: kernel launch");
     }
+    if (herm) {  // Y = D Y'
+        err = herm_finish(N, r, hw, dY, p->sm_count, st);
+        if (err != cudaSuccess) return cuda_error(err, "apply_tridiag: Hermitian phases");
+    }
     if (staged) {
-        if (!dy) err = cudaMemcpyAsync(Y, dY, sizeof(double) * nV, cudaMemcpyDeviceToHost, st);
+        if (!dy) err = cudaMemcpyAsync(Y, dY, sizeof(double) * nY, cudaMemcpyDeviceToHost, st);
         if (err == cudaSuccess) err = cudaStreamSynchronize(st);
         if (err != cudaSuccess) return cuda_error(err, "apply_tridiag: result copy");
     }

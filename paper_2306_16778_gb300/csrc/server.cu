@@ -47,7 +47,8 @@ struct Op {
     int kind = 0;
     int64_t n = 0;
     int a_cplx = 0;
-    void *data = nullptr;  // tridiag: d (n) then e (n-1); dense: A (n x n, ld n)
+    int herm = 0;          // tridiag with complex e: data holds d, |e| and the phases phi
+    void *data = nullptr;  // tridiag: d (n) then e (n-1) [then phi (n complex)]; dense: A (n x n, ld n)
     size_t bytes = 0;
 };
 
@@ -206,9 +207,18 @@ void run_request(expm_server_s *sv, Worker &w, Request &r, FactorEntry &fe, bool
     cudaError_t err = cudaSuccess;
     r.ts[2] = sv->now();
     const bool ff = r.opts.prec != EXPM_FP64;
+    // complex Hermitian T: the kernels solve with D^H V (in the worker's scratch past the
+    // solve part) for the real symmetric D^H T D, and Y's rows are then multiplied by phi
+    const double *Vin = (const double *)r.V;
+    const double *phi = op.herm ? (const double *)op.data + 2 * op.n : nullptr;
+    auto herm_in = [&](size_t solve_part) {
+        double *Vp = (double *)((unsigned char *)w.work + ((solve_part + 255) & ~(size_t)255));
+        Vin = Vp;
+        return herm_scale(op.n, r.k, phi, (const double *)r.V, r.v_cplx, Vp, 1, sv->sm_count, w.stream);
+    };
     if (op.kind == EXPM_OP_TRIDIAG && r.opts.prec == EXPM_MIXED_FP32) {
         // binary32 factors + refinement: the factor part is cached like the others
-        const int Rc = r.k * (r.v_cplx ? 2 : 1);
+        const int Rc = op.herm ? 2 * r.k : r.k * (r.v_cplx ? 2 : 1);
         TriGeom g = tri_mixed_geometry(op.n, r.plan->degree / 2, Rc, sv->sm_count);
         g.t = r.opts.t;
         g.cshift = r.opts.shift_c;
@@ -223,8 +233,10 @@ void run_request(expm_server_s *sv, Worker &w, Request &r, FactorEntry &fe, bool
         } else {
             err = fe.failed ? cudaErrorUnknown : cudaStreamWaitEvent(w.stream, fe.done, 0);
         }
-        if (err == cudaSuccess)
-            err = tri_mixed_solve(g, (const double *)r.V, (double *)r.Y, ps, fe.buf, w.work, mo, w.stream, off);
+        if (err == cudaSuccess && op.herm) err = herm_in(tri_mixed_solve_bytes(g, mo.max_refine));
+        if (err == cudaSuccess) err = tri_mixed_solve(g, Vin, (double *)r.Y, ps, fe.buf, w.work, mo, w.stream, off);
+        if (err == cudaSuccess && op.herm)
+            err = herm_scale(op.n, r.k, phi, (const double *)r.Y, 1, (double *)r.Y, 0, sv->sm_count, w.stream);
         MixResult mr{};
         if (err == cudaSuccess) err = tri_mixed_read_state(g, w.work, mo.max_refine, &mr, w.stream);  // synchronises
         if (err == cudaSuccess) {
@@ -233,7 +245,7 @@ void run_request(expm_server_s *sv, Worker &w, Request &r, FactorEntry &fe, bool
             if (mo.verify && !mr.converged) st = EXPM_ENOCONV;
         }
     } else if (op.kind == EXPM_OP_TRIDIAG) {
-        const int Rc = r.k * (r.v_cplx ? 2 : 1);
+        const int Rc = op.herm ? 2 * r.k : r.k * (r.v_cplx ? 2 : 1);
         TriGeom g = tri_geometry(op.n, r.plan->degree / 2, Rc, ff, sv->sm_count);
         g.t = r.opts.t;
         g.cshift = r.opts.shift_c;
@@ -247,8 +259,10 @@ void run_request(expm_server_s *sv, Worker &w, Request &r, FactorEntry &fe, bool
         } else {
             err = fe.failed ? cudaErrorUnknown : cudaStreamWaitEvent(w.stream, fe.done, 0);
         }
-        if (err == cudaSuccess)
-            err = tri_solve(g, ff, (const double *)r.V, (double *)r.Y, ps, fe.buf, w.work, w.stream, off);
+        if (err == cudaSuccess && op.herm) err = herm_in(tri_solve_bytes(g, ff));
+        if (err == cudaSuccess) err = tri_solve(g, ff, Vin, (double *)r.Y, ps, fe.buf, w.work, w.stream, off);
+        if (err == cudaSuccess && op.herm)
+            err = herm_scale(op.n, r.k, phi, (const double *)r.Y, 1, (double *)r.Y, 0, sv->sm_count, w.stream);
         if (err == cudaSuccess) err = cudaStreamSynchronize(w.stream);
     } else {
         const DenseGeom g = dense_geom(op, r.plan, r.opts, r.k, r.v_cplx);
@@ -462,12 +476,24 @@ expm_status expm_server_register_op(expm_server sv, const expm_op_desc *desc, ui
     cudaError_t e = cudaSuccess;
     if (desc->kind == EXPM_OP_TRIDIAG) {
         if (!desc->d || (desc->n > 1 && !desc->e)) return set_error(EXPM_EINVAL, "server_register_op: NULL d or e");
-        if (desc->e_is_complex) return set_error(EXPM_ENOTSUP, "server_register_op: complex off-diagonal");
-        op.bytes = sizeof(double) * (2 * (size_t)desc->n);
+        op.herm = desc->e_is_complex ? 1 : 0;
+        op.bytes = sizeof(double) * ((op.herm ? 4 : 2) * (size_t)desc->n);
         e = cudaMalloc(&op.data, op.bytes);
         if (e == cudaSuccess) e = cudaMemcpy(op.data, desc->d, sizeof(double) * desc->n, cudaMemcpyDefault);
-        if (e == cudaSuccess && desc->n > 1)
+        if (e == cudaSuccess && desc->n > 1 && !op.herm)
             e = cudaMemcpy((double *)op.data + desc->n, desc->e, sizeof(double) * (desc->n - 1), cudaMemcpyDefault);
+        if (e == cudaSuccess && op.herm) {  // |e| and phi once per operator (D^H T D real symmetric)
+            void *tmp = nullptr;
+            const size_t eb = 2 * sizeof(double) * (size_t)std::max<int64_t>(desc->n - 1, 1);
+            e = cudaMalloc(&tmp, eb + herm_part_bytes(desc->n));
+            if (e == cudaSuccess && desc->n > 1) e = cudaMemcpy(tmp, desc->e, eb, cudaMemcpyDefault);
+            double *dd = (double *)op.data;
+            if (e == cudaSuccess)
+                e = herm_phases(desc->n, (const double *)tmp, dd + desc->n, dd + 2 * desc->n,
+                                (double *)((unsigned char *)tmp + eb), nullptr);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(nullptr);
+            if (tmp) cudaFree(tmp);
+        }
     } else if (desc->kind == EXPM_OP_DENSE) {
         if (!desc->A || desc->lda < desc->n) return set_error(EXPM_EINVAL, "server_register_op: bad A or lda");
         op.a_cplx = desc->a_is_complex ? 1 : 0;
@@ -526,7 +552,7 @@ expm_status expm_server_submit(expm_server sv, uint64_t op_id, const expm_plan p
             return set_error(EXPM_EINVAL, "server_submit: tridiagonal precision must be FP64, MIXED_F32X2 or MIXED_FP32");
         if (tri_mixed && (opts.max_refine < 0 || opts.max_refine > 64 || !(opts.tol >= 0.0)))
             return set_error(EXPM_EINVAL, "server_submit: need 0 <= max_refine <= 64 and tol >= 0");
-        const int Rc = k * (v_is_complex ? 2 : 1);
+        const int Rc = op.herm ? 2 * k : k * (v_is_complex ? 2 : 1);
         if (tri_mixed) {
             const TriGeom g = tri_mixed_geometry(op.n, plan->degree / 2, Rc, sv->sm_count);
             r->solve_bytes = tri_mixed_solve_bytes(g, opts.max_refine);
@@ -536,6 +562,8 @@ expm_status expm_server_submit(expm_server sv, uint64_t op_id, const expm_plan p
             r->solve_bytes = tri_solve_bytes(g, ff);
             r->factor_bytes = tri_factor_bytes(g, ff);
         }
+        if (op.herm)  // D^H V past the solve part
+            r->solve_bytes = ((r->solve_bytes + 255) & ~(size_t)255) + 2 * sizeof(double) * (size_t)op.n * k;
     } else {
         if (opts.prec != EXPM_FP64 && opts.prec != EXPM_MIXED_FP32 && opts.prec != EXPM_MIXED_F32X2)
             return set_error(EXPM_EINVAL, "server_submit: dense precision must be FP64 or mixed");

@@ -70,4 +70,28 @@ cudaError_t tri_mixed_solve(const TriGeom &g, const double *V, double *Y, const 
 // copies the device-side refinement state back (synchronises the stream)
 cudaError_t tri_mixed_read_state(const TriGeom &g, const void *swork, int max_refine, MixResult *out, cudaStream_t st);
 
+// complex Hermitian T (tridiag_herm.cu): D^H T D is real symmetric with off-diagonal |e|
+// for a diagonal unitary D = diag(phi).  herm_prepare forms |e| (N-1 doubles), phi (N
+// complex) and V' = D^H V (N x r complex) in the scratch; the real-off-diagonal kernels
+// then solve with |e| and V' into the complex Y, and herm_finish multiplies row i of Y
+// by phi_i in place.
+struct HermWork {
+    double *eabs;  // |e_i|, N-1 doubles
+    double *phi;   // phi_i, N complex
+    double *Vp;    // D^H V, N x r complex
+    double *part;  // block products (scan scratch)
+};
+size_t herm_scratch_bytes(int64_t N, int r);
+size_t herm_part_bytes(int64_t N);  // scan scratch of herm_phases
+// |e| (N-1 doubles) and phi (N complex) of complex e (N-1 complex)
+cudaError_t herm_phases(int64_t N, const double *e, double *eabs, double *phi, double *part, cudaStream_t st);
+// Out = s(phi) X row by row (s = conj with conj_phi); X real or complex, Out complex; Out
+// may equal X when X is complex
+cudaError_t herm_scale(int64_t N, int r, const double *phi, const double *X, int x_cplx, double *Out, int conj_phi,
+                       int sm_count, cudaStream_t st);
+HermWork herm_carve(void *scratch, int64_t N, int r);
+cudaError_t herm_prepare(int64_t N, const double *e, const double *V, int r, int v_cplx, const HermWork &w,
+                         int sm_count, cudaStream_t st);
+cudaError_t herm_finish(int64_t N, int r, const HermWork &w, double *Y, int sm_count, cudaStream_t st);
+
 }  // namespace expm

@@ -58,7 +58,6 @@ extern "C" expm_status expm_apply_tridiag_noalloc(expm_plan p, int64_t N, const 
     if (opts.flags != 0) return set_error(EXPM_EINVAL, "apply_tridiag_noalloc: opts.flags must be 0");
     if (!std::isfinite(opts.t) || !std::isfinite(opts.shift_c))
         return set_error(EXPM_EINVAL, "apply_tridiag_noalloc: t and shift_c must be finite");
-    if (e_is_complex) return set_error(EXPM_ENOTSUP, "apply_tridiag_noalloc: complex off-diagonal not implemented");
     if (info) *info = expm_info{0, 0.0, 0.0, EXPM_OK};
 
     DeviceGuard guard(p->device);
@@ -67,7 +66,8 @@ extern "C" expm_status expm_apply_tridiag_noalloc(expm_plan p, int64_t N, const 
         return set_error(EXPM_EINVAL, "apply_tridiag_noalloc: d, e, V and Y must be device memory");
 
     const bool ff = opts.prec == EXPM_MIXED_F32X2;
-    const int Rc = r * (v_is_complex ? 2 : 1);
+    const bool herm = e_is_complex != 0;  // complex T: solved as D^H T D (real) on D^H V
+    const int Rc = herm ? 2 * r : r * (v_is_complex ? 2 : 1);
     const int S = p->degree / 2;
     TriPoles ps{};
     const double ec = std::exp(opts.shift_c);
@@ -80,7 +80,9 @@ extern "C" expm_status expm_apply_tridiag_noalloc(expm_plan p, int64_t N, const 
     TriGeom g = tri_geometry(N, S, Rc, ff, p->sm_count);
     g.t = opts.t;
     g.cshift = opts.shift_c;
-    const size_t need = tri_workspace_bytes(g, ff);
+    const size_t base_need = tri_workspace_bytes(g, ff);
+    const size_t herm_off = (base_need + 255) & ~(size_t)255;
+    const size_t need = herm ? herm_off + herm_scratch_bytes(N, r) : base_need;
     if (need > (size_t)EXPM_NOALLOC_SCRATCH_BYTES)
         return set_error(EXPM_EINVAL, "apply_tridiag_noalloc: problem needs " + std::to_string(need) +
                                           " bytes of scratch, more than the fixed " +
@@ -90,8 +92,18 @@ extern "C" expm_status expm_apply_tridiag_noalloc(expm_plan p, int64_t N, const 
     cudaError_t err = scratch_address(p->device, &scratch);
     if (err != cudaSuccess) return cuda_error(err, "apply_tridiag_noalloc: cudaGetSymbolAddress");
     Profiler off;  // no event timing: this path creates no CUDA objects
-    err = tri_run(g, ff, d, (const double *)e, (const double *)V, (double *)Y, ps, scratch,
-                  (cudaStream_t)opts.stream, off);
+    const cudaStream_t st = (cudaStream_t)opts.stream;
+    const double *dE = (const double *)e, *dV = (const double *)V;
+    HermWork hw{};
+    if (herm) {
+        hw = herm_carve((unsigned char *)scratch + herm_off, N, r);
+        err = herm_prepare(N, dE, dV, r, v_is_complex, hw, p->sm_count, st);
+        if (err != cudaSuccess) return cuda_error(err, "apply_tridiag_noalloc: Hermitian phases");
+        dE = hw.eabs;
+        dV = hw.Vp;
+    }
+    err = tri_run(g, ff, d, dE, dV, (double *)Y, ps, scratch, st, off);
+    if (err == cudaSuccess && herm) err = herm_finish(N, r, hw, (double *)Y, p->sm_count, st);
     if (err != cudaSuccess) return cuda_error(err, "apply_tridiag_noalloc: kernel launch");
     return EXPM_OK;
 }

@@ -45,9 +45,12 @@ def _oracle(d, e, V, n, t=1.0, c=0.0):
 
 def _gpu(plan, d, e, V, prec, t=1.0, c=0.0, **kw):
     dd = torch.from_numpy(d).to(DEV)
-    de = torch.from_numpy(e).to(DEV) if e.size else torch.zeros(1, dtype=torch.float64, device=DEV)
+    cplx_e = np.iscomplexobj(e)
+    de = torch.from_numpy(e).to(DEV) if e.size else \
+        torch.zeros(1, dtype=torch.complex128 if cplx_e else torch.float64, device=DEV)
     dv = torch.from_numpy(np.ascontiguousarray(V)).to(DEV)
-    dy = torch.empty_like(dv)
+    # Y is complex when V or e is complex
+    dy = torch.empty(V.shape, dtype=torch.complex128 if cplx_e or np.iscomplexobj(V) else torch.float64, device=DEV)
     P.expm_apply_tridiag(plan, dd, de, dv, dy, prec=prec, t=t, shift_c=c, **kw)
     torch.cuda.synchronize()
     return dy.cpu().numpy()
@@ -164,9 +167,9 @@ def test_invalid_arguments(plans):
     d, e, V = _random_tridiag(100, 2, 207)
     dd, de, dv = (torch.from_numpy(x).to(DEV) for x in (d, e, V))
     dy = torch.empty_like(dv)
-    with pytest.raises(P.ExpmError) as ei:
-        P.expm_apply_tridiag(plans[12], dd, de.to(torch.complex128), dv, dy)
-    assert ei.value.status == 9                        # EXPM_ENOTSUP: complex off-diagonal
+    with pytest.raises(P.ExpmError) as ei:             # r = 0
+        P.expm_apply_tridiag(plans[12], dd, de, dv[:, :0], dy[:, :0])
+    assert ei.value.status == 1                        # EXPM_EINVAL
     with pytest.raises(P.ExpmError) as ei:
         P.expm_apply_tridiag(plans[12], dd, de, dv, dy, prec=P.EXPM_MIXED_TF32X3)
     assert ei.value.status == 1                        # EXPM_EINVAL
@@ -258,3 +261,88 @@ def test_mixed_invalid_options(plans):
     with pytest.raises(P.ExpmError) as ei:            # the flag belongs to the refined path only
         P.expm_apply_tridiag(plans[12], dd, de, dv, dy, flags=P.EXPM_FLAG_SKIP_FINAL_RESIDUAL)
     assert ei.value.status == 1
+
+
+# ------------------------------------------------------------- complex Hermitian T
+
+def _random_hermitian(N, r, seed, complex_v=False):
+    """Complex off-diagonal e_i = |e_i| exp(i psi_i) with uniform phases (Gershgorin: the
+    spectrum stays in (-16, 0) as for the real cases), a few exact zeros (T splits there),
+    real negative and purely imaginary entries."""
+    d, e_abs, V = _random_tridiag(N, r, seed, complex_v)
+    g = workloads.rng(seed + 7)
+    e = e_abs * np.exp(1j * g.uniform(0.0, 2 * np.pi, e_abs.shape))
+    if N > 12:
+        e[3] = 0.0
+        e[5] = -e_abs[5]
+        e[7] = 1j * e_abs[7]
+        e[-1] = 0.0
+    return d, e, V
+
+
+@pytest.mark.parametrize("prec", ALL)
+@pytest.mark.parametrize("N,r,n,cv", [(1, 1, 12, False), (2, 3, 16, True), (7, 2, 12, False), (433, 8, 16, True),
+                                      (4096 + 13, 5, 12, False), (50_000, 8, 16, True), (200_003, 3, 12, False)])
+def test_hermitian_tridiag_parity(plans, prec, N, r, n, cv):
+    """Complex e: solved as the real symmetric D^H T D on D^H V (phases by a parallel prefix
+    product over several scan blocks and a ragged tail), against the oracle's direct
+    complex banded solves."""
+    d, e, V = _random_hermitian(N, r, 230 + N + r, cv)
+    Y = _gpu(plans[n], d, e, V, prec)     # N = 1: a complex-typed empty e, complex Y
+    Yo = _oracle(d, e, V, n)
+    assert Y.dtype == np.complex128
+    ok, rel = _close(Y, Yo, V, n, prec)
+    assert ok, rel
+    if N >= 100:
+        assert rel <= TOL[prec]
+
+
+def test_hermitian_with_real_entries_is_the_real_path(plans):
+    """A complex-typed e with real entries: every phase is exactly +-1, so the result is
+    bit-identical to the real-off-diagonal path (positive e with the same data; negative
+    e against |e| with the rows' signs flipped, rounding being sign-symmetric)."""
+    d, e, V = _random_tridiag(30_001, 3, 240, complex_v=True)
+    Yr = _gpu(plans[16], d, e, V, P.EXPM_FP64)
+    Yc = _gpu(plans[16], d, e.astype(np.complex128), V, P.EXPM_FP64)
+    np.testing.assert_array_equal(Yc, Yr)
+    s = np.where(np.arange(30_001) % 2 == 0, 1.0, -1.0)   # D = diag(+-1): (D T D) has -e
+    Yn = _gpu(plans[16], d, (-e).astype(np.complex128), V, P.EXPM_FP64)
+    Yd = s[:, None] * _gpu(plans[16], d, e, s[:, None] * V, P.EXPM_FP64)
+    np.testing.assert_array_equal(Yn, Yd)
+
+
+@pytest.mark.parametrize("prec", ALL)
+def test_hermitian_full_size_gauge_property(plans, full_size, prec):
+    """The 1D Laplacian workload at full size (N = 2^20, 8 RHS, degree 16) under a random
+    diagonal unitary gauge D0 = diag(exp(i psi)): T = D0 L D0^H has e_i = 100 exp(i(psi_i -
+    psi_{i+1})) and exp(T)V = D0 exp(L) (D0^H V) exactly, so the complex-e result must
+    equal D0 times the real path's result on D0^H V (the real path is checked against the
+    oracle at this size by test_laplacian_full_size)."""
+    w, _ = full_size
+    g = workloads.rng(241)
+    psi = g.uniform(0.0, 2 * np.pi, w["d"].shape[0])
+    ph = np.exp(1j * psi)
+    e = w["e"] * ph[:-1] * np.conj(ph[1:])
+    V = w["V"] + 1j * g.standard_normal(w["V"].shape)
+    Y = _gpu(plans[16], w["d"], e, V, prec)
+    Yl = ph[:, None] * _gpu(plans[16], w["d"], w["e"], np.conj(ph)[:, None] * V, P.EXPM_FP64)
+    assert matrix.rel_err(Y, Yl) <= TOL[prec]
+
+
+def test_hermitian_host_buffers_time_shift_and_mixed_info(plans):
+    """Host buffers (staged, complex e included), t and c, and the binary32 path's
+    refinement report on a complex T."""
+    d, e, V = _random_hermitian(40_000, 2, 242)
+    d = d + 12.0
+    Yd = _gpu(plans[16], d, e, V, P.EXPM_FP64, t=0.5, c=6.5)
+    Yh = np.empty(V.shape, dtype=np.complex128)
+    P.expm_apply_tridiag(plans[16], d, e, V, Yh, t=0.5, shift_c=6.5)
+    np.testing.assert_array_equal(Yh, Yd)
+    Yo = _oracle(d, e, V, 16, t=0.5, c=6.5)
+    assert matrix.rel_err(Yd, Yo) <= 1e-12
+    dd, de, dv = (torch.from_numpy(np.ascontiguousarray(x)).to(DEV) for x in (d, e, V))
+    dy = torch.empty(V.shape, dtype=torch.complex128, device=DEV)
+    info = P.expm_apply_tridiag(plans[16], dd, de, dv, dy, prec=P.EXPM_MIXED_FP32, t=0.5, shift_c=6.5)
+    torch.cuda.synchronize()
+    assert info.status_worst == 0 and info.refine_iters_max >= 1 and info.resid_rel_max <= 1e-12
+    assert matrix.rel_err(dy.cpu().numpy(), Yo) <= 1e-8

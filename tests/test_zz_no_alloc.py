@@ -61,6 +61,28 @@ def test_noalloc_matches_allocating_entry_point_and_oracle_twice(prec):
     plan.close()
 
 
+@pytest.mark.parametrize("prec", [P.EXPM_FP64, P.EXPM_MIXED_F32X2])
+def test_noalloc_complex_hermitian(prec):
+    """Complex e (the phases and D^H V in the fixed array too): equal to the allocating
+    entry point and within the tolerance of the oracle."""
+    plan = P.Plan(degree=16)
+    N, r = 12_001, 2
+    g = workloads.rng(403)
+    hd = g.uniform(-12.0, -4.0, N)
+    he = g.uniform(0.5, 2.0, N - 1) * np.exp(1j * g.uniform(0.0, 2 * np.pi, N - 1))
+    hV = g.standard_normal((N, r))
+    d, e, V = (torch.from_numpy(x).to(DEV) for x in (hd, he, hV))
+    Y_ref = torch.empty((N, r), dtype=torch.complex128, device=DEV)
+    P.expm_apply_tridiag(plan, d, e, V, Y_ref, prec=prec)
+    Y = torch.full_like(Y_ref, float("nan"))
+    P.expm_apply_tridiag_noalloc(plan, d, e, V, Y, prec=prec)
+    torch.cuda.synchronize()
+    assert torch.equal(Y, Y_ref)
+    Yo, _ = matrix.apply_tridiag(hd, he, hV, coeffs.theta(16), coeffs.residues(16))
+    assert matrix.rel_err(Y.cpu().numpy(), Yo) <= TOL[prec]
+    plan.close()
+
+
 def test_noalloc_calls_after_warm_up_allocate_nothing():
     """After one warm-up call (which may load the library's module and with it the fixed
     array), further calls leave the device's free memory unchanged."""
