@@ -519,6 +519,50 @@ def _pcts(ts):
     return xs[len(xs) // 2], xs[min(len(xs) - 1, int(math.ceil(0.99 * len(xs))) - 1)]
 
 
+def _queue_small(P, plan, A, V, prec, steps, Yo, nreq=8192, cap=512):
+    """The same evaluation through the device-fed queue (expm_queue_*): latency of one
+    request at a time (submit -> completion seen by poll), and throughput with up to `cap`
+    requests in flight (nreq requests, each with its own output buffer from a pool of cap)."""
+    import torch
+    from oracle import matrix
+    q = P.Queue(plan, k=1, prec=prec, capacity=cap, idle_ms=2000.0)
+    Y = torch.empty_like(V)
+    lat = []
+    for i in range(steps + 20):
+        t0 = time.perf_counter()
+        tk = q.submit(A, V, Y)
+        while (r := q.poll(tk)) is None:
+            pass
+        if i >= 20:
+            lat.append(time.perf_counter() - t0)
+        assert r[0] == 0
+    y0 = Y.cpu().numpy()
+    pool = [torch.empty_like(V) for _ in range(cap)]
+    torch.cuda.current_stream().synchronize()  # not the device: that waits for the idle consumer
+    pending, done, nxt = [], 0, 0
+    t0 = time.perf_counter()
+    while done < nreq:
+        while nxt < nreq and len(pending) < cap:
+            tk = q.submit(A, V, pool[nxt % cap])
+            if tk is None:
+                break
+            pending.append(tk)
+            nxt += 1
+        while pending and (r := q.poll(pending[0])) is not None:
+            assert r[0] == 0
+            pending.pop(0)
+            done += 1
+    wall = time.perf_counter() - t0
+    same = all(torch.equal(y, pool[0]) for y in pool[1:])
+    st = q.state()
+    q.close()
+    p50, p99 = _pcts(lat)
+    return {"latency_us": {"p50": round(p50 * 1e6, 2), "p99": round(p99 * 1e6, 2)},
+            "throughput": {"requests": nreq, "in_flight_max": cap, "evals_per_s": round(nreq / wall, 1)},
+            "clusters": st["clusters"], "kernel_launches": st["launches"],
+            "rel_err_vs_oracle": matrix.rel_err(y0, Yo), "all_outputs_identical": bool(same)}
+
+
 def cfg_dense_small(steps=300):
     """The small plain configuration: real symmetric 64 x 64, spectrum U[-20, 0], one Gaussian
     vector, degree 12 (12 poles, 6 conjugate pairs).  Latency of one evaluation through
@@ -556,6 +600,7 @@ def cfg_dense_small(steps=300):
                      "evals_per_s": round(1.0 / min(p50, g50), 1),
                      "rel_err_vs_oracle": matrix.rel_err(y, Yo), "graph_rel_err_vs_oracle": matrix.rel_err(yg, Yo),
                      "rel_err_vs_eigen_Rn": matrix.rel_err(y, Yeig), "rel_err_vs_exp": matrix.rel_err(y, Yexp)}
+        out[name]["queue"] = _queue_small(P, plan, A, V, prec, steps, Yo)
     out["exp_bound"] = {"sup_err_n": 2.0 ** -n, "note": "|R_n(x) - e^x| <= 2^-n on x <= 0 (Prop. 2.2); "
                         "relative to |exp(A)v| this allows ~6e-4 here (reading c6)"}
     out["tolerance"] = {"fp64": 1e-12, "mixed": 1e-8}

@@ -477,6 +477,62 @@ expm_status expm_server_destroy(expm_server server);
 expm_status expm_server_set_queue_limit(expm_server server, int max_queue);
 
 /*
+ * Device-fed work queue of small dense evaluations (no counterpart in the paper: a
+ * serving pattern around eq. expAx for problems too small to amortise a kernel launch).
+ * Each request is Y = e^c R_n(tA - cI) V for one dense Hermitian A of order n <= 64,
+ * evaluated as expm_apply_dense's one-launch small path does (the same device code,
+ * compiled into another kernel: results agree with that call to rounding, and identical
+ * requests give identical results).  Instead of a launch per request, a
+ * persistent kernel of thread-block clusters (one cluster per request in flight, one CTA
+ * per solved system) takes requests from a ring of `capacity` slots in mapped host
+ * memory: submit writes a slot and publishes it, a cluster claims it, evaluates it and
+ * publishes its completion, and poll reads that completion.  Every device-side wait is
+ * bounded: when no request arrives for idle_ms the kernel exits with the exit status
+ * EXPM_ETIMEOUT (expm_queue_state); the next submit or poll that finds it finished
+ * launches it again, so no request is lost, and results only need polling to advance.
+ *   expm_queue_create   plan (its poles and weights are copied: the plan may be destroyed
+ *                       afterwards); a_is_complex: A complex Hermitian, else real
+ *                       symmetric; k right-hand sides per request, complex iff
+ *                       v_is_complex (real A with complex V solves 2k real columns);
+ *                       at most 4 solved columns and 16 solved systems (degree/2 for
+ *                       real A, degree for complex A); opts: precision (EXPM_FP64, or any
+ *                       mixed precision: the binary32 inverse with binary64-residual
+ *                       refinement), tol, max_refine, growth_max (t, shift_c and stream
+ *                       are per request / unused); capacity 1..65536 slots; max_clusters
+ *                       requests in flight at most (0: as many clusters as fit on the
+ *                       device at once); idle_ms in (0, 600000]
+ *   expm_queue_submit   n <= 64; A (n x n, ld lda), V and Y (n x k, ld ldv / ldy),
+ *                       row-major, device memory that stays valid until the request is
+ *                       polled complete; whatever writes A and V must have completed
+ *                       before the call (the kernel may read them at once: it does not
+ *                       follow stream order); t and shift_c of this request.  *ticket
+ *                       identifies it.  EXPM_EAGAIN when `capacity` submitted requests
+ *                       have not yet been polled complete (nothing is queued).
+ *   expm_queue_poll     EXPM_EAGAIN while pending; then the request's status (EXPM_OK,
+ *                       EXPM_EGROWTH, EXPM_ENOCONV as expm_apply_dense, Y written in all
+ *                       three) with info filled, and the ticket is released (a second
+ *                       poll returns EXPM_ENOTFOUND).
+ *   expm_queue_state    running: the consumer kernel is on the device; last_exit:
+ *                       EXPM_ETIMEOUT when its last run ended on an idle wait, else
+ *                       EXPM_OK; launches: kernel launches so far; clusters: requests in
+ *                       flight at most.
+ *   expm_queue_destroy  sets the stop flag (clusters leave after the request they are
+ *                       evaluating), waits for the kernel and frees everything; requests
+ *                       not yet claimed are dropped.
+ * The consumer kernel runs on the queue's own stream; a device-wide synchronisation
+ * (cudaDeviceSynchronize, or a framework call that does one) waits for it, that is until
+ * it has been idle for idle_ms: synchronise streams instead while a queue is live.
+ */
+typedef struct expm_queue_s *expm_queue;
+expm_status expm_queue_create(expm_plan plan, int a_is_complex, int k, int v_is_complex, const expm_opts *opts,
+                              int capacity, int max_clusters, double idle_ms, expm_queue *out);
+expm_status expm_queue_submit(expm_queue queue, int n, const void *A, int lda, const void *V, int ldv, void *Y,
+                              int ldy, double t, double shift_c, uint64_t *ticket);
+expm_status expm_queue_poll(expm_queue queue, uint64_t ticket, expm_info *info);
+expm_status expm_queue_state(expm_queue queue, int *running, int *last_exit, uint64_t *launches, int *clusters);
+expm_status expm_queue_destroy(expm_queue queue);
+
+/*
  * Measurement hooks (no counterpart in the paper).  When enabled on a plan, every
  * kernel launch made through that plan is bracketed by CUDA events recorded on the
  * launch stream; expm_profile_read synchronises on the recorded events and returns,

@@ -21,6 +21,7 @@ from ._native import (  # noqa: F401
     BatchGraph,
     ExpmError,
     Plan,
+    Queue,
     Server,
     expm_apply_batched,
     expm_apply_dense,

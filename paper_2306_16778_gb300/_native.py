@@ -116,6 +116,17 @@ def _load() -> ctypes.CDLL:
     L.expm_server_destroy.restype = i
     L.expm_server_set_queue_limit.argtypes = [vp, i]
     L.expm_server_set_queue_limit.restype = i
+    L.expm_queue_create.argtypes = [vp, i, i, i, ctypes.POINTER(expm_opts), i, i, ctypes.c_double, ctypes.POINTER(vp)]
+    L.expm_queue_create.restype = i
+    L.expm_queue_submit.argtypes = [vp, i, vp, i, vp, i, vp, i, ctypes.c_double, ctypes.c_double,
+                                    ctypes.POINTER(u64)]
+    L.expm_queue_submit.restype = i
+    L.expm_queue_poll.argtypes = [vp, u64, ctypes.POINTER(expm_info)]
+    L.expm_queue_poll.restype = i
+    L.expm_queue_state.argtypes = [vp, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(u64), ctypes.POINTER(i)]
+    L.expm_queue_state.restype = i
+    L.expm_queue_destroy.argtypes = [vp]
+    L.expm_queue_destroy.restype = i
     for hook in ("expm_internal_server_fail_next_factor", "expm_internal_server_workers_alive"):
         getattr(L, hook).argtypes = [vp]
         getattr(L, hook).restype = i
@@ -428,6 +439,59 @@ class BatchGraph:
     def close(self) -> None:
         if getattr(self, "_h", None):
             lib.expm_batched_graph_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Queue:
+    """Device-fed work queue of small dense evaluations (expm_queue_*): a persistent
+    kernel evaluates each submitted request (n <= 64) as it is published; poll() returns
+    None while pending, else (status, info)."""
+
+    def __init__(self, plan: "Plan", a_is_complex=False, k=1, v_is_complex=False, prec=EXPM_FP64, tol=None,
+                 max_refine=None, growth_max=None, capacity=256, max_clusters=0, idle_ms=1000.0):
+        o = make_opts(prec, tol=tol, max_refine=max_refine, growth_max=growth_max)
+        self._h = ctypes.c_void_p()
+        _check(lib.expm_queue_create(plan.handle, int(bool(a_is_complex)), int(k), int(bool(v_is_complex)),
+                                     ctypes.byref(o), int(capacity), int(max_clusters), float(idle_ms),
+                                     ctypes.byref(self._h)), "expm_queue_create")
+        self.k = int(k)
+
+    def submit(self, A, V, Y, t=1.0, shift_c=0.0):
+        """Returns the ticket, or None when the ring is full (EXPM_EAGAIN)."""
+        n = int(A.shape[0])
+        tk = ctypes.c_uint64()
+        st = lib.expm_queue_submit(self._h, n, _ptr(A), n, _ptr(V), self.k, _ptr(Y), self.k, float(t), float(shift_c),
+                                   ctypes.byref(tk))
+        if st == 6:                       # EXPM_EAGAIN
+            return None
+        _check(st, "expm_queue_submit")
+        return int(tk.value)
+
+    def poll(self, ticket: int):
+        info = expm_info()
+        st = lib.expm_queue_poll(self._h, int(ticket), ctypes.byref(info))
+        if st == 6:                       # EXPM_EAGAIN: pending
+            return None
+        if st not in (0, 3, 4):           # OK, EGROWTH, ENOCONV carry a result
+            _check(st, "expm_queue_poll")
+        return st, info
+
+    def state(self) -> dict:
+        run, last, launches, clusters = ctypes.c_int(), ctypes.c_int(), ctypes.c_uint64(), ctypes.c_int()
+        _check(lib.expm_queue_state(self._h, ctypes.byref(run), ctypes.byref(last), ctypes.byref(launches),
+                                    ctypes.byref(clusters)), "expm_queue_state")
+        return {"running": bool(run.value), "last_exit": last.value, "launches": int(launches.value),
+                "clusters": clusters.value}
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            lib.expm_queue_destroy(self._h)
             self._h = None
 
     def __del__(self):

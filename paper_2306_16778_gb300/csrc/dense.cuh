@@ -94,6 +94,40 @@ bool dense_uses_inv(const DenseGeom &g);
 // residual and sweeps land in out[0..2], device memory; usable under stream capture);
 // dense_small_run also synchronises st to read them.
 bool dense_small_fits(const DenseGeom &g);
+// one small problem for the kernels of dense_small.cu (n <= 64, kc <= 4, nsys <= 16)
+struct SmallReq {
+    int n, kc, nsys, complex_a, v_cplx, y_real, mixed, max_refine;
+    double t, tol;
+    const double *A;
+    int64_t lda;
+    const double *V;
+    int64_t ldv;
+    double *Y;
+    int64_t ldy;
+    double *out;  // worst growth, worst residual, sweeps (3 doubles)
+};
+// Device-fed work queue of small problems (queue.cu): a persistent cluster kernel whose
+// clusters claim tickets, wait (bounded) for the host to publish each ticket's request in
+// mapped host memory, evaluate it and publish its completion.
+struct SmallQueueSlot {
+    SmallReq a;        // out is set on the device (the slot's stat entry)
+    DenseSystems sys;  // poles and weights (e^c folded in), shift c
+};
+struct SmallQueueArgs {
+    SmallQueueSlot *slots;       // cap slots (mapped host memory, device view)
+    unsigned long long *seq;     // cap: ticket + 1 once the slot holds that ticket's request
+    unsigned long long *done;    // cap: ticket + 1 once that ticket is evaluated
+    double *stat;                // cap x 3: growth, residual, sweeps of the slot's last request
+    unsigned *stop;              // set by the host: exit after the current request
+    unsigned *exit_status;       // set by the kernel: EXPM_ETIMEOUT when an idle wait ran out
+    unsigned long long *claim;   // next ticket to claim (device memory)
+    unsigned *halt;              // a cluster timed out or saw stop: the others exit too (device memory)
+    int cap, nsys;
+    long long idle_ns;           // longest wait for a request before the kernel exits
+};
+// mode 0: binary64; 1..4: mixed with that many columns
+cudaError_t dense_small_queue_launch(const SmallQueueArgs &q, int mode, int nclusters, cudaStream_t st);
+int dense_small_queue_max_clusters(int mode, int nsys);  // co-resident clusters (0 on error)
 size_t dense_small_workspace_bytes();
 cudaError_t dense_small_launch(const DenseGeom &g, const DenseIO &io, const DenseSystems &sys, double *out,
                                cudaStream_t st, Profiler &prof);

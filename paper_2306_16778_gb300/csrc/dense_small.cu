@@ -40,17 +40,7 @@ constexpr int DS_K = 4;        // largest number of complex right-hand-side colu
 constexpr int DS_THREADS = 256;
 constexpr int DS_LD = DS_N + 1;  // padded row stride of the shared matrix
 
-struct DsArgs {
-    int n, kc, nsys, complex_a, v_cplx, y_real, mixed, max_refine;
-    double t, tol;
-    const double *A;
-    int64_t lda;
-    const double *V;
-    int64_t ldv;
-    double *Y;
-    int64_t ldy;
-    double *out;  // worst growth, worst residual, sweeps (3 doubles, device memory)
-};
+using DsArgs = SmallReq;
 
 template <class W> EXPM_D cx<W> cmulW(cx<W> a, cx<W> b) {
     return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re};
@@ -203,7 +193,7 @@ EXPM_D void cluster_sum(const DsArgs &a, const DenseSystems &sys, cx<double> *Xs
 
 // ---------------------------------------------------------------------------------------
 // binary64: unpivoted LU in shared memory, one warp per column for the solves.
-__global__ void __launch_bounds__(DS_THREADS) dense_small_f64_kernel(DsArgs a, DenseSystems sys) {
+EXPM_D void ds_f64_body(const DsArgs &a, const DenseSystems &sys) {
     extern __shared__ __align__(16) unsigned char ds_smem[];
     cx<double> *M = reinterpret_cast<cx<double> *>(ds_smem);                                // DS_N x DS_LD
     cx<double> *Xs = reinterpret_cast<cx<double> *>(ds_smem + sizeof(cx<double>) * DS_N * DS_LD);  // DS_N x DS_K
@@ -295,7 +285,7 @@ constexpr int DS_Q = DS_THREADS / DS_N;  // column chunks of the matrix-vector p
 // KC = number of right-hand-side columns (a template argument, so that no binary64 warp
 // instruction is issued for absent columns).
 template <int KC>
-__global__ void __launch_bounds__(DS_THREADS, 1) dense_small_mixed_kernel(DsArgs a, DenseSystems sys) {
+EXPM_D void ds_mixed_body(const DsArgs &a, const DenseSystems &sys) {
     extern __shared__ __align__(16) unsigned char ds_smem[];
     cx<float> *MT = reinterpret_cast<cx<float> *>(ds_smem);  // DS_N x DS_LD: (M~^{-1})^T
     unsigned char *p = ds_smem + sizeof(cx<float>) * DS_N * DS_LD;
@@ -554,6 +544,116 @@ __global__ void __launch_bounds__(DS_THREADS, 1) dense_small_mixed_kernel(DsArgs
     cluster_sum(a, sys, Xs, stat);
 }
 
+__global__ void __launch_bounds__(DS_THREADS) dense_small_f64_kernel(DsArgs a, DenseSystems sys) {
+    ds_f64_body(a, sys);
+}
+template <int KC>
+__global__ void __launch_bounds__(DS_THREADS, 1) dense_small_mixed_kernel(DsArgs a, DenseSystems sys) {
+    ds_mixed_body<KC>(a, sys);
+}
+
+// ---------------------------------------------------------------------------------------
+// Device-fed queue: a persistent kernel of `nclusters` clusters of nsys CTAs.  Thread 0 of
+// each cluster's CTA 0 claims the next ticket (atomic counter), waits until the host has
+// published that ticket's request in mapped host memory (sequence word = ticket + 1),
+// broadcasts it to the cluster's CTAs through distributed shared memory, and after the
+// evaluation -- the same body as the one-launch kernels -- publishes ticket + 1 as the
+// slot's completion word (system-scope release after a system fence, so Y and the slot's
+// statistics are visible first).  Every wait is bounded: a cluster that waits longer than
+// idle_ns for a request sets the device halt flag and the ETIMEOUT exit status, and every
+// cluster leaves at its next claim once halt or the host's stop flag is set (a request
+// already being evaluated is finished first).  After a restart the claim counter starts at
+// the host's oldest unfinished ticket; tickets already completed are skipped.
+EXPM_D unsigned long long ld_acquire_sys(const unsigned long long *p) {
+    unsigned long long v;
+    asm volatile("ld.acquire.sys.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+EXPM_D unsigned ld_relaxed_sys(const unsigned *p) {
+    unsigned v;
+    asm volatile("ld.relaxed.sys.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+EXPM_D void st_release_sys(unsigned long long *p, unsigned long long v) {
+    asm volatile("st.release.sys.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+EXPM_D long long global_ns() {
+    long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(DS_THREADS, 1) dense_small_queue_kernel(SmallQueueArgs q) {
+    __shared__ DsArgs s_a;
+    __shared__ DenseSystems s_sys;
+    __shared__ unsigned long long s_ticket;
+    __shared__ int s_go;
+    cg::cluster_group cluster = cg::this_cluster();
+    const int rank = (int)cluster.block_rank(), tid = threadIdx.x;
+    bool timed_out = false;
+    for (;;) {
+        if (rank == 0 && tid == 0) {
+            int go = 0;
+            unsigned long long t = 0;
+            if (!ld_relaxed_sys(q.halt) && !ld_relaxed_sys(q.stop)) {
+                t = atomicAdd(q.claim, 1ull);
+                const long long t0 = global_ns();
+                for (;;) {
+                    if (ld_acquire_sys(q.seq + t % q.cap) == t + 1) {
+                        if (ld_acquire_sys(q.done + t % q.cap) == t + 1) {  // completed before a restart
+                            t = atomicAdd(q.claim, 1ull);
+                            continue;
+                        }
+                        go = 1;
+                        break;
+                    }
+                    if (ld_relaxed_sys(q.halt) || ld_relaxed_sys(q.stop)) break;
+                    if (global_ns() - t0 > q.idle_ns) {
+                        atomicExch(q.halt, 1u);
+                        timed_out = true;
+                        break;
+                    }
+                    __nanosleep(256);
+                }
+            }
+            for (int r = 0; r < q.nsys; ++r) {
+                *cluster.map_shared_rank(&s_go, r) = go;
+                *cluster.map_shared_rank(&s_ticket, r) = t;
+            }
+        }
+        cluster.sync();
+        if (!s_go) break;
+        const int slot = (int)(s_ticket % (unsigned long long)q.cap);
+        // every CTA acquires the published sequence word itself (system scope, on its own
+        // SM), so that its loads of the slot and of the request's A and V see what the host
+        // ordered before publishing, not lines cached by an earlier request
+        if (tid == 0) (void)ld_acquire_sys(q.seq + slot);
+        __syncthreads();
+        {  // the request into shared memory (one 8-byte word per thread and pass)
+            const unsigned long long *src = reinterpret_cast<const unsigned long long *>(&q.slots[slot].sys);
+            unsigned long long *dst = reinterpret_cast<unsigned long long *>(&s_sys);
+            for (int w = tid; w < (int)(sizeof(DenseSystems) / 8); w += DS_THREADS) dst[w] = __ldcv(src + w);
+            const unsigned long long *sa = reinterpret_cast<const unsigned long long *>(&q.slots[slot].a);
+            unsigned long long *da = reinterpret_cast<unsigned long long *>(&s_a);
+            if (tid < (int)(sizeof(DsArgs) / 8)) da[tid] = __ldcv(sa + tid);
+        }
+        __syncthreads();
+        if (tid == 0) s_a.out = q.stat + 3 * slot;
+        __syncthreads();
+        if constexpr (MODE == 0) {
+            ds_f64_body(s_a, s_sys);
+        } else {
+            ds_mixed_body<MODE>(s_a, s_sys);
+        }
+        if (rank == 0 && tid == 0) {  // Y and the statistics first, then the completion word
+            __threadfence_system();
+            st_release_sys(q.done + slot, s_ticket + 1);
+        }
+    }
+    if (rank == 0 && tid == 0 && timed_out) atomicExch(q.exit_status, (unsigned)EXPM_ETIMEOUT);
+}
+
 constexpr size_t DS_SMEM_F64 = sizeof(cx<double>) * DS_N * DS_LD + sizeof(cx<double>) * DS_N * DS_K;
 constexpr size_t DS_SMEM_MIXED = sizeof(cx<float>) * DS_N * DS_LD + sizeof(cx<double>) * DS_N * DS_LD +
                                  sizeof(cx<double>) * DS_N * DS_K + sizeof(cx<double>) * DS_Q * DS_N * DS_K +
@@ -593,6 +693,76 @@ cudaError_t launch_small(K kernel, int variant, size_t smem, const DsArgs &a, co
 }
 
 }  // namespace
+
+namespace {
+constexpr size_t ds_smem_of(int mode) { return mode == 0 ? DS_SMEM_F64 : DS_SMEM_MIXED; }
+
+template <int MODE>
+cudaLaunchConfig_t queue_config(int nsys, int nclusters, cudaStream_t st, cudaLaunchAttribute *attr) {
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3((unsigned)(nsys * nclusters));
+    cfg.blockDim = dim3(DS_THREADS);
+    cfg.dynamicSmemBytes = ds_smem_of(MODE);
+    cfg.stream = st;
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)nsys;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cfg;
+}
+
+template <int MODE>
+cudaError_t queue_attrs() {
+    auto k = dense_small_queue_kernel<MODE>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ds_smem_of(MODE));
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    return e;
+}
+
+template <int MODE>
+cudaError_t queue_launch(const SmallQueueArgs &q, int nclusters, cudaStream_t st) {
+    cudaError_t e = queue_attrs<MODE>();
+    if (e != cudaSuccess) return e;
+    cudaLaunchAttribute attr[1];
+    cudaLaunchConfig_t cfg = queue_config<MODE>(q.nsys, nclusters, st, attr);
+    return cudaLaunchKernelEx(&cfg, dense_small_queue_kernel<MODE>, q);
+}
+
+template <int MODE>
+int queue_clusters(int nsys) {
+    if (queue_attrs<MODE>() != cudaSuccess) return 0;
+    cudaLaunchAttribute attr[1];
+    cudaLaunchConfig_t cfg = queue_config<MODE>(nsys, 1, nullptr, attr);
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, dense_small_queue_kernel<MODE>, &cfg) != cudaSuccess) return 0;
+    return n;
+}
+}  // namespace
+
+cudaError_t dense_small_queue_launch(const SmallQueueArgs &q, int mode, int nclusters, cudaStream_t st) {
+    if (q.nsys < 1 || q.nsys > 16 || nclusters < 1 || q.cap < 1) return cudaErrorInvalidValue;
+    switch (mode) {
+        case 0: return queue_launch<0>(q, nclusters, st);
+        case 1: return queue_launch<1>(q, nclusters, st);
+        case 2: return queue_launch<2>(q, nclusters, st);
+        case 3: return queue_launch<3>(q, nclusters, st);
+        case 4: return queue_launch<4>(q, nclusters, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
+int dense_small_queue_max_clusters(int mode, int nsys) {
+    switch (mode) {
+        case 0: return queue_clusters<0>(nsys);
+        case 1: return queue_clusters<1>(nsys);
+        case 2: return queue_clusters<2>(nsys);
+        case 3: return queue_clusters<3>(nsys);
+        case 4: return queue_clusters<4>(nsys);
+    }
+    return 0;
+}
 
 bool dense_small_fits(const DenseGeom &g) {
     return g.ninst == 1 && g.n <= DS_N && g.kc <= DS_K && g.nsys >= 1 && g.nsys <= 16;
