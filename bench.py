@@ -155,6 +155,28 @@ def max_over_ranks(vals, world, device=None):
     return [float(x) for x in t.tolist()]
 
 
+def shard_columns(r, rank, world):
+    """Right-hand-side columns [c0, c1) of `rank` when one evaluation's r columns are split
+    over `world` ranks: the columns of eq. expAx are independent, so each rank evaluates
+    its block with the whole operator and the result is the concatenation (no exchange
+    until the gather)."""
+    base, extra = divmod(r, world)
+    c0 = rank * base + min(rank, extra)
+    return c0, c0 + base + (1 if rank < extra else 0)
+
+
+def shard_instances(sizes, world):
+    """Instances of an uneven batch assigned to `world` ranks: longest first, each to the
+    rank with the least work so far (n^3 per instance); one ascending index list per rank."""
+    load = [0.0] * world
+    out = [[] for _ in range(world)]
+    for i in sorted(range(len(sizes)), key=lambda j: (-sizes[j], j)):
+        r = min(range(world), key=lambda q: (load[q], q))
+        out[r].append(i)
+        load[r] += float(sizes[i]) ** 3
+    return [sorted(x) for x in out]
+
+
 def whole_job_value(world, steps, max_seconds):
     """Evaluations per second of the whole job: every rank runs `steps` evaluations of its
     own replica (weak scaling) in at most `max_seconds`."""
