@@ -195,6 +195,30 @@ def test_tridiag_general_matches_dense(complex_e):
     assert matrix.rel_err(Yt, ref) < 1e-12
 
 
+def test_tridiag_diagonal_unitary_gauge():
+    """The identity behind the complex-off-diagonal reading (Sec. 3, A Hermitian): for a
+    diagonal unitary D0 = diag(exp(i psi)), T = D0 T~ D0^H has off-diagonal
+    e_i = |e_i| exp(i (psi_i - psi_{i+1})) and every resolvent, hence e^c R_n(tT - cI)V,
+    equals D0 [e^c R_n(tT~ - cI)] (D0^H V).  The oracle solves both sides directly (complex
+    banded systems against real ones), so a dropped conjugate on the lower diagonal or a
+    swapped phase fails here."""
+    g = workloads.rng(113)
+    N = 257
+    d = g.uniform(-12.0, -4.0, N)
+    eabs = g.uniform(0.5, 2.0, N - 1)
+    psi = g.uniform(0.0, 2 * np.pi, N)
+    ph = np.exp(1j * psi)
+    e = eabs * ph[:-1] * np.conj(ph[1:])
+    V = g.standard_normal((N, 3)) + 1j * g.standard_normal((N, 3))
+    th, a = _coeffs(16)
+    Y, _ = matrix.apply_tridiag(d, e, V, th, a, t=0.8, c=0.5)
+    Yr, _ = matrix.apply_tridiag(d, eabs, np.conj(ph)[:, None] * V, th, a, t=0.8, c=0.5)
+    assert matrix.rel_err(Y, ph[:, None] * Yr) < 1e-13
+    # the gauge is not a symmetry of the wrong (conjugate-free) banded matrix
+    Yw, _ = matrix.apply_dense(np.diag(d) + np.diag(e, 1) + np.diag(e, -1), V, th, a, t=0.8, c=0.5)
+    assert matrix.rel_err(Yw, Y) > 1e-3
+
+
 @pytest.mark.parametrize("dx,dy", [(1, 1), (5, 7), (12, 9)])
 def test_laplacian2d_closed_form(dx, dy):
     """2D separable operator (Sec. 5): the DST-I closed form reproduces A V itself (f = id:
