@@ -16,10 +16,12 @@
 //
 // phi is a prefix product of unit complex numbers u_i = conj(e_{i-1}) / |e_{i-1}|
 // (u_0 = 1).  It is formed as a three-level scan (4 rows serially per thread, the
-// block's 256 threads by warp shuffles, the blocks' products by one scanning block),
-// so each phi_i is a product of at most about 30 rounded complex products, and it is
-// renormalised to unit modulus; its phase error stays within a few tens of binary64
-// units, far below the 1e-12 target of the binary64 path.  For a real e every factor is
+// block's 256 threads by warp shuffles, the blocks' products by one scanning block), so
+// the tree adds at most about 30 rounded complex products to each phi_i; but phi_i also
+// carries the rounding errors of all u_j, j <= i (a few units each).  Their phases add
+// up as a random walk (about sqrt(i) units: the result's error is 1.2e-13 at N = 2^20,
+// measured), and their moduli would drift further, so phi_i is renormalised to unit
+// modulus (without it the error was 4e-11 at N = 2^20).  For a real e every factor is
 // exactly +-1 (products of +-1 and 0 imaginary parts are exact), so the result is then
 // bit-identical to that of the real-off-diagonal path on the same data.
 #include "tridiag.cuh"
