@@ -57,9 +57,9 @@ typedef enum expm_status {
     EXPM_EGROWTH = 3,    /* pivot growth of an unpivoted LU exceeded opts.growth_max */
     EXPM_ENOCONV = 4,    /* iterative refinement did not reach opts.tol            */
     EXPM_ETIMEOUT = 5,   /* a bounded device-side wait gave up                     */
-    EXPM_EAGAIN = 6,     /* server: queue full, or request still pending           */
+    EXPM_EAGAIN = 6,     /* server / queue: full, or request still pending         */
     EXPM_ECUDA = 7,      /* a CUDA runtime call failed                             */
-    EXPM_ENOTFOUND = 8,  /* server: unknown ticket or operator id                  */
+    EXPM_ENOTFOUND = 8,  /* server / queue: unknown or released ticket, unknown id */
     EXPM_ENOTSUP = 9     /* combination of options not implemented                 */
 } expm_status;
 
